@@ -1,0 +1,310 @@
+"""Throughput of the SE-RBFNet optimisation hot path: fwd+bwd point-kernel
+pairs per second for full Algorithm 3 epochs (neighbour rebuild, forward,
+adjoint, optimiser step with gates, deletion and addition checks).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c2|c3|c1|c4]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the same workload
+
+Prints one JSON line on rank 0.  With N > 1 (torchrun) every rank fits its own
+replica of the workload (the path does not shard across GPUs: replicas only,
+weak scaling); value = pairs of all ranks / max over ranks of the timed span.
+Inputs are synthetic (seeded analytic SDFs); the L2 cache is flushed between
+timed steps.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "ERBF fwd+bwd point-kernel pairs/s"
+UNIT = "pairs/s"
+FWD_INSTR_PER_PAIR = 17  # minimum FP32-pipe instructions of one forward pair
+LAUNCHES_PER_STEP = 13   # prep, super lists, cell lists, forward, 4 adjoint, step, prune, 3 addition
+WORKLOADS = {
+    "c1": ("sphere |x|-0.5 on 32^3, M=64 isotropic", None),
+    "c2": ("torus R=0.5 r=0.2 on 32^3+64^3 union (after 32^3->64^3 refinement), M=512 anisotropic", [32, 64]),
+    "c3": ("union of 20 random primitives on 128^3, M=4096", None),
+    "c4": ("union of 60 random primitives, 256^3 band |S|<0.1 + 1/8 far field, M=16384", None),
+}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(pairs_local, seconds_local, ms_local, group=None):
+    """Whole-job throughput: pairs summed over ranks over the slowest rank's span."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return pairs_local / seconds_local, ms_local
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    t = torch.tensor([pairs_local], dtype=torch.float64, device=dev)
+    s = torch.tensor([seconds_local, ms_local], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX, group=group)
+    return float(t.item()) / float(s[0].item()), float(s[1].item())
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        self.path = tempfile.mktemp(suffix=".csv")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_problem(name, device):
+    from paper_2505_02350_gb300 import field
+    desc, layers = WORKLOADS[name]
+    cfg, lay, P = synth.workload(name, layers=layers)
+    x = np.concatenate([l[0] for l in lay])
+    y = np.concatenate([l[1] for l in lay])
+    z = np.concatenate([l[2] for l in lay])
+    S = np.concatenate([l[3] for l in lay])
+    grids = cfg["grids"] if layers is None else layers
+    pb = field.Problem(x, y, z, S, P, cfg["m"], synth.spacing(max(grids)), cap=2 * cfg["m"], device=device)
+    return pb, desc
+
+
+def run_native(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pb, desc = build_problem(args.config, dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB of L2
+    for _ in range(args.warmup):
+        pb.epoch()
+    torch.cuda.synchronize()
+    flags, needed = pb.status()
+    if flags:
+        raise RuntimeError("capacity flags %d needed %s" % (flags, needed))
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    pairs = torch.zeros(K, 2, dtype=torch.float64, device=dev)
+    sampler = ClockSampler(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    for k in range(K):
+        flush.fill_(k & 255)
+        e = ev[k]
+        e[0].record()
+        pb.build_neighbors()
+        e[1].record()
+        pb.forward()
+        e[2].record()
+        pb.backward()
+        pb.step()
+        pb.prune()
+        pb.add()
+        e[3].record()
+        pairs[k].copy_(pb.stats[4:6])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [ev[k][0].elapsed_time(ev[k][3]) for k in range(K)]
+    fwd_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
+    pr = pairs.cpu().numpy()
+    pf, pbk = pr[:, 0], pr[:, 1]
+    seconds = sum(step_ms) / 1e3
+    value, ms_max = aggregate(float(pf.sum() + pbk.sum()), seconds, sum(step_ms) / K)
+
+    # end to end through the public API with host buffers: per step the
+    # training points go host -> device from pinned memory, and the loss terms
+    # come back device -> host.
+    n = pb.n
+    host_pts = torch.stack([pb.xb[:n], pb.yb[:n], pb.zb[:n], pb.tb[:n]]).cpu().pin_memory()
+    host_stats = torch.zeros(16, dtype=torch.float64).pin_memory()
+    dev_pts = [pb.xb, pb.yb, pb.zb, pb.tb]
+    torch.cuda.synchronize()
+    e2e_pairs = 0.0
+    te = time.perf_counter()
+    for k in range(K):
+        for r in range(4):
+            dev_pts[r][:n].copy_(host_pts[r], non_blocking=True)
+        pb.epoch()
+        host_stats.copy_(pb.stats, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_pairs += float(host_stats[4] + host_stats[5])
+    e2e_s = time.perf_counter() - te
+    e2e_value, _ = aggregate(e2e_pairs, e2e_s, 0.0)
+
+    peaks = load_peaks()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_instr = nsm * 128 * sm_mhz * 1e6  # FP32 lanes x clock
+    fwd_s = sum(fwd_ms) / 1e3
+    achieved = FWD_INSTR_PER_PAIR * float(pf.sum()) / fwd_s
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "config": args.config, "points": n, "kernels": pb.m(),
+                   "pairs_fwd_per_step": float(pf.mean()), "pairs_bwd_per_step": float(pbk.mean()),
+                   "l2_flush": "256 MiB buffer written between timed steps", "parallelism": "replicas"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 128},
+        "gpu_launches": LAUNCHES_PER_STEP * K,
+        "roofline": {"bound": "alu", "kernel": "k_forward", "achieved": achieved / 1e12,
+                     "peak": peak_instr / 1e12, "unit": "T FP32-instr/s", "frac": achieved / peak_instr,
+                     "traffic": None, "instr_per_pair": FWD_INSTR_PER_PAIR,
+                     "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz" % (nsm, sm_mhz)},
+        "breakdown_ms": {"build_neighbors": statistics.mean(ev[k][0].elapsed_time(ev[k][1]) for k in range(K)),
+                         "forward": statistics.mean(fwd_ms),
+                         "backward_step_prune_add": statistics.mean(
+                             ev[k][2].elapsed_time(ev[k][3]) for k in range(K))},
+        "wall_s": wall,
+        "clocks": clocks,
+    }
+    return out, pb
+
+
+def time_oracle(name, budget_s=12.0, min_steps=1):
+    """The FP64 oracle as it stands on the host cores, on the same workload:
+    brute-force neighbour test + forward + App. A gradients per step."""
+    import oracle
+    desc, layers = WORKLOADS[name]
+    cfg, lay, P = synth.workload(name, layers=layers)
+    x = np.concatenate([l[0] for l in lay])
+    y = np.concatenate([l[1] for l in lay])
+    z = np.concatenate([l[2] for l in lay])
+    S = np.concatenate([l[3] for l in lay])
+    t, _, _ = oracle.normalize(S)
+    t = t.astype(np.float32)
+    m = cfg["m"]
+    P64 = P.astype(np.float64)
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    n = x.size
+    # bounded sample: a random subset of the points, all kernels
+    frac = 1.0 if n * m <= 2e8 else 2e8 / (n * m)
+    g = np.random.default_rng(0)
+    idx = np.sort(g.choice(n, int(n * frac), replace=False)) if frac < 1 else np.arange(n)
+    xs, ys, zs, ts = x[idx], y[idx], z[idx], t[idx]
+    steps, pairs, t0 = 0, 0.0, time.perf_counter()
+    while steps < min_steps or time.perf_counter() - t0 < budget_s:
+        psi, err, mask, st = oracle.forward(xs, ys, zs, ts, P64, m)
+        g2, npb = oracle.backward(xs, ys, zs, err, P64, m)
+        pairs += st[4] + npb
+        steps += 1
+    dt = time.perf_counter() - t0
+    sample = "%d of %d points (all %d kernels), %d oracle steps" % (idx.size, n, m, steps)
+    return pairs / dt, cores, sample, steps, dt, desc
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    v, cores, sample, steps, dt, desc = time_oracle(args.config)
+    return {
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": steps, "warmup": 0,
+        "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": desc, "config": args.config},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2505_02350_gb300 import build
+    build.build()
+    out, pb = run_native(args, ws, rank, local)
+    if rank == 0:
+        if ws == 1 and not args.no_cpu_baseline:
+            v, cores, sample, steps, dt, _ = time_oracle(args.config)
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

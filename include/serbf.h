@@ -1,0 +1,288 @@
+/*
+ * serbf.h -- C ABI of the GB300 (sm_103a) SE-RBFNet optimisation hot path.
+ *
+ * The library fits precomputed signed-distance samples with a sparse sum of
+ * ellipsoidal radial basis functions, following "Approximating Signed Distance
+ * Fields With Sparse Ellipsoidal Radial Basis Function Networks" (SE-RBFNet):
+ *
+ *   Psi(v_i) = sum_j w_j |w_j| exp(-|| D_j R_j (v_i - c_j) ||^2)      (Eq. 3-26)
+ *
+ * restricted to the support of each kernel (Eq. 3-15-1), with the loss of
+ * Eq. 3-19 over the filtered points of Eq. 3-18, the analytic gradients of
+ * App. A, the dynamic weighting of Eq. 3-21 and Adam (Algorithm 3), kernel
+ * deletion (Eq. 3-27), adaptive addition (Algorithm 2, Eq. 3-24) and
+ * coarse-to-fine refinement (Sec. 3.4.2).
+ *
+ * Conventions for every entry point
+ *   - Pointers named *_dev, and every array argument unless stated otherwise,
+ *     are DEVICE pointers owned by the caller.  The library allocates no
+ *     memory of its own: scratch lives in a caller-provided device buffer
+ *     described by a serbf_workspace (serbf_workspace_bytes/_init).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls are asynchronous on that stream unless documented as synchronising.
+ *   - Return value: SERBF_OK or a negative SERBF_E* code.  Argument errors are
+ *     detected on the host before anything is launched.  Capacity overflows
+ *     found on the device set a sticky flag read by serbf_status().
+ *   - Parameters: one float array of 10 rows x `cap` columns, row r at p + r*cap,
+ *     rows cx, cy, cz, d1, d2, d3, theta_x, theta_y, theta_z, w  (Sec. 3.2;
+ *     d_k multiplies the rotated offset, i.e. it is an inverse axis length).
+ *     The live count m is a DEVICE int32 so that deletion and addition can run
+ *     without a host round trip.
+ *   - Points: after serbf_bin_points every per-point array is in BINNED order
+ *     (sorted by cell, then original index); perm[k] is the original index of
+ *     binned point k.  Neighbour lists index binned points.
+ *   - Rotation: R is the matrix whose entries r1..r9 are listed in App. A.
+ */
+#ifndef SERBF_H
+#define SERBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SERBF_OK 0
+#define SERBF_EINVAL -1    /* NULL pointer, bad size or bad configuration */
+#define SERBF_ENOMEM -2    /* workspace buffer too small */
+#define SERBF_ECAPACITY -3 /* a list or array capacity is too small (see serbf_status) */
+#define SERBF_ECUDA -4     /* a CUDA launch or copy failed */
+#define SERBF_ETIMEOUT -5  /* a bounded device wait gave up */
+
+#define SERBF_NPARAM 10
+
+/* device status flags (bitmask) reported by serbf_status */
+#define SERBF_FLAG_SUPER_LIST 1   /* a super-cell candidate list exceeded super_cap */
+#define SERBF_FLAG_CELL_LIST 2    /* a cell candidate list exceeded cell_cap */
+#define SERBF_FLAG_ADD_CAPACITY 4 /* addition truncated at the parameter capacity */
+#define SERBF_FLAG_ROWS 8         /* a kernel's support spans more cell rows than supported */
+
+/* indices into the double stats[SERBF_NSTATS] device array */
+#define SERBF_STAT_L2 0        /* sum over id_all of E_i^2                 (Eq. 3-19) */
+#define SERBF_STAT_L1 1        /* sum_j |w_j| before the update            (Eq. 3-14_2) */
+#define SERBF_STAT_MAXE 2      /* max over id_all of |E_i|                 (Eq. l1_activate2) */
+#define SERBF_STAT_COUNT 3     /* |id_all|                                 (Eq. 3-18) */
+#define SERBF_STAT_PAIRS_FWD 4 /* point-kernel pairs evaluated by the forward */
+#define SERBF_STAT_PAIRS_BWD 5 /* point-kernel pairs evaluated by the adjoint */
+#define SERBF_STAT_ALPHA 6     /* alpha of the last step                   (Eq. 3-21) */
+#define SERBF_STAT_BETA 7      /* beta = 1 - alpha */
+#define SERBF_STAT_BF 8        /* b_f = #{|w_j| >= tau_d} after the step   (Sec. 3.4.3) */
+#define SERBF_STAT_LOSS 9      /* alpha L2 + beta L1 */
+#define SERBF_NSTATS 16
+
+/* Hyper-parameters.  serbf_config_default fills the values of the Algorithm 3
+ * input line and Sec. 4.1; the Adam moments are the Kingma-Ba defaults. */
+typedef struct {
+    double eps;        /* epsilon of the support radius, Eq. 3-15 (1e-7) */
+    double tau1, tau2; /* point filter, Eq. 3-18 (0.9, 1.1) */
+    double tau_m;      /* max-error gate, Eq. l1_activate2 (0.02) */
+    double tau_d;      /* deletion threshold, Eq. 3-27 (0.01) */
+    double tau_l1;     /* basis-count stability, Eq. add_activate (5) */
+    double tau_l2;     /* L2 stability, Eq. l1_activate (0.5) */
+    double lr;         /* Adam learning rate of the first phase (0.01) */
+    double lr_p2;      /* learning rate at T^e (1e-3), cosine-annealed ... */
+    double lr_min;     /* ... to lr_min at M^e (1e-5) */
+    double beta1, beta2, adam_eps; /* Adam (0.9, 0.999, 1e-8) */
+    double topk_frac;  /* addition keeps the top fraction of id_all by |E| (0.01); <= 0: no limit */
+    double add_radius; /* Algorithm 2 local-maximum radius r (world units) */
+    double dbar_min;   /* lower clamp of dbar in Eq. 3-24 (world units) */
+    int32_t k_l1, k_l2; /* window lengths (50, 10) */
+    int32_t T_e, M_e;  /* phase switch and last epoch (1600, 2000) */
+    int32_t kahan;     /* 1: compensated per-kernel sums in the adjoint */
+    int32_t reserved[3];
+} serbf_config;
+
+/* Optimiser state of Algorithm 3; lives in DEVICE memory (sizeof bytes). */
+typedef struct {
+    int32_t epoch;    /* completed epochs e_p */
+    int32_t l1_optim; /* Algorithm 3 flag */
+    int32_t phase2;   /* e_p reached T^e */
+    int32_t adam_t;   /* Adam step counter (reset to 0 when kernels are added) */
+    int32_t do_prune; /* Eq. 3-27 due (consumed by serbf_prune) */
+    int32_t do_add;   /* Eq. 3-24 due (consumed by serbf_add_kernels) */
+    int32_t n_l2, n_bf;
+    int32_t m_added, m_pruned;
+    int32_t reserved[2];
+    double lr;        /* learning rate of the next epoch */
+    double alpha, beta;
+    double l2_hist[64];  /* last k_l2 values of L2, oldest first */
+    int32_t bf_hist[256]; /* last k_l1 values of b_f, oldest first */
+} serbf_state;
+
+typedef struct {
+    const float *x, *y, *z; /* binned coordinates */
+    const float *t;         /* normalised targets, Eq. 3-10 (binned) */
+    int64_t n;
+} serbf_points;
+
+typedef struct {
+    float *p;     /* 10 x cap */
+    int32_t *m;   /* device: live kernel count */
+    int32_t cap;
+} serbf_params;
+
+typedef struct {
+    int64_t *rowptr; /* rows + 1 entries */
+    uint32_t *col;   /* capacity `cap` entries */
+    int64_t cap;
+} serbf_csr;
+
+typedef struct {
+    float origin[3]; /* lower corner of cell (0, 0, 0) */
+    float h;         /* cell edge length */
+    int32_t n[3];    /* cells per axis */
+} serbf_grid;
+
+typedef struct {
+    int64_t max_points;   /* training-set capacity */
+    int32_t max_kernels;  /* parameter capacity (== serbf_params.cap) */
+    int32_t max_cells;    /* >= n[0]*n[1]*n[2] of every grid used */
+    int32_t cell_cap;     /* candidate kernels per cell list */
+    int32_t super_cap;    /* candidate kernels per super-cell list */
+    int32_t super_factor; /* cells per super-cell edge (1..16) */
+    int32_t reserved;
+} serbf_ws_sizes;
+
+typedef struct serbf_workspace serbf_workspace; /* opaque, host memory of serbf_workspace_struct_size() bytes */
+
+/* ------------------------------------------------------------------ setup */
+const char *serbf_version(void);
+const char *serbf_status_string(int code);
+
+/* Fills *cfg with the defaults listed above (add_radius and dbar_min 0: the
+ * caller sets them from its grid spacing).  Returns SERBF_EINVAL for NULL. */
+int serbf_config_default(serbf_config *cfg);
+
+/* Host bytes the caller must provide for one serbf_workspace object. */
+size_t serbf_workspace_struct_size(void);
+
+/* Device bytes needed for the given capacities; EINVAL on non-positive sizes. */
+int serbf_workspace_bytes(const serbf_ws_sizes *sz, size_t *bytes);
+
+/* Carves the caller's device buffer `dev` (>= serbf_workspace_bytes, 256-byte
+ * aligned) into the scratch arrays.  ws points to serbf_workspace_struct_size()
+ * bytes of caller-owned host memory.  Synchronous (clears the status word).
+ * ENOMEM if `bytes` is too small, EINVAL on bad sizes or alignment. */
+int serbf_workspace_init(serbf_workspace *ws, void *dev, size_t bytes, const serbf_ws_sizes *sz);
+
+/* Reads and optionally clears the device status flags (synchronises `stream`).
+ * needed[0..3]: largest super list, cell list, kernel rows and requested
+ * additions seen since the last clear.  Returns SERBF_ECAPACITY when a flag is
+ * set, SERBF_OK otherwise. */
+int serbf_status(serbf_workspace *ws, int32_t *flags, int64_t needed[4], int clear, void *stream);
+
+/* Writes the initial Algorithm 3 state (epoch 0, l1_optim false, lr = cfg->lr). */
+int serbf_state_init(serbf_state *st_dev, const serbf_config *cfg, void *stream);
+
+/* ------------------------------------------------------------------ a1 */
+/* Eq. 3-10 (Sec. 3.3): t_i = 2 exp(-h (S_i - m)^2), m = min_i S_i,
+ * h = ln 2 / m^2, evaluated in double and rounded to float.  mh_dev[0] = m,
+ * mh_dev[1] = h.  Requires m != 0 (EINVAL is not detectable on the host; a
+ * zero minimum yields non-finite t). */
+int serbf_normalize_sdf(const float *S, float *t, int64_t n, double *mh_dev, serbf_workspace *ws,
+                        void *stream);
+
+/* ------------------------------------------------------------------ a2 */
+/* Cell binning of the training points (the neighbour structure that serves
+ * the support test of Eq. 3-15; the paper leaves its data structure open).
+ * Cell key per axis k = clamp(floor(fl(fl(x - origin) / h)), 0, n - 1), linear
+ * key (kz * ny + ky) * nx + kx; points are radix-sorted by (key, index).
+ * Writes perm (binned -> original index) and the binned coordinates, and
+ * records cell ranges, cell/super-cell bounding boxes and 32-point tiles in
+ * the workspace.  SYNCHRONISES the stream once (reads the tile count).
+ * EINVAL: n > max_points, grid cells > max_cells, non-positive h. */
+int serbf_bin_points(const float *x, const float *y, const float *z, int64_t n, const serbf_grid *grid,
+                     uint32_t *perm, float *xb, float *yb, float *zb, serbf_workspace *ws, void *stream);
+
+/* dst[k] = src[perm[k]] for k < n (puts targets, SDF values, ... into binned order). */
+int serbf_gather(const float *src, const uint32_t *perm, float *dst, int64_t n, void *stream);
+
+/* ------------------------------------------------------------------ a3 */
+/* Per-step rebuild of the kernel <-> point neighbour structure, Eq. 3-15-1:
+ * point v_i is in the support of kernel j iff, in float with no fused
+ * multiply-add, fl(fl(fl(dx*dx) + fl(dy*dy)) + fl(dz*dz)) < r2_j where
+ * dx = fl(x_i - cx_j), ..., r2_j = fl(fl(-ln eps) / min_k fl(d_jk * d_jk)).
+ * Always rebuilds the workspace's cell -> candidate-kernel lists used by
+ * serbf_forward / serbf_backward (asynchronous).  If kmajor and/or pmajor is
+ * non-NULL it also writes the explicit CSR lists: kernel-major rows (m + 1
+ * rowptr entries) list binned point indices in ascending order; point-major
+ * rows (n + 1 entries) list kernel indices in ascending order.  Producing CSR
+ * lists SYNCHRONISES the stream; when a col capacity is too small the call
+ * returns SERBF_ECAPACITY with the pair count in *npairs (rowptr is valid).
+ * npairs (host, may be NULL) receives the number of pairs when CSR lists were
+ * requested. */
+int serbf_build_neighbors(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg,
+                          serbf_csr *kmajor, serbf_csr *pmajor, int64_t *npairs, serbf_workspace *ws,
+                          void *stream);
+
+/* ------------------------------------------------------------------ a4 */
+/* Eq. 3-26 forward over the pairs of Eq. 3-15-1, Eq. 3-18 filter and the
+ * Eq. 3-19 loss terms: psi[i], mask[i] (1 = in id_all), err[i] = psi - t on
+ * id_all and 0 elsewhere; stats[L2], stats[MAXE], stats[COUNT] and
+ * stats[PAIRS_FWD] (device doubles, deterministic).  Pair arithmetic in
+ * float, loss sums in double.  Uses the lists of the last
+ * serbf_build_neighbors call for these parameters. */
+int serbf_forward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi,
+                  float *err, uint8_t *mask, double *stats, serbf_workspace *ws, void *stream);
+
+/* ------------------------------------------------------------------ a5 */
+/* App. A gradients of sum_i err_i^2 (i.e. of L2 when err is the forward's E)
+ * with respect to all ten parameters of every live kernel, summed over the
+ * pairs of Eq. 3-15-1 with err_i != 0; grad is 10 x cap (same rows as p).
+ * Basis values are recomputed, never stored.  stats[PAIRS_BWD] receives the
+ * number of pairs.  For an arbitrary upstream gradient g of Psi pass
+ * err = g / 2.  Uses the lists of the last serbf_build_neighbors call. */
+int serbf_backward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg,
+                   const float *err, float *grad, double *stats, serbf_workspace *ws, void *stream);
+
+/* ------------------------------------------------------------------ a6 */
+/* One Algorithm 3 parameter update for the full batch: if l1_optim and
+ * stats[MAXE] < tau_m, alpha from Eq. 3-21 on the weight gradients (double),
+ * else alpha = 1; beta = 1 - alpha; gradient of Eq. grad (App. A); Adam; then
+ * the epoch tail of Algorithm 3 (deletion due, Eq. l1_activate, Eq.
+ * add_activate, switch to the L2-only phase with a cosine learning rate at
+ * T^e).  grad holds the raw L2 gradients from serbf_backward and is not
+ * modified.  adam_m / adam_v are 10 x cap.  Writes stats[L1, ALPHA, BETA, BF,
+ * LOSS].  One launch. */
+int serbf_step(serbf_params *prm, const float *grad, float *adam_m, float *adam_v, serbf_state *st_dev,
+               double *stats, const serbf_config *cfg, void *stream);
+
+/* ------------------------------------------------------------------ a7 */
+/* Eq. 3-27: when st->do_prune is set, removes every kernel with |w| < tau_d
+ * (stable order), compacting the parameters and the Adam moments and updating
+ * the device count; clears do_prune.  A no-op launch otherwise. */
+int serbf_prune(serbf_params *prm, float *adam_m, float *adam_v, serbf_state *st_dev,
+                const serbf_config *cfg, void *stream);
+
+/* ------------------------------------------------------------------ a8 */
+/* Algorithm 2 in its top-k form and Eq. 3-24: when st->do_add is set (or
+ * force != 0): candidates are id_all points with |E| > tau_m / 2; the
+ * ceil(topk_frac * |id_all|) largest |E| are kept (ties by ascending binned
+ * index); a candidate survives if no id_all point within add_radius has a
+ * larger |E|; survivors become kernels c = v, w = -E, d = sqrt(ln(|E|/eps)) /
+ * dbar on all axes (dbar = max(|S_raw|, dbar_min)), theta = 0, appended in
+ * selection order.  Adam moments are reset (reading: new kernels start from
+ * zero moments, t = 0).  Sets st->m_added and clears do_add.
+ * S_raw: raw signed distances in binned order. */
+int serbf_add_kernels(const serbf_points *pts, const float *S_raw, const float *err, const uint8_t *mask,
+                      serbf_params *prm, float *adam_m, float *adam_v, serbf_state *st_dev,
+                      const double *stats, const serbf_config *cfg, int force, serbf_workspace *ws,
+                      void *stream);
+
+/* ------------------------------------------------------------------ a9 */
+/* Sec. 3.4.2 coarse-to-fine step: appends the next grid layer (x_new.., t_new,
+ * s_new, n_new points) to the original-order training set (x_all.., t_all,
+ * s_all holding n_old points and capacity for n_old + n_new; may alias the
+ * old arrays), then re-bins the union into perm / xb, yb, zb and gathers t and
+ * S into tb / sb.  Parameters are untouched (training continues from them).
+ * SYNCHRONISES the stream (through serbf_bin_points). */
+int serbf_refine(float *x_all, float *y_all, float *z_all, float *t_all, float *s_all, int64_t n_old,
+                 const float *x_new, const float *y_new, const float *z_new, const float *t_new,
+                 const float *s_new, int64_t n_new, const serbf_grid *grid, uint32_t *perm, float *xb,
+                 float *yb, float *zb, float *tb, float *sb, serbf_workspace *ws, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SERBF_H */

@@ -1,0 +1,275 @@
+// Point binning (the data structure behind the support test of Eq. 3-15):
+// cell keys, a stable LSD radix sort by (key, index), cell ranges, cell and
+// super-cell bounding boxes and 32-point tiles.  Also the Sec. 3.4.2
+// refinement entry point, which re-bins the grown training set.
+#include <math.h>
+
+#include "common.cuh"
+
+using namespace serbf;
+
+namespace {
+
+__global__ void k_keys(const float *x, const float *y, const float *z, int64_t n, serbf_grid g,
+                       uint32_t *keys, uint32_t *vals) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int kx = cell_axis(x[i], g.origin[0], g.h, g.n[0]);
+        int ky = cell_axis(y[i], g.origin[1], g.h, g.n[1]);
+        int kz = cell_axis(z[i], g.origin[2], g.h, g.n[2]);
+        keys[i] = ((uint32_t)kz * (uint32_t)g.n[1] + (uint32_t)ky) * (uint32_t)g.n[0] + (uint32_t)kx;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_radix_hist(const uint32_t *keys, int64_t n, int shift, uint32_t *hist,
+                                                    int64_t nblk) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t start = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortTile / 256; ++r) {
+        int64_t e = start + r * 256 + threadIdx.x;
+        if (e < n) atomicAdd(&h[(keys[e] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: within a block, elements keep their order per digit; blocks
+// are placed in order by the digit-major exclusive scan of the histograms.
+__global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t *kin, const uint32_t *vin, uint32_t *kout,
+                                                       uint32_t *vout, int64_t n, int shift,
+                                                       const uint32_t *hist, int64_t nblk) {
+    __shared__ uint32_t wcnt[8][257];
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t base[256];
+    int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    base[tid] = hist[(int64_t)tid * nblk + blockIdx.x];
+    run[tid] = 0;
+    for (int k = tid; k < 8 * 257; k += 256) (&wcnt[0][0])[k] = 0;
+    __syncthreads();
+    int64_t start = (int64_t)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortTile / 256; ++r) {
+        int64_t e = start + r * 256 + tid;
+        bool valid = e < n;
+        uint32_t key = valid ? kin[e] : 0u, val = valid ? vin[e] : 0u;
+        uint32_t d = valid ? (key >> shift) & 255u : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        uint32_t acc = run[tid];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            uint32_t c = wcnt[w][tid];
+            wcnt[w][tid] = acc;
+            acc += c;
+        }
+        run[tid] = acc;
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = base[d] + wcnt[warp][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        for (int k = tid; k < 8 * 257; k += 256) (&wcnt[0][0])[k] = 0;
+        __syncthreads();
+    }
+}
+
+__global__ void k_apply_perm(const uint32_t *sorted_vals, const float *x, const float *y, const float *z,
+                             int64_t n, uint32_t *perm, float *xb, float *yb, float *zb) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t i = sorted_vals[k];
+        perm[k] = i;
+        xb[k] = x[i];
+        yb[k] = y[i];
+        zb[k] = z[i];
+    }
+}
+
+__global__ void k_zero_u32(uint32_t *a, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        a[k] = 0u;
+}
+
+__global__ void k_count_cells(const uint32_t *keys, int64_t n, uint32_t *cnt) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[keys[k]], 1u);
+}
+
+// One warp per cell: bounding box of the points actually in the cell.
+__global__ void k_cell_boxes(const uint32_t *cell_start, int ncells, const float *xb, const float *yb,
+                             const float *zb, float4 *lo, float4 *hi, uint32_t *tiles) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= ncells) return;
+    uint32_t b = cell_start[warp], e = cell_start[warp + 1];
+    float mnx = INFINITY, mny = INFINITY, mnz = INFINITY, mxx = -INFINITY, mxy = -INFINITY, mxz = -INFINITY;
+    for (uint32_t k = b + lane; k < e; k += 32) {
+        mnx = fminf(mnx, xb[k]);
+        mny = fminf(mny, yb[k]);
+        mnz = fminf(mnz, zb[k]);
+        mxx = fmaxf(mxx, xb[k]);
+        mxy = fmaxf(mxy, yb[k]);
+        mxz = fmaxf(mxz, zb[k]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+        mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+        mnz = fminf(mnz, __shfl_xor_sync(0xffffffffu, mnz, o));
+        mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+        mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+        mxz = fmaxf(mxz, __shfl_xor_sync(0xffffffffu, mxz, o));
+    }
+    if (lane == 0) {
+        lo[warp] = make_float4(mnx, mny, mnz, 0.f);
+        hi[warp] = make_float4(mxx, mxy, mxz, 0.f);
+        tiles[warp] = (e - b + kTile - 1) / kTile;
+    }
+}
+
+__global__ void k_super_boxes(const float4 *clo, const float4 *chi, serbf_grid g, int sf, int nsx, int nsy,
+                              int nsz, float4 *slo, float4 *shi) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsx * nsy * nsz) return;
+    int sx = s % nsx, sy = (s / nsx) % nsy, sz = s / (nsx * nsy);
+    float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f), hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+    for (int kz = sz * sf; kz < min(g.n[2], (sz + 1) * sf); ++kz)
+        for (int ky = sy * sf; ky < min(g.n[1], (sy + 1) * sf); ++ky)
+            for (int kx = sx * sf; kx < min(g.n[0], (sx + 1) * sf); ++kx) {
+                int c = (kz * g.n[1] + ky) * g.n[0] + kx;
+                float4 a = clo[c], b = chi[c];
+                lo.x = fminf(lo.x, a.x);
+                lo.y = fminf(lo.y, a.y);
+                lo.z = fminf(lo.z, a.z);
+                hi.x = fmaxf(hi.x, b.x);
+                hi.y = fmaxf(hi.y, b.y);
+                hi.z = fmaxf(hi.z, b.z);
+            }
+    slo[s] = lo;
+    shi[s] = hi;
+}
+
+__global__ void k_fill_tiles(const uint32_t *cell_start, const uint32_t *tile0, int ncells, uint32_t *tile_cell,
+                             uint32_t *tile_start) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
+        uint32_t t0 = tile0[c], t1 = tile0[c + 1], p0 = cell_start[c];
+        for (uint32_t t = t0; t < t1; ++t) {
+            tile_cell[t] = (uint32_t)c;
+            tile_start[t] = p0 + (t - t0) * kTile;
+        }
+    }
+}
+
+__global__ void k_concat(float *dst, const float *src, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        dst[k] = src[k];
+}
+
+int gsz(int64_t n, int t) {
+    int64_t b = (n + t - 1) / t;
+    if (b < 1) b = 1;
+    if (b > 152 * 64) b = 152 * 64;
+    return (int)b;
+}
+
+}  // namespace
+
+extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, int64_t n, const serbf_grid *grid,
+                                uint32_t *perm, float *xb, float *yb, float *zb, serbf_workspace *ws,
+                                void *stream) {
+    if (!ws || ws->magic != kMagic || !grid || n < 0) return SERBF_EINVAL;
+    if (n > 0 && (!x || !y || !z || !perm || !xb || !yb || !zb)) return SERBF_EINVAL;
+    if (n > ws->sz.max_points) return SERBF_EINVAL;
+    if (!(grid->h > 0.f) || grid->n[0] < 1 || grid->n[1] < 1 || grid->n[2] < 1) return SERBF_EINVAL;
+    int64_t cells = (int64_t)grid->n[0] * grid->n[1] * grid->n[2];
+    if (cells > ws->sz.max_cells) return SERBF_EINVAL;
+    int sf = ws->sz.super_factor;
+    int nsx = (grid->n[0] + sf - 1) / sf, nsy = (grid->n[1] + sf - 1) / sf, nsz = (grid->n[2] + sf - 1) / sf;
+    int64_t nsuper = (int64_t)nsx * nsy * nsz;
+    {
+        // same bound as the carve-up
+        double e = cbrt((double)ws->sz.max_cells);
+        int64_t per = (int64_t)ceil(e / sf) + 1;
+        if (nsuper > per * per * per) return SERBF_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    ws->grid = *grid;
+    ws->ncells = (int32_t)cells;
+    ws->sf = sf;
+    ws->ns[0] = nsx;
+    ws->ns[1] = nsy;
+    ws->ns[2] = nsz;
+    ws->nsuper = (int32_t)nsuper;
+    ws->npoints = n;
+    ws->binned = 0;
+
+    uint32_t *kin = ws->keys0, *vin = ws->vals0, *kout = ws->keys1, *vout = ws->vals1;
+    if (n > 0) {
+        k_keys<<<gsz(n, 256), 256, 0, s>>>(x, y, z, n, *grid, kin, vin);
+        int nbits = 1;
+        while (nbits < 32 && (1ll << nbits) < cells) ++nbits;
+        int64_t nblk = (n + kSortTile - 1) / kSortTile;
+        for (int shift = 0; shift < nbits; shift += 8) {
+            k_radix_hist<<<(unsigned)nblk, 256, 0, s>>>(kin, n, shift, ws->hist, nblk);
+            int rc = launch_exscan_u32(ws->hist, 256 * nblk, s);
+            if (rc) return rc;
+            k_radix_scatter<<<(unsigned)nblk, 256, 0, s>>>(kin, vin, kout, vout, n, shift, ws->hist, nblk);
+            uint32_t *t = kin;
+            kin = kout;
+            kout = t;
+            t = vin;
+            vin = vout;
+            vout = t;
+        }
+        k_apply_perm<<<gsz(n, 256), 256, 0, s>>>(vin, x, y, z, n, perm, xb, yb, zb);
+    }
+    k_zero_u32<<<gsz(cells + 1, 256), 256, 0, s>>>(ws->cell_start, cells + 1);
+    if (n > 0) k_count_cells<<<gsz(n, 256), 256, 0, s>>>(kin, n, ws->cell_start);
+    int rc = launch_exscan_u32(ws->cell_start, cells, s);
+    if (rc) return rc;
+    k_cell_boxes<<<(unsigned)((cells * 32 + 255) / 256), 256, 0, s>>>(ws->cell_start, (int)cells, xb, yb, zb,
+                                                                      ws->cell_lo, ws->cell_hi, ws->cell_tile0);
+    k_super_boxes<<<(unsigned)((nsuper + 127) / 128), 128, 0, s>>>(ws->cell_lo, ws->cell_hi, *grid, sf, nsx, nsy,
+                                                                   nsz, ws->sup_lo, ws->sup_hi);
+    rc = launch_exscan_u32(ws->cell_tile0, cells, s);
+    if (rc) return rc;
+    k_fill_tiles<<<gsz(cells, 256), 256, 0, s>>>(ws->cell_start, ws->cell_tile0, (int)cells, ws->tile_cell,
+                                                 ws->tile_start);
+    SERBF_CHECK_LAUNCH();
+    uint32_t nt = 0;
+    if (cudaMemcpyAsync(&nt, ws->cell_tile0 + cells, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SERBF_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SERBF_ECUDA;
+    if ((int64_t)nt > ws->max_tiles) return SERBF_ECAPACITY;
+    ws->ntiles = nt;
+    ws->binned = 1;
+    return SERBF_OK;
+}
+
+extern "C" int serbf_refine(float *x_all, float *y_all, float *z_all, float *t_all, float *s_all, int64_t n_old,
+                            const float *x_new, const float *y_new, const float *z_new, const float *t_new,
+                            const float *s_new, int64_t n_new, const serbf_grid *grid, uint32_t *perm, float *xb,
+                            float *yb, float *zb, float *tb, float *sb, serbf_workspace *ws, void *stream) {
+    if (!ws || ws->magic != kMagic || n_old < 0 || n_new < 0) return SERBF_EINVAL;
+    if (!x_all || !y_all || !z_all || !t_all || !s_all || !tb || !sb) return SERBF_EINVAL;
+    if (n_new > 0 && (!x_new || !y_new || !z_new || !t_new || !s_new)) return SERBF_EINVAL;
+    int64_t n = n_old + n_new;
+    if (n > ws->sz.max_points) return SERBF_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_new > 0) {
+        k_concat<<<gsz(n_new, 256), 256, 0, s>>>(x_all + n_old, x_new, n_new);
+        k_concat<<<gsz(n_new, 256), 256, 0, s>>>(y_all + n_old, y_new, n_new);
+        k_concat<<<gsz(n_new, 256), 256, 0, s>>>(z_all + n_old, z_new, n_new);
+        k_concat<<<gsz(n_new, 256), 256, 0, s>>>(t_all + n_old, t_new, n_new);
+        k_concat<<<gsz(n_new, 256), 256, 0, s>>>(s_all + n_old, s_new, n_new);
+        SERBF_CHECK_LAUNCH();
+    }
+    int rc = serbf_bin_points(x_all, y_all, z_all, n, grid, perm, xb, yb, zb, ws, stream);
+    if (rc) return rc;
+    rc = serbf_gather(t_all, perm, tb, n, stream);
+    if (rc) return rc;
+    return serbf_gather(s_all, perm, sb, n, stream);
+}

@@ -1,0 +1,180 @@
+"""Device-resident fitting problem: the buffers of one SDF field and the calls
+of one optimisation epoch (Algorithm 3, full batch).
+
+PyTorch is only used for device memory and the stream; every step of the
+path runs in libserbf.so.  Point arrays are kept twice: in the caller's order
+(for refinement) and in binned order (for the kernels).
+"""
+import math
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def grid_for(spacing, lo=-1.0, hi=1.0, points_per_cell=4):
+    """Binning grid whose cells hold points_per_cell^3 points of a vertex grid
+    with the given spacing (cell faces fall half-way between grid planes)."""
+    h = points_per_cell * spacing
+    origin = lo - 0.5 * spacing
+    n = int(math.ceil((hi - lo + spacing) / h - 1e-6))
+    g = N.Grid()
+    for k in range(3):
+        g.origin[k] = origin
+        g.n[k] = n
+    g.h = h
+    return g
+
+
+class Problem:
+    """One field: training points, targets, kernels, optimiser state and scratch."""
+
+    def __init__(self, x, y, z, S, P, m, spacing, cfg=None, cap=None, max_points=None, t=None,
+                 cell_cap=2048, super_cap=8192, super_factor=4, device="cuda"):
+        dev = torch.device(device)
+        self.dev = dev
+        self.cfg = cfg if cfg is not None else N.config_default()
+        if self.cfg.add_radius == 0.0:
+            self.cfg.add_radius = 2.0 * spacing
+        if self.cfg.dbar_min == 0.0:
+            self.cfg.dbar_min = 0.5 * spacing
+        n = int(len(x))
+        self.cap = int(cap if cap is not None else max(P.shape[1], m))
+        self.max_points = int(max_points if max_points is not None else n)
+        self.spacing = spacing
+        self.grid = grid_for(spacing)
+        f32 = dict(dtype=torch.float32, device=dev)
+        self.x_all = torch.zeros(self.max_points, **f32)
+        self.y_all = torch.zeros(self.max_points, **f32)
+        self.z_all = torch.zeros(self.max_points, **f32)
+        self.t_all = torch.zeros(self.max_points, **f32)
+        self.s_all = torch.zeros(self.max_points, **f32)
+        self.n = n
+        self.x_all[:n] = torch.as_tensor(np.asarray(x, np.float32), device=dev)
+        self.y_all[:n] = torch.as_tensor(np.asarray(y, np.float32), device=dev)
+        self.z_all[:n] = torch.as_tensor(np.asarray(z, np.float32), device=dev)
+        self.s_all[:n] = torch.as_tensor(np.asarray(S, np.float32), device=dev)
+        self.mh = torch.zeros(2, dtype=torch.float64, device=dev)
+        self.perm = torch.zeros(self.max_points, dtype=torch.int32, device=dev)
+        self.xb = torch.zeros(self.max_points, **f32)
+        self.yb = torch.zeros(self.max_points, **f32)
+        self.zb = torch.zeros(self.max_points, **f32)
+        self.tb = torch.zeros(self.max_points, **f32)
+        self.sb = torch.zeros(self.max_points, **f32)
+        self.psi = torch.zeros(self.max_points, **f32)
+        self.err = torch.zeros(self.max_points, **f32)
+        self.mask = torch.zeros(self.max_points, dtype=torch.uint8, device=dev)
+        Pp = np.zeros((10, self.cap), np.float32)
+        Pp[:, :m] = np.asarray(P, np.float32)[:, :m]
+        self.p = torch.as_tensor(Pp, device=dev).contiguous()
+        self.m_dev = torch.tensor([m], dtype=torch.int32, device=dev)
+        self.adam_m = torch.zeros(10, self.cap, **f32)
+        self.adam_v = torch.zeros(10, self.cap, **f32)
+        self.grad = torch.zeros(10, self.cap, **f32)
+        self.state = torch.zeros(N.STATE_BYTES, dtype=torch.uint8, device=dev)
+        self.stats = torch.zeros(N.NSTATS, dtype=torch.float64, device=dev)
+        ncell = self.grid.n[0] * self.grid.n[1] * self.grid.n[2]
+        self.sizes = N.WsSizes(self.max_points, self.cap, ncell, cell_cap, super_cap, super_factor, 0)
+        nbytes = N.serbf_workspace_bytes(self.sizes)
+        self.ws_dev = torch.zeros(nbytes + 256, dtype=torch.uint8, device=dev)
+        off = (-self.ws_dev.data_ptr()) % 256
+        self.ws_view = self.ws_dev[off:off + nbytes]
+        self.ws = N.workspace_struct()
+        N.serbf_workspace_init(self.ws, self.ws_view, self.sizes)
+        N.serbf_state_init(self.state, self.cfg)
+        if t is None:
+            N.serbf_normalize_sdf(self.s_all[:n], self.t_all[:n], self.mh, self.ws)
+        else:
+            self.t_all[:n] = torch.as_tensor(np.asarray(t, np.float32), device=dev)
+        self.bin()
+
+    # ------------------------------------------------------------ structure
+    def bin(self):
+        n = self.n
+        N.serbf_bin_points(self.x_all[:n], self.y_all[:n], self.z_all[:n], self.grid, self.perm[:n],
+                           self.xb[:n], self.yb[:n], self.zb[:n], self.ws)
+        N.serbf_gather(self.t_all, self.perm[:n], self.tb, n)
+        N.serbf_gather(self.s_all, self.perm[:n], self.sb, n)
+
+    def refine(self, x, y, z, S, t, spacing=None):
+        """Sec. 3.4.2: append the next layer (its targets t from the global Eq. 3-10 map)."""
+        n_new = int(len(x))
+        if spacing is not None and spacing < self.spacing:
+            self.spacing = spacing
+            g = grid_for(spacing)
+            ncell = g.n[0] * g.n[1] * g.n[2]
+            if ncell > self.sizes.max_cells:
+                raise ValueError("refined grid needs a workspace with max_cells >= %d" % ncell)
+            self.grid = g
+        dev = self.dev
+        tt = lambda a: torch.as_tensor(np.asarray(a, np.float32), device=dev)
+        N.serbf_refine(self.x_all, self.y_all, self.z_all, self.t_all, self.s_all, self.n, tt(x), tt(y), tt(z),
+                       tt(t), tt(S), self.grid, self.perm, self.xb, self.yb, self.zb, self.tb, self.sb, self.ws)
+        self.n += n_new
+
+    @property
+    def pts(self):
+        n = self.n
+        return N.points(self.xb[:n], self.yb[:n], self.zb[:n], self.tb[:n], n)
+
+    @property
+    def prm(self):
+        return N.params(self.p, self.m_dev)
+
+    # ------------------------------------------------------------ hot path
+    def build_neighbors(self, kmajor=None, pmajor=None):
+        return N.serbf_build_neighbors(self.pts, self.prm, self.cfg, self.ws, kmajor, pmajor)
+
+    def forward(self):
+        n = self.n
+        N.serbf_forward(self.pts, self.prm, self.cfg, self.psi[:n], self.err[:n], self.mask[:n], self.stats,
+                        self.ws)
+
+    def backward(self, err=None):
+        n = self.n
+        N.serbf_backward(self.pts, self.prm, self.cfg, self.err[:n] if err is None else err, self.grad,
+                         self.stats, self.ws)
+
+    def step(self):
+        N.serbf_step(self.prm, self.grad, self.adam_m, self.adam_v, self.state, self.stats, self.cfg)
+
+    def prune(self):
+        N.serbf_prune(self.prm, self.adam_m, self.adam_v, self.state, self.cfg)
+
+    def add(self, force=False):
+        n = self.n
+        N.serbf_add_kernels(self.pts, self.sb[:n], self.err[:n], self.mask[:n], self.prm, self.adam_m,
+                            self.adam_v, self.state, self.stats, self.cfg, self.ws, force=force)
+
+    def epoch(self):
+        """One Algorithm 3 epoch with the full batch: no host synchronisation."""
+        self.build_neighbors()
+        self.forward()
+        self.backward()
+        self.step()
+        self.prune()
+        self.add()
+
+    # ------------------------------------------------------------ host views
+    def status(self, clear=False):
+        return N.serbf_status(self.ws, clear=clear)
+
+    def m(self):
+        return int(self.m_dev.item())
+
+    def params_host(self):
+        return self.p[:, :self.m()].cpu().numpy()
+
+    def state_host(self):
+        st = N.State()
+        b = self.state.cpu().numpy().tobytes()
+        import ctypes
+        ctypes.memmove(ctypes.addressof(st), b, len(b))
+        return st
+
+    def binned_host(self):
+        n = self.n
+        return dict(x=self.xb[:n].cpu().numpy(), y=self.yb[:n].cpu().numpy(), z=self.zb[:n].cpu().numpy(),
+                    t=self.tb[:n].cpu().numpy(), S=self.sb[:n].cpu().numpy(),
+                    perm=self.perm[:n].cpu().numpy().astype(np.int64))

@@ -1,0 +1,406 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Bars: bit-exact binning, neighbour lists and selected indices;
+forward max |error| <= 1e-5 * max|t|; gradient relative L2 <= 1e-4 per
+parameter group; Adam/alpha to float rounding."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import host_params, problem, rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+FWD_TOL = 1e-5   # forward: max |Psi_gpu - Psi_oracle| <= FWD_TOL * max |t|
+GRAD_TOL = 1e-4  # adjoint: relative L2 error per parameter group
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = torch_cuda()
+    from paper_2505_02350_gb300 import build
+    build.build()
+    return t
+
+
+@pytest.fixture(scope="module")
+def c1(torch):
+    return problem("c1")
+
+
+@pytest.fixture(scope="module")
+def c2(torch):
+    return problem("c2", layers=[32, 64])
+
+
+def _oracle_inputs(pb):
+    h = pb.binned_host()
+    return h, host_params(pb)
+
+
+# ------------------------------------------------------------------ a1, a2
+def test_normalize_matches_oracle(torch, orc):
+    from paper_2505_02350_gb300 import _native as N
+    cfg, lay, _ = synth.workload("c2", layers=[32, 64])
+    S = np.concatenate([l[3] for l in lay])
+    pb = problem("c1")
+    St = torch.as_tensor(S, device="cuda")
+    t = torch.zeros_like(St)
+    mh = torch.zeros(2, dtype=torch.float64, device="cuda")
+    N.serbf_normalize_sdf(St, t, mh, pb.ws)
+    t_or, m, h = orc.normalize(S)
+    assert mh[0].item() == m and mh[1].item() == pytest.approx(h, rel=1e-15)
+    np.testing.assert_allclose(t.cpu().numpy(), t_or.astype(np.float32), rtol=2 ** -23, atol=0)
+
+
+@pytest.mark.parametrize("which", ["c1", "c2"])
+def test_binning_bitexact(torch, orc, which, c1, c2):
+    pb = c1 if which == "c1" else c2
+    n = pb.n
+    g = pb.grid
+    perm_or = orc.bin_points(pb.x_all[:n].cpu().numpy(), pb.y_all[:n].cpu().numpy(), pb.z_all[:n].cpu().numpy(),
+                             tuple(g.origin), g.h, tuple(g.n))
+    np.testing.assert_array_equal(pb.perm[:n].cpu().numpy().astype(np.uint32), perm_or)
+    np.testing.assert_array_equal(pb.xb[:n].cpu().numpy(), pb.x_all[:n].cpu().numpy()[perm_or])
+
+
+def test_binning_random_cloud_with_clamped_keys(torch, orc):
+    from paper_2505_02350_gb300 import field
+    g = np.random.default_rng(21)
+    n = 20011  # ragged: not a multiple of the tile or sort block
+    x, y, z = (g.uniform(-1.3, 1.3, n).astype(np.float32) for _ in range(3))
+    S = (np.sqrt(x * x + y * y + z * z) - 0.5).astype(np.float32)
+    P = synth.init_kernels(5, 40, rotate=True, length_range=(0.05, 0.2))
+    pb = field.Problem(x, y, z, S, P, 40, spacing=0.05)
+    gr = pb.grid
+    perm_or = orc.bin_points(x, y, z, tuple(gr.origin), gr.h, tuple(gr.n))
+    np.testing.assert_array_equal(pb.perm[:n].cpu().numpy().astype(np.uint32), perm_or)
+
+
+# ------------------------------------------------------------------ a3
+def _csr_check(torch, orc, pb):
+    from paper_2505_02350_gb300 import _native as N
+    h, P = _oracle_inputs(pb)
+    m, n = pb.m(), pb.n
+    krow_o, kcol_o, prow_o, pcol_o = orc.neighbors(h["x"], h["y"], h["z"], P, m)
+    tot = int(krow_o[-1])
+    kr = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+    kc = torch.zeros(max(tot, 1), dtype=torch.int32, device="cuda")
+    pr = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    pc = torch.zeros(max(tot, 1), dtype=torch.int32, device="cuda")
+    rc, npairs = pb.build_neighbors(N.csr(kr, kc), N.csr(pr, pc))
+    assert rc == N.SERBF_OK and npairs == tot
+    np.testing.assert_array_equal(kr.cpu().numpy(), krow_o)
+    np.testing.assert_array_equal(kc[:tot].cpu().numpy().astype(np.uint32), kcol_o)
+    np.testing.assert_array_equal(pr.cpu().numpy(), prow_o)
+    np.testing.assert_array_equal(pc[:tot].cpu().numpy().astype(np.uint32), pcol_o)
+    assert pb.status()[0] == 0
+    return tot
+
+
+def test_csr_bitexact_c1(torch, orc, c1):
+    assert _csr_check(torch, orc, c1) > 100000
+
+
+def test_csr_bitexact_c2_union(torch, orc, c2):
+    assert _csr_check(torch, orc, c2) > 1000000
+
+
+def test_csr_capacity_error_reports_count(torch, c1):
+    from paper_2505_02350_gb300 import _native as N
+    m, n = c1.m(), c1.n
+    kr = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+    kc = torch.zeros(10, dtype=torch.int32, device="cuda")
+    rc, npairs = c1.build_neighbors(N.csr(kr, kc), None)
+    assert rc == N.SERBF_ECAPACITY and npairs == int(kr[-1].item()) > 10
+
+
+# ------------------------------------------------------------------ a4
+def _forward_check(torch, orc, pb):
+    pb.build_neighbors()
+    pb.forward()
+    torch.cuda.synchronize()
+    h, P = _oracle_inputs(pb)
+    m, n = pb.m(), pb.n
+    psi_o, err_o, mask_o, st_o = orc.forward(h["x"], h["y"], h["z"], h["t"], P, m)
+    psi = pb.psi[:n].cpu().numpy()
+    mask = pb.mask[:n].cpu().numpy()
+    err = pb.err[:n].cpu().numpy()
+    tmax = float(np.abs(h["t"]).max())
+    assert np.abs(psi - psi_o).max() <= FWD_TOL * tmax
+    st = pb.stats.cpu().numpy()
+    assert st[4] == st_o[4]  # pairs: the same neighbour lists
+    same = mask == mask_o
+    flips = int((~same).sum())
+    assert flips <= max(3, n // 10000), flips
+    assert np.abs(err[same] - err_o[same]).max() <= FWD_TOL * tmax
+    # loss terms on the GPU's own mask
+    sel = mask.astype(bool)
+    l2_ref = float(np.sum((psi_o[sel] - h["t"][sel].astype(np.float64)) ** 2))
+    assert st[0] == pytest.approx(l2_ref, rel=1e-4, abs=1e-8)
+    assert st[3] == sel.sum()
+    assert st[2] == pytest.approx(float(np.abs(err[sel]).max()) if sel.any() else 0.0, rel=1e-6)
+    return psi, err, mask
+
+
+def test_forward_parity_c1(torch, orc, c1):
+    _forward_check(torch, orc, c1)
+
+
+def test_forward_parity_c2(torch, orc, c2):
+    _forward_check(torch, orc, c2)
+
+
+def test_forward_is_deterministic(torch, c2):
+    c2.build_neighbors()
+    c2.forward()
+    a = c2.psi[:c2.n].clone()
+    s1 = c2.stats.clone()
+    c2.forward()
+    assert torch.equal(a, c2.psi[:c2.n]) and torch.equal(s1[:5], c2.stats[:5])
+
+
+# ------------------------------------------------------------------ a5
+def _backward_check(torch, orc, pb, kahan=False):
+    pb.cfg.kahan = int(kahan)
+    pb.build_neighbors()
+    pb.forward()
+    pb.backward()
+    torch.cuda.synchronize()
+    h, P = _oracle_inputs(pb)
+    m, n = pb.m(), pb.n
+    E = pb.err[:n].cpu().numpy().astype(np.float64)
+    g_o, np_o = orc.backward(h["x"], h["y"], h["z"], E, P, m)
+    g = pb.grad[:, :m].cpu().numpy()
+    assert pb.stats[5].item() == np_o
+    names = ["c", "d", "theta", "w"]
+    groups = [slice(0, 3), slice(3, 6), slice(6, 9), slice(9, 10)]
+    for nm, sl in zip(names, groups):
+        e = rel_l2(g[sl], g_o[sl])
+        assert e <= GRAD_TOL, (nm, e)
+    pb.cfg.kahan = 0
+    return g, g_o
+
+
+def test_backward_parity_c1(torch, orc, c1):
+    _backward_check(torch, orc, c1)
+
+
+def test_backward_parity_c2(torch, orc, c2):
+    _backward_check(torch, orc, c2)
+
+
+def test_backward_parity_c2_kahan(torch, orc, c2):
+    _backward_check(torch, orc, c2, kahan=True)
+
+
+def test_backward_arbitrary_upstream_weights(torch, orc, c1):
+    """err need not come from the forward: any per-point weights (zeros skipped)."""
+    n, m = c1.n, c1.m()
+    g = np.random.default_rng(3)
+    w = g.normal(0, 1, n).astype(np.float32)
+    w[g.uniform(size=n) < 0.5] = 0.0
+    c1.build_neighbors()
+    c1.backward(torch.as_tensor(w, device="cuda"))
+    h, P = _oracle_inputs(c1)
+    g_o, np_o = orc.backward(h["x"], h["y"], h["z"], w.astype(np.float64), P, m)
+    assert c1.stats[5].item() == np_o
+    assert rel_l2(c1.grad[:, :m].cpu().numpy(), g_o) <= GRAD_TOL
+
+
+# ------------------------------------------------------------------ a6
+def _set_state(pb, **fields):
+    from paper_2505_02350_gb300 import _native as N
+    import ctypes
+    st = pb.state_host()
+    for k, v in fields.items():
+        setattr(st, k, v)
+    raw = np.frombuffer(ctypes.string_at(ctypes.addressof(st), N.STATE_BYTES), np.uint8).copy()
+    pb.state.copy_(pb.state.new_tensor(raw))
+
+
+@pytest.mark.parametrize("l1", [False, True])
+def test_step_parity(torch, orc, l1):
+    pb = problem("c1")
+    pb.build_neighbors()
+    pb.forward()
+    pb.backward()
+    if l1:
+        _set_state(pb, l1_optim=1)
+        pb.stats[2] = 0.0  # pass the max-error gate
+    torch.cuda.synchronize()
+    m, cap = pb.m(), pb.cap
+    P0 = pb.p.cpu().numpy().astype(np.float64)
+    grad = pb.grad[:, :m].cpu().numpy().astype(np.float64)
+    st = pb.stats.cpu().numpy()
+    ocfg = orc.default_cfg()
+    ost = orc.state_init(ocfg)
+    ost.l1_optim = int(l1)
+    mo = np.zeros((10, cap))
+    v = np.zeros((10, cap))
+    Po = P0.copy()
+    orc.step(Po, m, grad, mo, v, st[0], st[2], ocfg, ost)
+    pb.step()
+    torch.cuda.synchronize()
+    P1 = pb.p.cpu().numpy().astype(np.float64)
+    s = pb.state_host()
+    assert s.alpha == pytest.approx(ost.alpha, rel=1e-12, abs=1e-15)
+    if l1:
+        assert 0.0 <= s.alpha < 1.0
+    np.testing.assert_allclose(P1[:, :m], Po[:, :m], rtol=2e-6, atol=1e-7)
+    np.testing.assert_allclose(pb.adam_m[:, :m].cpu().numpy(), mo[:, :m], rtol=1e-5, atol=1e-9)
+    assert (s.epoch, s.l1_optim, s.adam_t, s.do_prune, s.do_add) == (ost.epoch, ost.l1_optim, ost.adam_t,
+                                                                     ost.do_prune, ost.do_add)
+    assert pb.stats[8].item() == np.sum(np.abs(P1[9, :m]) >= 0.01)
+
+
+def test_gate_sequence_matches_oracle(torch, orc):
+    """Run the device state machine for many epochs on fixed gradients and a
+    scripted L2 sequence; every flag must follow the oracle's Algorithm 3."""
+    pb = problem("c1")
+    m, cap = pb.m(), pb.cap
+    pb.cfg.T_e = 70
+    pb.cfg.M_e = 90
+    ocfg = orc.default_cfg(T_e=70, M_e=90)
+    ost = orc.state_init(ocfg)
+    from paper_2505_02350_gb300 import _native as N
+    N.serbf_state_init(pb.state, pb.cfg)
+    pb.grad.zero_()
+    Po = pb.p.cpu().numpy().astype(np.float64)
+    mo = np.zeros((10, cap))
+    v = np.zeros((10, cap))
+    for e in range(85):
+        l2 = 5.0 if e > 4 else 100.0 - e
+        pb.stats[0] = l2
+        pb.stats[2] = 0.5
+        pb.step()
+        orc.step(Po, m, np.zeros((10, m)), mo, v, l2, 0.5, ocfg, ost)
+        s = pb.state_host()
+        assert (s.epoch, s.l1_optim, s.phase2, s.do_prune, s.do_add) == (ost.epoch, ost.l1_optim, ost.phase2,
+                                                                         ost.do_prune, ost.do_add), e
+        assert s.lr == pytest.approx(ost.lr, rel=1e-12)
+        _set_state(pb, do_add=0, do_prune=0)
+        ost.do_add = 0
+        ost.do_prune = 0
+
+
+# ------------------------------------------------------------------ a7
+def test_prune_parity(torch, orc):
+    pb = problem("c1")
+    g = np.random.default_rng(9)
+    m = pb.m()
+    w = pb.p[9, :m].cpu().numpy()
+    w[g.uniform(size=m) < 0.4] = 0.004
+    pb.p[9, :m] = torch.as_tensor(w, device="cuda")
+    pb.adam_m[:, :m] = torch.as_tensor(g.normal(size=(10, m)).astype(np.float32), device="cuda")
+    Po = pb.p.cpu().numpy().astype(np.float64)
+    mo = pb.adam_m.cpu().numpy().astype(np.float64)
+    vo = pb.adam_v.cpu().numpy().astype(np.float64)
+    m2 = orc.prune(Po, m, 0.01, mo=mo, v=vo)
+    _set_state(pb, do_prune=1)
+    pb.prune()
+    assert pb.m() == m2 < m
+    np.testing.assert_array_equal(pb.p[:, :m2].cpu().numpy(), Po[:, :m2].astype(np.float32))
+    np.testing.assert_array_equal(pb.adam_m[:, :m2].cpu().numpy(), mo[:, :m2].astype(np.float32))
+    assert pb.state_host().do_prune == 0 and pb.state_host().m_pruned == m - m2
+
+
+# ------------------------------------------------------------------ a8
+@pytest.mark.parametrize("frac", [0.01, 0.0])
+def test_add_parity(torch, orc, frac):
+    pb = problem("c2", layers=[32], cap=2048)
+    pb.cfg.topk_frac = frac
+    pb.build_neighbors()
+    pb.forward()
+    torch.cuda.synchronize()
+    n, m = pb.n, pb.m()
+    h = pb.binned_host()
+    E = pb.err[:n].cpu().numpy()
+    mask = pb.mask[:n].cpu().numpy()
+    cnt = int(mask.sum())
+    k = math.ceil(frac * cnt) if frac > 0 else 8192
+    cand = orc.select_topk(E, mask, 0.01, k)
+    r2 = np.float32(pb.cfg.add_radius * pb.cfg.add_radius)
+    ext = orc.local_max(h["x"], h["y"], h["z"], E, mask, cand, r2)
+    assert len(ext) > 0
+    pb.add(force=True)
+    torch.cuda.synchronize()
+    m2 = pb.m()
+    assert m2 == m + len(ext)
+    P = pb.p[:, m:m2].cpu().numpy()
+    for q, i in enumerate(ext):
+        dbar = max(abs(float(h["S"][i])), pb.cfg.dbar_min)
+        ref = orc.new_kernel((h["x"][i], h["y"][i], h["z"][i]), E[i], dbar)
+        np.testing.assert_allclose(P[:, q], ref.astype(np.float32), rtol=1e-6, atol=0)
+    s = pb.state_host()
+    assert s.m_added == len(ext) and s.adam_t == 0
+    assert float(pb.adam_v[:, :m2].abs().max().item()) == 0.0
+
+
+# ------------------------------------------------------------------ a9
+def test_refine_appends_layer_and_rebins(torch, orc):
+    cfg, lay, P = synth.workload("c2", layers=[32, 64])
+    S_all = np.concatenate([lay[0][3], lay[1][3]])
+    t_all, _, _ = orc.normalize(S_all)
+    t32 = t_all[:lay[0][0].size].astype(np.float32)
+    t64 = t_all[lay[0][0].size:].astype(np.float32)
+    from paper_2505_02350_gb300 import field
+    n_all = S_all.size
+    pb = field.Problem(lay[0][0], lay[0][1], lay[0][2], lay[0][3], P, cfg["m"], synth.spacing(32),
+                       max_points=n_all, t=t32, cap=cfg["m"])
+    ref = problem("c2", layers=[32, 64])
+    pb.refine(lay[1][0], lay[1][1], lay[1][2], lay[1][3], t64, spacing=synth.spacing(64))
+    torch.cuda.synchronize()
+    assert pb.n == n_all
+    np.testing.assert_array_equal(pb.perm[:n_all].cpu().numpy(), ref.perm[:n_all].cpu().numpy())
+    np.testing.assert_allclose(pb.tb[:n_all].cpu().numpy(), ref.tb[:n_all].cpu().numpy(), rtol=2 ** -23, atol=0)
+    pb.build_neighbors()
+    pb.forward()
+    ref.build_neighbors()
+    ref.forward()
+    assert torch.equal(pb.psi[:n_all], ref.psi[:n_all])
+
+
+# ------------------------------------------------------------------ edge cases
+def test_no_kernels(torch):
+    pb = problem("c1")
+    pb.m_dev.fill_(0)
+    pb.epoch()
+    torch.cuda.synchronize()
+    assert float(pb.psi[:pb.n].abs().max()) == 0.0
+    assert pb.stats[4].item() == 0 and pb.stats[5].item() == 0
+
+
+def test_tiny_ragged_problem(torch, orc):
+    from paper_2505_02350_gb300 import field
+    x, y, z = synth.grid(7)
+    S = synth.sdf_sphere(x, y, z)
+    P = synth.init_kernels(3, 5, rotate=True, length_range=(0.2, 0.5))
+    pb = field.Problem(x, y, z, S, P, 5, spacing=synth.spacing(7))
+    _csr_check(torch, orc, pb)
+    _forward_check(torch, orc, pb)
+    _backward_check(torch, orc, pb)
+
+
+def test_full_size_c3_sampled(torch, orc):
+    """128^3, 4096 kernels, launch as in the bench: sampled outputs vs the oracle."""
+    pb = problem("c3")
+    pb.build_neighbors()
+    pb.forward()
+    pb.backward()
+    torch.cuda.synchronize()
+    assert pb.status()[0] == 0
+    h, P = _oracle_inputs(pb)
+    n, m = pb.n, pb.m()
+    g = np.random.default_rng(0)
+    idx = np.sort(g.choice(n, 3000, replace=False))
+    psi_o, _, _, _ = orc.forward(h["x"][idx], h["y"][idx], h["z"][idx], h["t"][idx], P, m)
+    psi = pb.psi[:n].cpu().numpy()[idx]
+    assert np.abs(psi - psi_o).max() <= FWD_TOL * float(np.abs(h["t"]).max())
+    ks = np.sort(g.choice(m, 48, replace=False))
+    E = pb.err[:n].cpu().numpy().astype(np.float64)
+    g_o, _ = orc.backward(h["x"], h["y"], h["z"], E, P[:, ks].copy(), len(ks))
+    gk = pb.grad[:, ks].cpu().numpy()
+    for sl in (slice(0, 3), slice(3, 6), slice(6, 9), slice(9, 10)):
+        assert rel_l2(gk[sl], g_o[sl]) <= GRAD_TOL
