@@ -54,9 +54,7 @@ extern "C" {
 
 /* device status flags (bitmask) reported by serbf_status */
 #define SERBF_FLAG_SUPER_LIST 1   /* a super-cell candidate list exceeded super_cap */
-#define SERBF_FLAG_CELL_LIST 2    /* a cell candidate list exceeded cell_cap */
 #define SERBF_FLAG_ADD_CAPACITY 4 /* addition truncated at the parameter capacity */
-#define SERBF_FLAG_ROWS 8         /* a kernel's support spans more cell rows than supported */
 
 /* indices into the double stats[SERBF_NSTATS] device array */
 #define SERBF_STAT_L2 0        /* sum over id_all of E_i^2                 (Eq. 3-19) */
@@ -106,8 +104,8 @@ typedef struct {
     int32_t reserved[2];
     double lr;        /* learning rate of the next epoch */
     double alpha, beta;
-    double l2_hist[64];  /* last k_l2 values of L2, oldest first */
-    int32_t bf_hist[256]; /* last k_l1 values of b_f, oldest first */
+    double l2_hist[64];  /* L2 of epoch e at index (e - 1) mod k_l2 */
+    int32_t bf_hist[256]; /* b_f of epoch e at index (e - 1) mod k_l1 */
 } serbf_state;
 
 typedef struct {
@@ -138,7 +136,7 @@ typedef struct {
     int64_t max_points;   /* training-set capacity */
     int32_t max_kernels;  /* parameter capacity (== serbf_params.cap) */
     int32_t max_cells;    /* >= n[0]*n[1]*n[2] of every grid used */
-    int32_t cell_cap;     /* candidate kernels per cell list */
+    int32_t reserved0;    /* must be 0 */
     int32_t super_cap;    /* candidate kernels per super-cell list */
     int32_t super_factor; /* cells per super-cell edge (1..16) */
     int32_t reserved;
@@ -167,8 +165,8 @@ int serbf_workspace_bytes(const serbf_ws_sizes *sz, size_t *bytes);
 int serbf_workspace_init(serbf_workspace *ws, void *dev, size_t bytes, const serbf_ws_sizes *sz);
 
 /* Reads and optionally clears the device status flags (synchronises `stream`).
- * needed[0..3]: largest super list, cell list, kernel rows and requested
- * additions seen since the last clear.  Returns SERBF_ECAPACITY when a flag is
+ * needed[0] = largest super-cell list, needed[3] = kernel count an addition
+ * asked for, both since the last clear.  Returns SERBF_ECAPACITY when a flag is
  * set, SERBF_OK otherwise. */
 int serbf_status(serbf_workspace *ws, int32_t *flags, int64_t needed[4], int clear, void *stream);
 
@@ -186,11 +184,14 @@ int serbf_normalize_sdf(const float *S, float *t, int64_t n, double *mh_dev, ser
 /* ------------------------------------------------------------------ a2 */
 /* Cell binning of the training points (the neighbour structure that serves
  * the support test of Eq. 3-15; the paper leaves its data structure open).
- * Cell key per axis k = clamp(floor(fl(fl(x - origin) / h)), 0, n - 1), linear
- * key (kz * ny + ky) * nx + kx; points are radix-sorted by (key, index).
- * Writes perm (binned -> original index) and the binned coordinates, and
- * records cell ranges, cell/super-cell bounding boxes and 32-point tiles in
- * the workspace.  SYNCHRONISES the stream once (reads the tile count).
+ * Cell index per axis k = clamp(floor(fl(fl(x - origin) / h)), 0, n - 1);
+ * cells are grouped into super cells of sf^3 (sf = super_factor) and the key
+ * is super-major: ((sk_z * ns_y + sk_y) * ns_x + sk_x) * sf^3 +
+ * (l_z * sf + l_y) * sf + l_x with sk = k / sf, l = k % sf, ns = ceil(n / sf).
+ * Points are radix-sorted by (key, index).  Writes perm (binned -> original
+ * index) and the binned coordinates, and records cell ranges, 32-point tiles
+ * (never straddling a super cell) and tile / super-cell bounding boxes in the
+ * workspace.  SYNCHRONISES the stream once (reads the tile count).
  * EINVAL: n > max_points, grid cells > max_cells, non-positive h. */
 int serbf_bin_points(const float *x, const float *y, const float *z, int64_t n, const serbf_grid *grid,
                      uint32_t *perm, float *xb, float *yb, float *zb, serbf_workspace *ws, void *stream);

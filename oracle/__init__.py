@@ -53,9 +53,9 @@ def lib():
         L.oracle_erbf.argtypes = [C.c_double, C.c_double, C.c_double, f64p, C.c_int32, C.c_int32]
         L.oracle_normalize.argtypes = [f32p, C.c_int64, f64p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.oracle_cell_keys.argtypes = [f32p, f32p, f32p, C.c_int64, C.c_float, C.c_float, C.c_float,
-                                       C.c_float, C.c_int32, C.c_int32, C.c_int32, u32p]
+                                       C.c_float, C.c_int32, C.c_int32, C.c_int32, C.c_int32, u32p]
         L.oracle_bin.argtypes = [f32p, f32p, f32p, C.c_int64, C.c_float, C.c_float, C.c_float,
-                                 C.c_float, C.c_int32, C.c_int32, C.c_int32, u32p]
+                                 C.c_float, C.c_int32, C.c_int32, C.c_int32, C.c_int32, u32p]
         L.oracle_neighbors.restype = C.c_int64
         L.oracle_neighbors.argtypes = [f32p, f32p, f32p, C.c_int64, f64p, C.c_int32, C.c_int32,
                                        C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -129,19 +129,19 @@ def normalize(S):
     return t, m.value, h.value
 
 
-def cell_keys(x, y, z, origin, h, ncell):
+def cell_keys(x, y, z, origin, h, ncell, sf):
     x, y, z = _f32(x), _f32(y), _f32(z)
     k = np.zeros(x.shape[0], np.uint32)
     lib().oracle_cell_keys(x, y, z, x.shape[0], origin[0], origin[1], origin[2], h,
-                           ncell[0], ncell[1], ncell[2], k)
+                           ncell[0], ncell[1], ncell[2], sf, k)
     return k
 
 
-def bin_points(x, y, z, origin, h, ncell):
+def bin_points(x, y, z, origin, h, ncell, sf):
     x, y, z = _f32(x), _f32(y), _f32(z)
     perm = np.zeros(x.shape[0], np.uint32)
     lib().oracle_bin(x, y, z, x.shape[0], origin[0], origin[1], origin[2], h,
-                     ncell[0], ncell[1], ncell[2], perm)
+                     ncell[0], ncell[1], ncell[2], sf, perm)
     return perm
 
 

@@ -9,7 +9,7 @@
  *       lam = min_k fl(d_k*d_k),  r2 = fl(neg_ln_eps / lam),
  *       dx = fl(px-cx) (etc.),  dist2 = fl(fl(fl(dx*dx)+fl(dy*dy))+fl(dz*dz)),
  *       member  <=>  dist2 < r2   (strict, as in Eq. 3-15-1);
- *   - the binning cell key: k = clamp(floor(fl(fl(x-ox)/h)), 0, n-1).
+ *   - the binning cell index: k = clamp(floor(fl(fl(x-ox)/h)), 0, n-1).
  * The file must be compiled with -ffp-contract=off so that no multiply-add is
  * fused in those two float expressions.
  *
@@ -114,8 +114,9 @@ void oracle_normalize(const float *S, int64_t n, double *t, double *m_out, doubl
 /* ---------------------------------------------------------------------------
  * Point binning for the neighbour search (Sec. 3.4.4 "nearest-neighbour based"
  * restriction).  The paper does not fix a data structure; the reading used by
- * this project: a uniform cell grid, points stably sorted by (cell, index).
- * Pinned by: numpy lexsort of the same keys. */
+ * this project: a uniform cell grid whose cells are grouped into super cells
+ * of sf^3 cells, points stably sorted by (super cell, cell in the super cell,
+ * index).  Pinned by: numpy lexsort of the same keys. */
 static uint32_t cell_axis(float v, float o, float h, int32_t n) {
     float f = (v - o) / h;
     float fl = floorf(f);
@@ -125,11 +126,16 @@ static uint32_t cell_axis(float v, float o, float h, int32_t n) {
 }
 
 void oracle_cell_keys(const float *x, const float *y, const float *z, int64_t n, float ox, float oy,
-                      float oz, float h, int32_t nx, int32_t ny, int32_t nz, uint32_t *key) {
+                      float oz, float h, int32_t nx, int32_t ny, int32_t nz, int32_t sf, uint32_t *key) {
+    uint32_t nsx = (uint32_t)((nx + sf - 1) / sf), nsy = (uint32_t)((ny + sf - 1) / sf);
+    uint32_t s3 = (uint32_t)(sf * sf * sf);
+    (void)nz;
     for (int64_t i = 0; i < n; ++i) {
         uint32_t kx = cell_axis(x[i], ox, h, nx), ky = cell_axis(y[i], oy, h, ny),
                  kz = cell_axis(z[i], oz, h, nz);
-        key[i] = (kz * (uint32_t)ny + ky) * (uint32_t)nx + kx;
+        uint32_t super = ((kz / sf) * nsy + ky / sf) * nsx + kx / sf;
+        uint32_t local = ((kz % sf) * sf + ky % sf) * sf + kx % sf;
+        key[i] = super * s3 + local;
     }
 }
 
@@ -142,9 +148,9 @@ static int cmp_key_index(const void *a, const void *b) {
 }
 
 void oracle_bin(const float *x, const float *y, const float *z, int64_t n, float ox, float oy, float oz,
-                float h, int32_t nx, int32_t ny, int32_t nz, uint32_t *perm) {
+                float h, int32_t nx, int32_t ny, int32_t nz, int32_t sf, uint32_t *perm) {
     uint32_t *key = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n ? n : 1));
-    oracle_cell_keys(x, y, z, n, ox, oy, oz, h, nx, ny, nz, key);
+    oracle_cell_keys(x, y, z, n, ox, oy, oz, h, nx, ny, nz, sf, key);
     for (int64_t i = 0; i < n; ++i) perm[i] = (uint32_t)i;
     g_sort_keys = key;
     qsort(perm, (size_t)n, sizeof(uint32_t), cmp_key_index);

@@ -45,11 +45,11 @@ double oracle_erbf(double vx, double vy, double vz, const double *P, int32_t cap
 /* Eq. 3-10 target normalisation */
 void oracle_normalize(const float *S, int64_t n, double *t, double *m_out, double *h_out);
 
-/* Point binning: canonical float cell key, stable sort by (key, index) */
+/* Point binning: canonical float cell index, super-major key, stable sort by (key, index) */
 void oracle_cell_keys(const float *x, const float *y, const float *z, int64_t n, float ox, float oy,
-                      float oz, float h, int32_t nx, int32_t ny, int32_t nz, uint32_t *key);
+                      float oz, float h, int32_t nx, int32_t ny, int32_t nz, int32_t sf, uint32_t *key);
 void oracle_bin(const float *x, const float *y, const float *z, int64_t n, float ox, float oy, float oz,
-                float h, int32_t nx, int32_t ny, int32_t nz, uint32_t *perm);
+                float h, int32_t nx, int32_t ny, int32_t nz, int32_t sf, uint32_t *perm);
 
 /* Eq. 3-15-1 neighbour lists by brute force over all pairs; CSR in both orientations.
  * kcol / pcol may be NULL (count only).  Returns the number of pairs. */

@@ -17,7 +17,7 @@ SERBF_ECAPACITY = -3
 SERBF_ECUDA = -4
 SERBF_ETIMEOUT = -5
 
-FLAG_SUPER_LIST, FLAG_CELL_LIST, FLAG_ADD_CAPACITY, FLAG_ROWS = 1, 2, 4, 8
+FLAG_SUPER_LIST, FLAG_ADD_CAPACITY = 1, 4
 
 STAT_L2, STAT_L1, STAT_MAXE, STAT_COUNT, STAT_PAIRS_FWD, STAT_PAIRS_BWD = 0, 1, 2, 3, 4, 5
 STAT_ALPHA, STAT_BETA, STAT_BF, STAT_LOSS, NSTATS = 6, 7, 8, 9, 16
@@ -64,7 +64,7 @@ class Grid(C.Structure):
 
 class WsSizes(C.Structure):
     _fields_ = [("max_points", C.c_int64), ("max_kernels", C.c_int32), ("max_cells", C.c_int32),
-                ("cell_cap", C.c_int32), ("super_cap", C.c_int32), ("super_factor", C.c_int32),
+                ("reserved0", C.c_int32), ("super_cap", C.c_int32), ("super_factor", C.c_int32),
                 ("reserved", C.c_int32)]
 
 

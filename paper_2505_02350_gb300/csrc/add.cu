@@ -123,8 +123,9 @@ __global__ void __launch_bounds__(kAddThreads) k_add_select(const float *E, cons
 // radius has a larger |E| (distance in float, same operation order as the
 // support test, <= r2).
 __global__ void k_add_localmax(const float *x, const float *y, const float *z, const float *E,
-                               const uint8_t *mask, const uint32_t *cell_start, serbf_grid g, float r2,
-                               int reach, const unsigned long long *sel, const int32_t *info, uint32_t *keep) {
+                               const uint8_t *mask, const uint32_t *cell_start, serbf_grid g, int sf, int nsx,
+                               int nsy, float r2, int reach, const unsigned long long *sel, const int32_t *info,
+                               uint32_t *keep) {
     if (!info[0]) return;
     const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (s >= info[1]) return;
@@ -135,20 +136,22 @@ __global__ void k_add_localmax(const float *x, const float *y, const float *z, c
     const int kz = cell_axis(zi, g.origin[2], g.h, g.n[2]);
     bool bad = false;
     for (int cz = max(0, kz - reach); cz <= min(g.n[2] - 1, kz + reach) && !bad; ++cz)
-        for (int cy = max(0, ky - reach); cy <= min(g.n[1] - 1, ky + reach) && !bad; ++cy) {
-            const int r0 = (cz * g.n[1] + cy) * g.n[0];
-            const uint32_t b = cell_start[r0 + max(0, kx - reach)], e = cell_start[r0 + min(g.n[0] - 1, kx + reach) + 1];
-            for (uint32_t q0 = b; q0 < e && !bad; q0 += 32) {
-                const uint32_t q = q0 + lane;
-                bool v = false;
-                if (q < e && mask[q]) {
-                    const float dx = __fsub_rn(x[q], xi), dy = __fsub_rn(y[q], yi), dz = __fsub_rn(z[q], zi);
-                    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                    v = d2 <= r2 && fabsf(E[q]) > ei;
+        for (int cy = max(0, ky - reach); cy <= min(g.n[1] - 1, ky + reach) && !bad; ++cy)
+            for (int cx = max(0, kx - reach); cx <= min(g.n[0] - 1, kx + reach) && !bad; ++cx) {
+                const uint32_t key = cell_key(cx, cy, cz, sf, nsx, nsy);
+                const uint32_t b = cell_start[key], e = cell_start[key + 1];
+                for (uint32_t q0 = b; q0 < e && !bad; q0 += 32) {
+                    const uint32_t q = q0 + lane;
+                    bool v = false;
+                    if (q < e && mask[q]) {
+                        const float dx = __fsub_rn(x[q], xi), dy = __fsub_rn(y[q], yi), dz = __fsub_rn(z[q], zi);
+                        const float d2 =
+                            __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                        v = d2 <= r2 && fabsf(E[q]) > ei;
+                    }
+                    bad = __any_sync(0xffffffffu, v);
                 }
-                bad = __any_sync(0xffffffffu, v);
             }
-        }
     if (lane == 0) keep[s] = !bad;
 }
 
@@ -236,8 +239,9 @@ extern "C" int serbf_add_kernels(const serbf_points *pts, const float *S_raw, co
     int reach = (int)ceil(cfg->add_radius / ws->grid.h) + 1;
     if (reach > 1 << 20) reach = 1 << 20;
     unsigned lm_blocks = (unsigned)((kSelMax * 32 + 255) / 256);
-    k_add_localmax<<<lm_blocks, 256, 0, s>>>(pts->x, pts->y, pts->z, err, mask, ws->cell_start, ws->grid, r2, reach,
-                                            ws->sel_key, ws->add_info, ws->sel_keep);
+    k_add_localmax<<<lm_blocks, 256, 0, s>>>(pts->x, pts->y, pts->z, err, mask, ws->cell_start, ws->grid, ws->sf,
+                                            ws->ns[0], ws->ns[1], r2, reach, ws->sel_key, ws->add_info,
+                                            ws->sel_keep);
     k_add_append<<<1, kAddThreads, 0, s>>>(pts->x, pts->y, pts->z, err, S_raw, cfg->dbar_min, cfg->eps, ws->sel_key,
                                            ws->sel_keep, ws->add_info, prm->p, adam_m, adam_v, prm->m, prm->cap,
                                            st_dev, ws->status, ws->needed);

@@ -33,42 +33,46 @@ struct Carver {
 
 bool sizes_ok(const serbf_ws_sizes *s) {
     return s && s->max_points > 0 && s->max_points < (1ll << 31) && s->max_kernels > 0 && s->max_cells > 0 &&
-           s->cell_cap > 0 && s->super_cap > 0 && s->super_factor >= 1 && s->super_factor <= 16;
+           s->super_cap > 0 && s->super_factor >= 1 && s->super_factor <= 16;
 }
 
 void carve(Carver &c, serbf_workspace *w, const serbf_ws_sizes *s) {
     int64_t N = s->max_points, K = s->max_kernels, C = s->max_cells;
-    int64_t T = N / kTile + C + 1;
+    int64_t S = max_supers_for(C, s->super_factor);
+    int64_t cps = (int64_t)s->super_factor * s->super_factor * s->super_factor;
+    int64_t T = N / kTile + S + 1;
     int64_t SB = (N + kSortTile - 1) / kSortTile;
     if (SB < 1) SB = 1;
-    int64_t S = max_supers_for(C, s->super_factor);
+    int64_t K8 = K > 8192 ? K : 8192;
     w->max_tiles = T;
+    w->max_supers = S;
     w->sort_blocks = SB;
     w->keys0 = c.take<uint32_t>(N);
     w->keys1 = c.take<uint32_t>(N);
     w->vals0 = c.take<uint32_t>(N);
     w->vals1 = c.take<uint32_t>(N);
     w->hist = c.take<uint32_t>(256 * SB + 1);
-    w->cell_start = c.take<uint32_t>(C + 1);
-    w->cell_lo = c.take<float4>(C);
-    w->cell_hi = c.take<float4>(C);
+    w->cell_start = c.take<uint32_t>(S * cps + 1);
+    w->super_tile0 = c.take<uint32_t>(S + 1);
+    w->tile_super = c.take<uint32_t>(T);
+    w->tile_start = c.take<uint32_t>(T);
+    w->tile_lo = c.take<float4>(T);
+    w->tile_hi = c.take<float4>(T);
     w->sup_lo = c.take<float4>(S);
     w->sup_hi = c.take<float4>(S);
-    w->cell_tile0 = c.take<uint32_t>(C + 1);
-    w->tile_cell = c.take<uint32_t>(T);
-    w->tile_start = c.take<uint32_t>(T);
     w->kfwd = c.take<float4>(3 * K);
     w->kbwd = c.take<float4>(4 * K);
     w->sup_list = c.take<uint32_t>(S * (int64_t)s->super_cap);
     w->sup_cnt = c.take<uint32_t>(S);
-    w->cell_list = c.take<uint32_t>(C * (int64_t)s->cell_cap);
-    w->cell_cnt = c.take<uint32_t>(C);
     w->fwd_part = c.take<FwdPart>(T / kFwdWarps + 2);
     w->bwd_pairs = c.take<unsigned long long>(K);
-    w->tile_nz = c.take<uint32_t>(T + 1);
-    w->nz_pts = c.take<float4>(N);
-    w->sel_key = c.take<unsigned long long>(K > 8192 ? K : 8192);
-    w->sel_keep = c.take<uint32_t>(K > 8192 ? K : 8192);
+    w->moments = c.take<float>((int64_t)K * kBwdWarpsPerKernel * 22);
+    w->tile_cnt = c.take<uint32_t>(T);
+    w->nzt = c.take<uint32_t>(T);
+    w->nzt_cnt = c.take<uint32_t>(S);
+    w->nz = c.take<float4>(T * kTile);
+    w->sel_key = c.take<unsigned long long>(K8);
+    w->sel_keep = c.take<uint32_t>(K8);
     w->add_info = c.take<int32_t>(16);
     w->status = c.take<int32_t>(16);
     w->needed = c.take<long long>(4);

@@ -1,6 +1,11 @@
-// Point binning (the data structure behind the support test of Eq. 3-15):
-// cell keys, a stable LSD radix sort by (key, index), cell ranges, cell and
-// super-cell bounding boxes and 32-point tiles.  Also the Sec. 3.4.2
+// Point binning (the data structure behind the support test of Eq. 3-15).
+//
+// Cells of edge h are grouped into super cells of sf^3 cells.  Points are
+// radix-sorted by (super cell, cell within the super cell, original index), so
+// every super cell -- and every cell -- is a contiguous range of binned
+// points.  Each super cell's range is cut into 32-point tiles (one warp each);
+// tiles never straddle a super cell, so they are full except the last one of
+// each super cell, and a tile's bounding box is tight.  Also the Sec. 3.4.2
 // refinement entry point, which re-bins the grown training set.
 #include <math.h>
 
@@ -10,13 +15,13 @@ using namespace serbf;
 
 namespace {
 
-__global__ void k_keys(const float *x, const float *y, const float *z, int64_t n, serbf_grid g,
-                       uint32_t *keys, uint32_t *vals) {
+__global__ void k_keys(const float *x, const float *y, const float *z, int64_t n, serbf_grid g, int sf, int nsx,
+                       int nsy, uint32_t *keys, uint32_t *vals) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int kx = cell_axis(x[i], g.origin[0], g.h, g.n[0]);
         int ky = cell_axis(y[i], g.origin[1], g.h, g.n[1]);
         int kz = cell_axis(z[i], g.origin[2], g.h, g.n[2]);
-        keys[i] = ((uint32_t)kz * (uint32_t)g.n[1] + (uint32_t)ky) * (uint32_t)g.n[0] + (uint32_t)kx;
+        keys[i] = cell_key(kx, ky, kz, sf, nsx, nsy);
         vals[i] = (uint32_t)i;
     }
 }
@@ -99,20 +104,73 @@ __global__ void k_count_cells(const uint32_t *keys, int64_t n, uint32_t *cnt) {
         atomicAdd(&cnt[keys[k]], 1u);
 }
 
-// One warp per cell: bounding box of the points actually in the cell.
-__global__ void k_cell_boxes(const uint32_t *cell_start, int ncells, const float *xb, const float *yb,
-                             const float *zb, float4 *lo, float4 *hi, uint32_t *tiles) {
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= ncells) return;
-    uint32_t b = cell_start[warp], e = cell_start[warp + 1];
+// tiles per super cell (for the scan that numbers the tiles)
+__global__ void k_super_tiles(const uint32_t *cell_start, int nsuper, int cps, uint32_t *stile) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsuper; s += gridDim.x * blockDim.x) {
+        uint32_t b = cell_start[(int64_t)s * cps], e = cell_start[(int64_t)(s + 1) * cps];
+        stile[s] = (e - b + kTile - 1) / kTile;
+    }
+}
+
+__global__ void k_fill_tiles(const uint32_t *cell_start, const uint32_t *stile0, int nsuper, int cps,
+                             uint32_t *tile_super, uint32_t *tile_start) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsuper; s += gridDim.x * blockDim.x) {
+        uint32_t t0 = stile0[s], t1 = stile0[s + 1], p0 = cell_start[(int64_t)s * cps];
+        for (uint32_t t = t0; t < t1; ++t) {
+            tile_super[t] = (uint32_t)s;
+            tile_start[t] = p0 + (t - t0) * kTile;
+        }
+    }
+}
+
+__device__ __forceinline__ void warp_box(float x, float y, float z, bool v, float4 &lo, float4 &hi) {
+    float mnx = v ? x : INFINITY, mny = v ? y : INFINITY, mnz = v ? z : INFINITY;
+    float mxx = v ? x : -INFINITY, mxy = v ? y : -INFINITY, mxz = v ? z : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+        mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+        mnz = fminf(mnz, __shfl_xor_sync(0xffffffffu, mnz, o));
+        mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+        mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+        mxz = fmaxf(mxz, __shfl_xor_sync(0xffffffffu, mxz, o));
+    }
+    lo = make_float4(mnx, mny, mnz, 0.f);
+    hi = make_float4(mxx, mxy, mxz, 0.f);
+}
+
+// One warp per tile: the bounding box of its points.
+__global__ void k_tile_boxes(const uint32_t *tile_super, const uint32_t *tile_start, const uint32_t *cell_start,
+                             int cps, int64_t ntiles, const float *xb, const float *yb, const float *zb, float4 *lo,
+                             float4 *hi) {
+    int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (t >= ntiles) return;
+    uint32_t s = tile_super[t], p0 = tile_start[t], pe = cell_start[(int64_t)(s + 1) * cps];
+    uint32_t i = p0 + lane;
+    bool v = i < pe;
+    float4 a, b;
+    warp_box(v ? xb[i] : 0.f, v ? yb[i] : 0.f, v ? zb[i] : 0.f, v, a, b);
+    if (lane == 0) {
+        lo[t] = a;
+        hi[t] = b;
+    }
+}
+
+// One warp per super cell: union of its tile boxes (empty: +inf / -inf).
+__global__ void k_super_boxes(const uint32_t *stile0, int nsuper, const float4 *tlo, const float4 *thi, float4 *slo,
+                              float4 *shi) {
+    int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (s >= nsuper) return;
     float mnx = INFINITY, mny = INFINITY, mnz = INFINITY, mxx = -INFINITY, mxy = -INFINITY, mxz = -INFINITY;
-    for (uint32_t k = b + lane; k < e; k += 32) {
-        mnx = fminf(mnx, xb[k]);
-        mny = fminf(mny, yb[k]);
-        mnz = fminf(mnz, zb[k]);
-        mxx = fmaxf(mxx, xb[k]);
-        mxy = fmaxf(mxy, yb[k]);
-        mxz = fmaxf(mxz, zb[k]);
+    for (uint32_t t = stile0[s] + lane; t < stile0[s + 1]; t += 32) {
+        float4 a = tlo[t], b = thi[t];
+        mnx = fminf(mnx, a.x);
+        mny = fminf(mny, a.y);
+        mnz = fminf(mnz, a.z);
+        mxx = fmaxf(mxx, b.x);
+        mxy = fmaxf(mxy, b.y);
+        mxz = fmaxf(mxz, b.z);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -124,42 +182,8 @@ __global__ void k_cell_boxes(const uint32_t *cell_start, int ncells, const float
         mxz = fmaxf(mxz, __shfl_xor_sync(0xffffffffu, mxz, o));
     }
     if (lane == 0) {
-        lo[warp] = make_float4(mnx, mny, mnz, 0.f);
-        hi[warp] = make_float4(mxx, mxy, mxz, 0.f);
-        tiles[warp] = (e - b + kTile - 1) / kTile;
-    }
-}
-
-__global__ void k_super_boxes(const float4 *clo, const float4 *chi, serbf_grid g, int sf, int nsx, int nsy,
-                              int nsz, float4 *slo, float4 *shi) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nsx * nsy * nsz) return;
-    int sx = s % nsx, sy = (s / nsx) % nsy, sz = s / (nsx * nsy);
-    float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f), hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
-    for (int kz = sz * sf; kz < min(g.n[2], (sz + 1) * sf); ++kz)
-        for (int ky = sy * sf; ky < min(g.n[1], (sy + 1) * sf); ++ky)
-            for (int kx = sx * sf; kx < min(g.n[0], (sx + 1) * sf); ++kx) {
-                int c = (kz * g.n[1] + ky) * g.n[0] + kx;
-                float4 a = clo[c], b = chi[c];
-                lo.x = fminf(lo.x, a.x);
-                lo.y = fminf(lo.y, a.y);
-                lo.z = fminf(lo.z, a.z);
-                hi.x = fmaxf(hi.x, b.x);
-                hi.y = fmaxf(hi.y, b.y);
-                hi.z = fmaxf(hi.z, b.z);
-            }
-    slo[s] = lo;
-    shi[s] = hi;
-}
-
-__global__ void k_fill_tiles(const uint32_t *cell_start, const uint32_t *tile0, int ncells, uint32_t *tile_cell,
-                             uint32_t *tile_start) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncells; c += gridDim.x * blockDim.x) {
-        uint32_t t0 = tile0[c], t1 = tile0[c + 1], p0 = cell_start[c];
-        for (uint32_t t = t0; t < t1; ++t) {
-            tile_cell[t] = (uint32_t)c;
-            tile_start[t] = p0 + (t - t0) * kTile;
-        }
+        slo[s] = make_float4(mnx, mny, mnz, 0.f);
+        shi[s] = make_float4(mxx, mxy, mxz, 0.f);
     }
 }
 
@@ -186,18 +210,13 @@ extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, 
     if (!(grid->h > 0.f) || grid->n[0] < 1 || grid->n[1] < 1 || grid->n[2] < 1) return SERBF_EINVAL;
     int64_t cells = (int64_t)grid->n[0] * grid->n[1] * grid->n[2];
     if (cells > ws->sz.max_cells) return SERBF_EINVAL;
-    int sf = ws->sz.super_factor;
-    int nsx = (grid->n[0] + sf - 1) / sf, nsy = (grid->n[1] + sf - 1) / sf, nsz = (grid->n[2] + sf - 1) / sf;
-    int64_t nsuper = (int64_t)nsx * nsy * nsz;
-    {
-        // same bound as the carve-up
-        double e = cbrt((double)ws->sz.max_cells);
-        int64_t per = (int64_t)ceil(e / sf) + 1;
-        if (nsuper > per * per * per) return SERBF_EINVAL;
-    }
+    const int sf = ws->sz.super_factor, cps = sf * sf * sf;
+    const int nsx = (grid->n[0] + sf - 1) / sf, nsy = (grid->n[1] + sf - 1) / sf, nsz = (grid->n[2] + sf - 1) / sf;
+    const int64_t nsuper = (int64_t)nsx * nsy * nsz;
+    if (nsuper > ws->max_supers) return SERBF_EINVAL;
+    const int64_t ncp = nsuper * cps;  // cells including the padding of partial super cells
     cudaStream_t s = (cudaStream_t)stream;
     ws->grid = *grid;
-    ws->ncells = (int32_t)cells;
     ws->sf = sf;
     ws->ns[0] = nsx;
     ws->ns[1] = nsy;
@@ -208,9 +227,9 @@ extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, 
 
     uint32_t *kin = ws->keys0, *vin = ws->vals0, *kout = ws->keys1, *vout = ws->vals1;
     if (n > 0) {
-        k_keys<<<gsz(n, 256), 256, 0, s>>>(x, y, z, n, *grid, kin, vin);
+        k_keys<<<gsz(n, 256), 256, 0, s>>>(x, y, z, n, *grid, sf, nsx, nsy, kin, vin);
         int nbits = 1;
-        while (nbits < 32 && (1ll << nbits) < cells) ++nbits;
+        while (nbits < 32 && (1ll << nbits) < ncp) ++nbits;
         int64_t nblk = (n + kSortTile - 1) / kSortTile;
         for (int shift = 0; shift < nbits; shift += 8) {
             k_radix_hist<<<(unsigned)nblk, 256, 0, s>>>(kin, n, shift, ws->hist, nblk);
@@ -226,25 +245,28 @@ extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, 
         }
         k_apply_perm<<<gsz(n, 256), 256, 0, s>>>(vin, x, y, z, n, perm, xb, yb, zb);
     }
-    k_zero_u32<<<gsz(cells + 1, 256), 256, 0, s>>>(ws->cell_start, cells + 1);
+    k_zero_u32<<<gsz(ncp + 1, 256), 256, 0, s>>>(ws->cell_start, ncp + 1);
     if (n > 0) k_count_cells<<<gsz(n, 256), 256, 0, s>>>(kin, n, ws->cell_start);
-    int rc = launch_exscan_u32(ws->cell_start, cells, s);
+    int rc = launch_exscan_u32(ws->cell_start, ncp, s);
     if (rc) return rc;
-    k_cell_boxes<<<(unsigned)((cells * 32 + 255) / 256), 256, 0, s>>>(ws->cell_start, (int)cells, xb, yb, zb,
-                                                                      ws->cell_lo, ws->cell_hi, ws->cell_tile0);
-    k_super_boxes<<<(unsigned)((nsuper + 127) / 128), 128, 0, s>>>(ws->cell_lo, ws->cell_hi, *grid, sf, nsx, nsy,
-                                                                   nsz, ws->sup_lo, ws->sup_hi);
-    rc = launch_exscan_u32(ws->cell_tile0, cells, s);
+    k_super_tiles<<<gsz(nsuper, 256), 256, 0, s>>>(ws->cell_start, (int)nsuper, cps, ws->super_tile0);
+    rc = launch_exscan_u32(ws->super_tile0, nsuper, s);
     if (rc) return rc;
-    k_fill_tiles<<<gsz(cells, 256), 256, 0, s>>>(ws->cell_start, ws->cell_tile0, (int)cells, ws->tile_cell,
-                                                 ws->tile_start);
+    k_fill_tiles<<<gsz(nsuper, 256), 256, 0, s>>>(ws->cell_start, ws->super_tile0, (int)nsuper, cps,
+                                                  ws->tile_super, ws->tile_start);
     SERBF_CHECK_LAUNCH();
     uint32_t nt = 0;
-    if (cudaMemcpyAsync(&nt, ws->cell_tile0 + cells, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (cudaMemcpyAsync(&nt, ws->super_tile0 + nsuper, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SERBF_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SERBF_ECUDA;
     if ((int64_t)nt > ws->max_tiles) return SERBF_ECAPACITY;
     ws->ntiles = nt;
+    if (nt > 0)
+        k_tile_boxes<<<(unsigned)((nt * 32 + 255) / 256), 256, 0, s>>>(ws->tile_super, ws->tile_start, ws->cell_start,
+                                                                        cps, nt, xb, yb, zb, ws->tile_lo, ws->tile_hi);
+    k_super_boxes<<<(unsigned)((nsuper * 32 + 255) / 256), 256, 0, s>>>(ws->super_tile0, (int)nsuper, ws->tile_lo,
+                                                                        ws->tile_hi, ws->sup_lo, ws->sup_hi);
+    SERBF_CHECK_LAUNCH();
     ws->binned = 1;
     return SERBF_OK;
 }

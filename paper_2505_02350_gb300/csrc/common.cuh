@@ -12,18 +12,20 @@ namespace serbf {
 constexpr uint64_t kMagic = 0x53455242465753ull;  // "SERBFWS"
 constexpr int kTile = 32;                         // points per forward/backward tile (one warp)
 constexpr int kSortTile = 4096;                   // elements per radix-sort block
-constexpr int kFwdWarps = 4;                      // warps (tiles) per forward block
-constexpr int kFwdBatch = 64;                     // candidate kernels staged per warp and batch
-constexpr int kBwdThreads = 256;                  // threads per adjoint block (one block per kernel)
+constexpr int kFwdWarps = 2;                      // warps (tiles) per forward block
+constexpr int kQueue = 64;                        // per-warp ring of staged candidates
+constexpr int kBwdThreads = 64;                   // threads per adjoint block
+constexpr int kBwdSplit = 16;                     // blocks per kernel in the adjoint
+constexpr int kBwdWarpsPerKernel = kBwdSplit * kBwdThreads / 32;  // == 32, one epilogue lane each
 constexpr int kMaxRowsPerKernel = 1 << 16;        // cell rows a kernel support may span
 constexpr float kLog2e = 1.4426950408889634f;
 
 // Parameter rows (Sec. 3.2): centre, axis parameters d, angles, weight.
 enum { PCX = 0, PCY, PCZ, PD1, PD2, PD3, PTX, PTY, PTZ, PW };
 
-// Per-block partials of the forward reduction.
+// Per-block partials of the forward reduction (L2 as a float-float pair).
 struct FwdPart {
-    double l2;
+    float l2hi, l2lo;
     float maxe;
     uint32_t cnt;
     unsigned long long pairs;
@@ -38,35 +40,36 @@ struct serbf_workspace {
     size_t bytes;
     serbf_ws_sizes sz;
     int64_t max_tiles;
+    int64_t max_supers;
     int64_t sort_blocks;
     // grid recorded by serbf_bin_points
     serbf_grid grid;
-    int32_t ncells;
-    int32_t sf;       // super factor
+    int32_t sf;       // cells per super-cell edge
     int32_t ns[3];    // super cells per axis
     int32_t nsuper;
+    int32_t binned;
     int64_t npoints;
     int64_t ntiles;
-    int32_t binned;
-    int32_t pad0;
     // binning
     uint32_t *keys0, *keys1, *vals0, *vals1, *hist;
-    uint32_t *cell_start;  // ncells + 1
-    float4 *cell_lo, *cell_hi;
+    uint32_t *cell_start;   // nsuper * sf^3 + 1 (super-major cell order)
+    uint32_t *super_tile0;  // nsuper + 1: first tile of each super cell
+    uint32_t *tile_super, *tile_start;
+    float4 *tile_lo, *tile_hi;
     float4 *sup_lo, *sup_hi;
-    uint32_t *cell_tile0;  // ncells + 1 (first tile of each cell)
-    uint32_t *tile_cell, *tile_start;
     // per-kernel records
     float4 *kfwd;  // 3 per kernel
     float4 *kbwd;  // 4 per kernel
-    // candidate lists
+    // candidate lists (ascending kernel index) per super cell
     uint32_t *sup_list, *sup_cnt;
-    uint32_t *cell_list, *cell_cnt;
     // reductions
     serbf::FwdPart *fwd_part;
     unsigned long long *bwd_pairs;
-    uint32_t *tile_nz;  // max_tiles + 1
-    float4 *nz_pts;     // max_points
+    float *moments;     // max_kernels x kBwdWarpsPerKernel x 22 (float-float partial moments, pairs)
+    uint32_t *tile_cnt; // nonzero-residual points per tile
+    uint32_t *nzt;      // per super cell: ids of its tiles with nonzero residuals (in its tile range)
+    uint32_t *nzt_cnt;  // per super cell: number of such tiles
+    float4 *nz;         // 32 slots per tile: (x, y, z, E) of its nonzero-residual points
     // addition scratch
     unsigned long long *sel_key;  // max(max_kernels, 8192)
     uint32_t *sel_keep;           // max(max_kernels, 8192)
@@ -124,6 +127,46 @@ __device__ __forceinline__ int cell_axis(float v, float o, float h, int n) {
     if (!(f >= 0.f)) return 0;
     if (f >= (float)(n - 1)) return n - 1;
     return (int)f;
+}
+
+// Super-major cell key: super cell id * sf^3 + cell id inside the super cell.
+__device__ __forceinline__ uint32_t cell_key(int kx, int ky, int kz, int sf, int nsx, int nsy) {
+    const int sx = kx / sf, sy = ky / sf, sz = kz / sf;
+    const int lx = kx - sx * sf, ly = ky - sy * sf, lz = kz - sz * sf;
+    const uint32_t sup = ((uint32_t)sz * (uint32_t)nsy + (uint32_t)sy) * (uint32_t)nsx + (uint32_t)sx;
+    return sup * (uint32_t)(sf * sf * sf) + (uint32_t)((lz * sf + ly) * sf + lx);
+}
+
+// Float-float ("double-float") accumulator: hi + lo carries about 48 bits.
+// FP64 throughput on this part is a small fraction of FP32, so per-point and
+// per-pair sums use this instead of double.
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const ff s = two_sum(a.hi, b.hi);
+    const float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s.hi, lo);
+    return {hi, __fsub_rn(lo, __fsub_rn(hi, s.hi))};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, float b) { return ff_add(a, ff{b, 0.f}); }
+
+__device__ __forceinline__ ff warp_sum_ff(ff v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ff w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = ff_add(v, w);
+    }
+    return v;
 }
 
 template <typename T>
@@ -202,24 +245,6 @@ __device__ __forceinline__ KBox kernel_box(float cx, float cy, float cz, float r
     b.nyr = b.ky1 - b.ky0 + 1;
     b.nrows = b.nyr * (b.kz1 - b.kz0 + 1);
     return b;
-}
-
-// First and last cell of row `row` whose box may hold support points
-// (c0 = -1 when none).  Cells are consecutive ids along x.
-__device__ __forceinline__ void row_cells(const KBox &b, int row, float cx, float cy, float cz, float r2,
-                                          const float4 *lo, const float4 *hi, const serbf_grid &g, int &c0,
-                                          int &c1) {
-    int ky = b.ky0 + row % b.nyr, kz = b.kz0 + row / b.nyr;
-    int base = (kz * g.n[1] + ky) * g.n[0];
-    c0 = -1;
-    c1 = -1;
-    for (int kx = b.kx0; kx <= b.kx1; ++kx) {
-        int c = base + kx;
-        if (box_d2(cx, cy, cz, lo[c], hi[c]) < r2) {
-            if (c0 < 0) c0 = c;
-            c1 = c;
-        }
-    }
 }
 
 }  // namespace serbf

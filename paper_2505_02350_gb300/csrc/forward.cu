@@ -1,12 +1,16 @@
 // Point-major forward (Eq. 3-26) over the support pairs of Eq. 3-15-1, the
 // point filter of Eq. 3-18 and the loss terms of Eq. 3-19.
 //
-// One warp per 32-point tile of a cell; lanes are points.  The warp walks its
-// cell's candidate kernels in ascending order: their records are gathered
-// from global memory with float4 loads into a per-warp shared-memory batch and
-// then read back as warp-wide broadcasts, so every lane evaluates the same
-// kernel at once.  Each lane applies the exact support predicate to its own
-// point, so the pairs summed are exactly the point-major neighbour rows.
+// One warp per 32-point tile; lanes are points.  The warp streams its super
+// cell's candidate list (ascending kernel index), keeps the kernels whose
+// support reaches the tile's bounding box (one candidate per lane, ballot),
+// and gathers their records with float4 loads into a per-warp shared-memory
+// ring.  Each full batch of 32 staged kernels is then evaluated with warp-wide
+// broadcast reads: every lane applies the exact support predicate to its own
+// point, so the pairs summed are exactly the point-major neighbour rows, in
+// ascending kernel order.
+#include <math.h>
+
 #include "common.cuh"
 
 using namespace serbf;
@@ -15,12 +19,13 @@ namespace {
 
 struct FwdArgs {
     const float *x, *y, *z, *t;
-    const uint32_t *tile_cell, *tile_start, *cell_start;
-    const uint32_t *clist, *ccnt;
+    const uint32_t *tile_super, *tile_start, *cell_start;
+    const float4 *tile_lo, *tile_hi;
+    const uint32_t *slist, *scnt;
     const float4 *kfwd;
     int64_t ntiles;
-    int ccap;
-    double tau1, tau2;
+    int scap, cps;
+    float tau1, tau2;  // tau1 rounded down, tau2 rounded up to float: exact double decisions
     float *psi, *err;
     uint8_t *mask;
     FwdPart *part;
@@ -28,95 +33,175 @@ struct FwdArgs {
     double *stats;
 };
 
+// Squared distance from c to the farthest corner of a box, rounded so that
+// it is never below the float squared distance of any point inside the box:
+// box_far_d2 < r2 means every point of the box is in the support.
+__device__ __forceinline__ float box_far_d2(float cx, float cy, float cz, float4 lo, float4 hi) {
+    const float ax = fmaxf(__fsub_rn(cx, lo.x), __fsub_rn(hi.x, cx));
+    const float ay = fmaxf(__fsub_rn(cy, lo.y), __fsub_rn(hi.y, cy));
+    const float az = fmaxf(__fsub_rn(cz, lo.z), __fsub_rn(hi.z, cz));
+    return __fadd_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)), __fmul_rn(az, az));
+}
+
+// Up to 32 kernels whose support only partly covers the tile: exact predicate per lane.
+template <int UNROLL>
+__device__ __forceinline__ void eval_partial(const float4 (*ring)[3], int cnt, float px, float py, float pz,
+                                            float &acc, uint32_t &n) {
+#pragma unroll UNROLL
+    for (int q = 0; q < cnt; ++q) {
+        {
+            const float4 k0 = ring[q][0], k1 = ring[q][1], k2 = ring[q][2];
+            const float dx = __fsub_rn(px, k0.x), dy = __fsub_rn(py, k0.y), dz = __fsub_rn(pz, k0.z);
+            const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
+            const bool in = __fadd_rn(__fadd_rn(xx, yy), zz) < k0.w;
+            // q = dv^T Q dv (log2 units): dx (Q11 dx + 2Q12 dy + 2Q13 dz) + dy (Q22 dy + 2Q23 dz) + Q33 dz^2
+            const float ra = fmaf(k2.y, dz, fmaf(k2.x, dy, k1.x * dx));
+            const float rb = fmaf(k2.z, dz, k1.y * dy);
+            const float qv = fmaf(k1.z, zz, fmaf(dy, rb, dx * ra));
+            const float phi = ex2_approx(-qv);
+            acc = in ? fmaf(k1.w, phi, acc) : acc;
+            n += in;
+        }
+    }
+}
+
+// Up to 32 kernels whose support covers the whole tile box: no predicate needed.
+template <int UNROLL>
+__device__ __forceinline__ void eval_full(const float4 (*ring)[3], int cnt, float px, float py, float pz,
+                                         float &acc) {
+#pragma unroll UNROLL
+    for (int q = 0; q < cnt; ++q) {
+        {
+            const float4 k0 = ring[q][0], k1 = ring[q][1], k2 = ring[q][2];
+            const float dx = px - k0.x, dy = py - k0.y, dz = pz - k0.z;
+            const float ra = fmaf(k2.y, dz, fmaf(k2.x, dy, k1.x * dx));
+            const float rb = fmaf(k2.z, dz, k1.y * dy);
+            const float qv = fmaf(k1.z, dz * dz, fmaf(dy, rb, dx * ra));
+            acc = fmaf(k1.w, ex2_approx(-qv), acc);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kFwdWarps * 32) k_forward(FwdArgs a) {
-    __shared__ float4 sk[kFwdWarps][kFwdBatch][3];
-    __shared__ double s_l2[kFwdWarps];
+    // two rings per warp (kernels partly / fully covering the tile); a ring
+    // holds 64 staged records and is consumed 32 at a time from slot 0 or 32
+    __shared__ float4 ringP[kFwdWarps][kQueue][3];
+    __shared__ float4 ringF[kFwdWarps][kQueue][3];
+    __shared__ ff s_l2[kFwdWarps];
     __shared__ float s_mx[kFwdWarps];
     __shared__ uint32_t s_cnt[kFwdWarps];
     __shared__ unsigned long long s_pairs[kFwdWarps];
     __shared__ bool s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t tile = (int64_t)blockIdx.x * kFwdWarps + warp;
+    const unsigned lt = (1u << lane) - 1u;
 
-    double l2 = 0.0;
+    float l2 = 0.f;
     float mx = 0.f;
     uint32_t cnt = 0;
     uint32_t pairs = 0;
     if (tile < a.ntiles) {
-        const uint32_t cell = a.tile_cell[tile];
-        const uint32_t p0 = a.tile_start[tile], pe = a.cell_start[cell + 1];
+        const uint32_t sup = a.tile_super[tile];
+        const uint32_t p0 = a.tile_start[tile], pe = a.cell_start[(int64_t)(sup + 1) * a.cps];
         const int64_t i = (int64_t)p0 + lane;
         const bool valid = i < (int64_t)pe;
         // invalid lanes carry NaN so the support test fails for them
         const float px = valid ? a.x[i] : __int_as_float(0x7fc00000);
         const float py = valid ? a.y[i] : 0.f;
         const float pz = valid ? a.z[i] : 0.f;
-        const uint32_t *lst = a.clist + (size_t)cell * a.ccap;
-        const int L = min((int)a.ccnt[cell], a.ccap);
+        const float4 lo = a.tile_lo[tile], hi = a.tile_hi[tile];
+        const uint32_t *lst = a.slist + (size_t)sup * a.scap;
+        const int L = min((int)a.scnt[sup], a.scap);
+        int hp = 0, qp = 0, hf = 0, qf = 0;
+        uint32_t nfull = 0;
         float acc = 0.f;
-        for (int b0 = 0; b0 < L; b0 += kFwdBatch) {
-            const int nb = min(kFwdBatch, L - b0);
-            for (int s = lane; s < nb; s += 32) {
-                const uint32_t j = lst[b0 + s];
-                sk[warp][s][0] = a.kfwd[3 * j + 0];
-                sk[warp][s][1] = a.kfwd[3 * j + 1];
-                sk[warp][s][2] = a.kfwd[3 * j + 2];
+        uint32_t np = 0;
+        uint32_t jn = lane < L ? lst[lane] : 0u;
+        for (int b = 0; b < L; b += 32) {
+            const uint32_t j = jn;
+            const bool live = b + lane < L;
+            if (b + 32 + lane < L) jn = lst[b + 32 + lane];  // prefetch the next chunk
+            bool part = false, full = false;
+            float4 k0;
+            if (live) {
+                k0 = a.kfwd[3 * j];
+                if (box_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w) {
+                    full = box_far_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w;
+                    part = !full;
+                }
             }
+            const unsigned bp = __ballot_sync(0xffffffffu, part), bf = __ballot_sync(0xffffffffu, full);
+            if (part || full) {
+                float4(*ring)[3] = part ? ringP[warp] : ringF[warp];
+                const int slot = part ? ((hp + qp + __popc(bp & lt)) & (kQueue - 1))
+                                      : ((hf + qf + __popc(bf & lt)) & (kQueue - 1));
+                ring[slot][0] = k0;
+                ring[slot][1] = a.kfwd[3 * j + 1];
+                ring[slot][2] = a.kfwd[3 * j + 2];
+            }
+            qp += __popc(bp);
+            qf += __popc(bf);
             __syncwarp();
-#pragma unroll 4
-            for (int s = 0; s < nb; ++s) {
-                const float4 k0 = sk[warp][s][0], k1 = sk[warp][s][1], k2 = sk[warp][s][2];
-                const float dx = __fsub_rn(px, k0.x), dy = __fsub_rn(py, k0.y), dz = __fsub_rn(pz, k0.z);
-                const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
-                const bool in = __fadd_rn(__fadd_rn(xx, yy), zz) < k0.w;
-                // q = dv^T Q dv (log2 units): dx (Q11 dx + 2Q12 dy + 2Q13 dz) + dy (Q22 dy + 2Q23 dz) + Q33 dz^2
-                const float ra = fmaf(k2.y, dz, fmaf(k2.x, dy, k1.x * dx));
-                const float rb = fmaf(k2.z, dz, k1.y * dy);
-                const float q = fmaf(k1.z, zz, fmaf(dy, rb, dx * ra));
-                const float phi = ex2_approx(-q);
-                acc = in ? fmaf(k1.w, phi, acc) : acc;
-                pairs += in;
+            if (qp >= 32) {
+                eval_partial<8>(ringP[warp] + hp, 32, px, py, pz, acc, np);
+                hp ^= 32;
+                qp -= 32;
+            }
+            if (qf >= 32) {
+                eval_full<8>(ringF[warp] + hf, 32, px, py, pz, acc);
+                hf ^= 32;
+                qf -= 32;
+                nfull += 32;
             }
             __syncwarp();
         }
+        // leftovers: head is 0 or 32 and fewer than 32 remain, so they do not wrap
+        if (qp > 0) eval_partial<1>(ringP[warp] + hp, qp, px, py, pz, acc, np);
+        if (qf > 0) {
+            eval_full<1>(ringF[warp] + hf, qf, px, py, pz, acc);
+            nfull += qf;
+        }
         if (valid) {
-            const double t = a.t[i];
-            const double ps = acc;
+            pairs = np + nfull;
+            const float t = a.t[i], ps = acc;
             const bool m0 = (a.tau1 < t) && (t < a.tau2);
             const bool m1 = (t <= a.tau1) && (ps > a.tau1);
             const bool m2 = (t >= a.tau2) && (ps < a.tau2);
             const bool mk = m0 || m1 || m2;
-            const float e = mk ? __fsub_rn(acc, a.t[i]) : 0.f;
-            a.psi[i] = acc;
+            const float e = mk ? __fsub_rn(ps, t) : 0.f;
+            a.psi[i] = ps;
             a.err[i] = e;
             a.mask[i] = (uint8_t)mk;
             if (mk) {
-                l2 = (double)e * (double)e;
+                l2 = e * e;
                 mx = fabsf(e);
                 cnt = 1;
             }
         }
     }
     // deterministic reduction: lanes -> warp -> block partial -> last block
-    l2 = warp_sum(l2);
+    const ff l2w = warp_sum_ff(ff{l2, 0.f});
     mx = warp_max(mx);
     cnt = warp_sum(cnt);
-    unsigned long long pr = warp_sum((unsigned long long)pairs);
+    const unsigned long long pr = warp_sum((unsigned long long)pairs);
     if (lane == 0) {
-        s_l2[warp] = l2;
+        s_l2[warp] = l2w;
         s_mx[warp] = mx;
         s_cnt[warp] = cnt;
         s_pairs[warp] = pr;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        FwdPart p{0.0, 0.f, 0u, 0ull};
+        ff l{0.f, 0.f};
+        FwdPart p{0.f, 0.f, 0.f, 0u, 0ull};
         for (int w = 0; w < kFwdWarps; ++w) {
-            p.l2 += s_l2[w];
+            l = ff_add(l, s_l2[w]);
             p.maxe = fmaxf(p.maxe, s_mx[w]);
             p.cnt += s_cnt[w];
             p.pairs += s_pairs[w];
         }
+        p.l2hi = l.hi;
+        p.l2lo = l.lo;
         a.part[blockIdx.x] = p;
         __threadfence();
         const uint32_t prev = atomicAdd(a.counter, 1u);
@@ -126,17 +211,17 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_forward(FwdArgs a) {
     if (!s_last) return;
     __threadfence();
     // last block: fixed-order sum of all block partials
-    double L2 = 0.0;
+    ff L2{0.f, 0.f};
     float MX = 0.f;
     unsigned long long C = 0, P = 0;
     for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
         const FwdPart *q = a.part + b;
-        L2 += __ldcg(&q->l2);
+        L2 = ff_add(L2, ff{__ldcg(&q->l2hi), __ldcg(&q->l2lo)});
         MX = fmaxf(MX, __ldcg(&q->maxe));
         C += __ldcg(&q->cnt);
         P += __ldcg(&q->pairs);
     }
-    L2 = warp_sum(L2);
+    L2 = warp_sum_ff(L2);
     MX = warp_max(MX);
     C = warp_sum(C);
     P = warp_sum(P);
@@ -148,16 +233,16 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_forward(FwdArgs a) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double l = 0.0;
+        ff l{0.f, 0.f};
         float m = 0.f;
         unsigned long long c = 0, pp = 0;
         for (int w = 0; w < kFwdWarps; ++w) {
-            l += s_l2[w];
+            l = ff_add(l, s_l2[w]);
             m = fmaxf(m, s_mx[w]);
             c += s_cnt[w];
             pp += s_pairs[w];
         }
-        a.stats[SERBF_STAT_L2] = l;
+        a.stats[SERBF_STAT_L2] = (double)l.hi + (double)l.lo;
         a.stats[SERBF_STAT_MAXE] = m;
         a.stats[SERBF_STAT_COUNT] = (double)c;
         a.stats[SERBF_STAT_PAIRS_FWD] = (double)pp;
@@ -178,16 +263,23 @@ extern "C" int serbf_forward(const serbf_points *pts, const serbf_params *prm, c
     a.y = pts->y;
     a.z = pts->z;
     a.t = pts->t;
-    a.tile_cell = ws->tile_cell;
+    a.tile_super = ws->tile_super;
     a.tile_start = ws->tile_start;
     a.cell_start = ws->cell_start;
-    a.clist = ws->cell_list;
-    a.ccnt = ws->cell_cnt;
+    a.tile_lo = ws->tile_lo;
+    a.tile_hi = ws->tile_hi;
+    a.slist = ws->sup_list;
+    a.scnt = ws->sup_cnt;
     a.kfwd = ws->kfwd;
     a.ntiles = ws->ntiles;
-    a.ccap = ws->sz.cell_cap;
-    a.tau1 = cfg->tau1;
-    a.tau2 = cfg->tau2;
+    a.scap = ws->sz.super_cap;
+    a.cps = ws->sf * ws->sf * ws->sf;
+    // float thresholds that give the same decisions as comparing in double:
+    // t <= tau1 iff t <= (largest float <= tau1), t >= tau2 iff t >= (smallest float >= tau2)
+    a.tau1 = (float)cfg->tau1;
+    if ((double)a.tau1 > cfg->tau1) a.tau1 = nextafterf(a.tau1, -INFINITY);
+    a.tau2 = (float)cfg->tau2;
+    if ((double)a.tau2 < cfg->tau2) a.tau2 = nextafterf(a.tau2, INFINITY);
     a.psi = psi;
     a.err = err;
     a.mask = mask;

@@ -1,7 +1,9 @@
 // Per-step rebuild of the kernel <-> point neighbour structure (Eq. 3-15,
-// Eq. 3-15-1): per-kernel records, super-cell and cell candidate lists (every
-// list in ascending kernel index), and on request the explicit kernel-major and
-// point-major CSR lists.
+// Eq. 3-15-1): per-kernel records and, per super cell, the list of kernels
+// (ascending index) whose support may reach it.  The forward and the adjoint
+// refine these lists against tight 32-point tile boxes and apply the exact
+// support predicate per pair.  On request the explicit kernel-major and
+// point-major CSR lists are produced from the same structure.
 #include <math.h>
 
 #include "common.cuh"
@@ -19,13 +21,12 @@ __global__ void k_prep(const float *p, int cap, const int32_t *m_dev, float nle,
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
         float cx = p[PCX * cap + j], cy = p[PCY * cap + j], cz = p[PCZ * cap + j];
         float d1 = p[PD1 * cap + j], d2 = p[PD2 * cap + j], d3 = p[PD3 * cap + j];
-        double tx = p[PTX * cap + j], ty = p[PTY * cap + j], tz = p[PTZ * cap + j];
         float w = p[PW * cap + j];
-        double sx, cxs, sy, cys, sz, czs;
-        sincos(tx, &sx, &cxs);
-        sincos(ty, &sy, &cys);
-        sincos(tz, &sz, &czs);
-        double R[9];
+        float sx, cxs, sy, cys, sz, czs;
+        sincosf(p[PTX * cap + j], &sx, &cxs);
+        sincosf(p[PTY * cap + j], &sy, &cys);
+        sincosf(p[PTZ * cap + j], &sz, &czs);
+        float R[9];
         R[0] = cxs * cys;
         R[1] = -czs * sx - sy * sz * cxs;
         R[2] = sx * sz - cxs * czs * sy;
@@ -35,21 +36,20 @@ __global__ void k_prep(const float *p, int cap, const int32_t *m_dev, float nle,
         R[6] = sy;
         R[7] = cys * sz;
         R[8] = cys * czs;
-        double L2E = 1.4426950408889634;
-        double e[3] = {L2E * (double)d1 * d1, L2E * (double)d2 * d2, L2E * (double)d3 * d3};
-        double Q[3][3];
+        const float e[3] = {kLog2e * d1 * d1, kLog2e * d2 * d2, kLog2e * d3 * d3};
+        float Q[3][3];
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b)
-                Q[a][b] = e[0] * R[a] * R[b] + e[1] * R[3 + a] * R[3 + b] + e[2] * R[6 + a] * R[6 + b];
+                Q[a][b] = fmaf(e[0] * R[a], R[b], fmaf(e[1] * R[3 + a], R[3 + b], e[2] * R[6 + a] * R[6 + b]));
         float r2 = support_r2(d1, d2, d3, nle);
         float aw = w * fabsf(w);
         kfwd[3 * j + 0] = make_float4(cx, cy, cz, r2);
-        kfwd[3 * j + 1] = make_float4((float)Q[0][0], (float)Q[1][1], (float)Q[2][2], aw);
-        kfwd[3 * j + 2] = make_float4((float)(2.0 * Q[0][1]), (float)(2.0 * Q[0][2]), (float)(2.0 * Q[1][2]), 0.f);
+        kfwd[3 * j + 1] = make_float4(Q[0][0], Q[1][1], Q[2][2], aw);
+        kfwd[3 * j + 2] = make_float4(2.f * Q[0][1], 2.f * Q[0][2], 2.f * Q[1][2], 0.f);
         kbwd[4 * j + 0] = make_float4(cx, cy, cz, r2);
-        kbwd[4 * j + 1] = make_float4((float)R[0], (float)R[1], (float)R[2], (float)e[0]);
-        kbwd[4 * j + 2] = make_float4((float)R[3], (float)R[4], (float)R[5], (float)e[1]);
-        kbwd[4 * j + 3] = make_float4((float)R[6], (float)R[7], (float)R[8], (float)e[2]);
+        kbwd[4 * j + 1] = make_float4(R[0], R[1], R[2], e[0]);
+        kbwd[4 * j + 2] = make_float4(R[3], R[4], R[5], e[1]);
+        kbwd[4 * j + 3] = make_float4(R[6], R[7], R[8], e[2]);
     }
 }
 
@@ -88,69 +88,32 @@ __global__ void __launch_bounds__(256) k_super_lists(const float4 *kfwd, const i
     }
 }
 
-// One warp per cell: filter the super-cell list against the cell's box.
-__global__ void k_cell_lists(const float4 *kfwd, const float4 *clo, const float4 *chi, int ncells, serbf_grid g,
-                             int sf, int nsx, int nsy, const uint32_t *slist, const uint32_t *scnt, int scap,
-                             uint32_t *list, uint32_t *cnt, int ccap, int32_t *status, long long *needed) {
-    int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (c >= ncells) return;
-    float4 lo = clo[c], hi = chi[c];
-    if (!(lo.x <= hi.x)) {
-        if (lane == 0) cnt[c] = 0;
-        return;
-    }
-    int kx = c % g.n[0], ky = (c / g.n[0]) % g.n[1], kz = c / (g.n[0] * g.n[1]);
-    int s = ((kz / sf) * nsy + ky / sf) * nsx + kx / sf;
-    int L = min((int)scnt[s], scap);
-    const uint32_t *in = slist + (size_t)s * scap;
-    uint32_t *out = list + (size_t)c * ccap;
-    uint32_t count = 0;
-    for (int b = 0; b < L; b += 32) {
-        int idx = b + lane;
-        bool hit = false;
-        uint32_t j = 0;
-        if (idx < L) {
-            j = in[idx];
-            float4 k = kfwd[3 * j];
-            hit = box_d2(k.x, k.y, k.z, lo, hi) < k.w;
-        }
-        unsigned bal = __ballot_sync(0xffffffffu, hit);
-        uint32_t rank = __popc(bal & ((1u << lane) - 1u));
-        if (hit && count + rank < (uint32_t)ccap) out[count + rank] = j;
-        count += __popc(bal);
-    }
-    if (lane == 0) {
-        cnt[c] = count;
-        if (count > (uint32_t)ccap) {
-            atomicOr(status, SERBF_FLAG_CELL_LIST);
-            atomicMax(needed + 1, (long long)count);
-        }
-    }
-}
-
 // ---------------------------------------------------------------- point-major CSR
-// One warp per tile; lanes are points, the cell's candidate list is walked in
-// ascending kernel order, so each row comes out sorted.
+// One warp per tile; lanes are points.  The super cell's list is walked in
+// ascending kernel order (entries whose support misses the tile box are
+// skipped), so each row comes out sorted.
 template <bool FILL>
-__global__ void k_pmajor(const float *x, const float *y, const float *z, const uint32_t *tile_cell,
-                         const uint32_t *tile_start, const uint32_t *cell_start, int64_t ntiles,
-                         const uint32_t *clist, const uint32_t *ccnt, int ccap, const float4 *kfwd,
-                         int64_t *rowptr, uint32_t *col) {
+__global__ void k_pmajor(const float *x, const float *y, const float *z, const uint32_t *tile_super,
+                         const uint32_t *tile_start, const float4 *tlo, const float4 *thi, const uint32_t *cell_start,
+                         int cps, int64_t ntiles, const uint32_t *slist, const uint32_t *scnt, int scap,
+                         const float4 *kfwd, int64_t *rowptr, uint32_t *col) {
     int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (t >= ntiles) return;
-    uint32_t c = tile_cell[t], p0 = tile_start[t], pe = cell_start[c + 1];
+    uint32_t s = tile_super[t], p0 = tile_start[t], pe = cell_start[(int64_t)(s + 1) * cps];
     int64_t i = (int64_t)p0 + lane;
     bool valid = i < (int64_t)pe;
     float px = valid ? x[i] : __int_as_float(0x7fc00000);
     float py = valid ? y[i] : 0.f, pz = valid ? z[i] : 0.f;
-    int L = min((int)ccnt[c], ccap);
-    const uint32_t *lst = clist + (size_t)c * ccap;
+    float4 lo = tlo[t], hi = thi[t];
+    int L = min((int)scnt[s], scap);
+    const uint32_t *lst = slist + (size_t)s * scap;
     int64_t o = FILL && valid ? rowptr[i] : 0;
     int64_t n = 0;
-    for (int s = 0; s < L; ++s) {
-        uint32_t j = lst[s];
+    for (int q = 0; q < L; ++q) {
+        uint32_t j = lst[q];
         float4 k = kfwd[3 * j];
+        if (!(box_d2(k.x, k.y, k.z, lo, hi) < k.w)) continue;
         if (in_support(px, py, pz, k.x, k.y, k.z, k.w)) {
             if (FILL) col[o + n] = j;
             ++n;
@@ -160,62 +123,36 @@ __global__ void k_pmajor(const float *x, const float *y, const float *z, const u
 }
 
 // ---------------------------------------------------------------- kernel-major CSR
-// One block per kernel.  Rows of cells are visited in ascending (kz, ky); within
-// a row, cells and points are in ascending binned order, so each CSR row comes
-// out sorted.  Elements are compacted in order with block scans.
+// One warp per kernel.  Super cells are visited in ascending id, their tiles in
+// ascending order and each tile's points in order, which is ascending binned
+// index, so each CSR row comes out sorted.
 template <bool FILL>
-__global__ void __launch_bounds__(256) k_kmajor(const float *x, const float *y, const float *z,
-                                                const float4 *kfwd, const int32_t *m_dev, serbf_grid g,
-                                                const float4 *clo, const float4 *chi, const uint32_t *cell_start,
-                                                int64_t *rowptr, uint32_t *col) {
-    __shared__ uint32_t rs[256];
-    __shared__ uint32_t ro[257];
-    __shared__ uint32_t tmp[33];
-    int j = blockIdx.x;
-    int m = *m_dev;
-    if (j >= m) return;
+__global__ void k_kmajor(const float *x, const float *y, const float *z, const float4 *kfwd, const int32_t *m_dev,
+                         serbf_grid g, int sf, int nsx, int nsy, const float4 *slo, const float4 *shi,
+                         const uint32_t *stile0, const uint32_t *tile_start, const float4 *tlo, const float4 *thi,
+                         const uint32_t *cell_start, int cps, int64_t *rowptr, uint32_t *col) {
+    int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (j >= *m_dev) return;
     float4 k = kfwd[3 * j];
     KBox b = kernel_box(k.x, k.y, k.z, k.w, g);
     int64_t base = FILL ? rowptr[j] : 0;
     uint32_t count = 0;
-    for (int r0 = 0; r0 < b.nrows; r0 += 256) {
-        int row = r0 + threadIdx.x;
-        uint32_t start = 0, len = 0;
-        if (row < b.nrows) {
-            int c0, c1;
-            row_cells(b, row, k.x, k.y, k.z, k.w, clo, chi, g, c0, c1);
-            if (c0 >= 0) {
-                start = cell_start[c0];
-                len = cell_start[c1 + 1] - start;
-            }
-        }
-        uint32_t total;
-        uint32_t off = block_exscan(len, tmp, &total);
-        rs[threadIdx.x] = start;
-        ro[threadIdx.x] = off;
-        if (threadIdx.x == 0) ro[256] = total;
-        __syncthreads();
-        for (uint32_t e0 = 0; e0 < total; e0 += 256) {
-            uint32_t e = e0 + threadIdx.x;
-            uint32_t hit = 0, idx = 0;
-            if (e < total) {
-                int lo = 0, hi = 255;
-                while (lo < hi) {  // last row with ro[row] <= e
-                    int mid = (lo + hi + 1) >> 1;
-                    if (ro[mid] <= e) lo = mid;
-                    else hi = mid - 1;
+    for (int sz = b.kz0 / sf; sz <= b.kz1 / sf; ++sz)
+        for (int sy = b.ky0 / sf; sy <= b.ky1 / sf; ++sy)
+            for (int sx = b.kx0 / sf; sx <= b.kx1 / sf; ++sx) {
+                int s = (sz * nsy + sy) * nsx + sx;
+                if (!(box_d2(k.x, k.y, k.z, slo[s], shi[s]) < k.w)) continue;
+                uint32_t pe_s = cell_start[(int64_t)(s + 1) * cps];
+                for (uint32_t t = stile0[s]; t < stile0[s + 1]; ++t) {
+                    if (!(box_d2(k.x, k.y, k.z, tlo[t], thi[t]) < k.w)) continue;
+                    uint32_t i = tile_start[t] + lane;
+                    bool hit = i < pe_s && in_support(x[i], y[i], z[i], k.x, k.y, k.z, k.w);
+                    unsigned bal = __ballot_sync(0xffffffffu, hit);
+                    if (FILL && hit) col[base + count + __popc(bal & ((1u << lane) - 1u))] = i;
+                    count += __popc(bal);
                 }
-                idx = rs[lo] + (e - ro[lo]);
-                hit = in_support(x[idx], y[idx], z[idx], k.x, k.y, k.z, k.w);
             }
-            uint32_t tot;
-            uint32_t o = block_exscan(hit, tmp, &tot);
-            if (FILL && hit) col[base + count + o] = idx;
-            count += tot;
-        }
-        __syncthreads();
-    }
-    if (!FILL && threadIdx.x == 0) rowptr[j] = count;
+    if (!FILL && lane == 0) rowptr[j] = count;
 }
 
 __global__ void k_zero_i64(int64_t *a, int64_t n) {
@@ -251,28 +188,29 @@ extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params
     if (rc) return rc;
     k_super_lists<<<ws->nsuper, 256, 0, s>>>(ws->kfwd, prm->m, ws->sup_lo, ws->sup_hi, ws->sup_list, ws->sup_cnt,
                                               ws->sz.super_cap, ws->status, ws->needed);
-    k_cell_lists<<<(unsigned)((ws->ncells * 32ll + 255) / 256), 256, 0, s>>>(
-        ws->kfwd, ws->cell_lo, ws->cell_hi, ws->ncells, ws->grid, ws->sf, ws->ns[0], ws->ns[1], ws->sup_list,
-        ws->sup_cnt, ws->sz.super_cap, ws->cell_list, ws->cell_cnt, ws->sz.cell_cap, ws->status, ws->needed);
     SERBF_CHECK_LAUNCH();
     if (!kmajor && !pmajor) return SERBF_OK;
 
-    // Explicit lists: the capacity overflow of the candidate lists must be
-    // excluded first, otherwise the lists would be silently incomplete.
+    // Explicit lists: an overflowing candidate list would make them silently
+    // incomplete, so the status is checked first.
     int32_t flags;
     rc = serbf_status(ws, &flags, nullptr, 0, stream);
     if (rc) return rc;
     int32_t m = 0;
     if (cudaMemcpyAsync(&m, prm->m, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SERBF_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SERBF_ECUDA;
+    const int cps = ws->sf * ws->sf * ws->sf;
     int64_t n = pts->n;
     int64_t total = -1;
     int result = SERBF_OK;
     if (kmajor) {
+        unsigned blocks = (unsigned)(((int64_t)m * 32 + 255) / 256);
         k_zero_i64<<<1, 256, 0, s>>>(kmajor->rowptr, (int64_t)m + 1);
         if (m > 0)
-            k_kmajor<false><<<m, 256, 0, s>>>(pts->x, pts->y, pts->z, ws->kfwd, prm->m, ws->grid, ws->cell_lo,
-                                              ws->cell_hi, ws->cell_start, kmajor->rowptr, nullptr);
+            k_kmajor<false><<<blocks, 256, 0, s>>>(pts->x, pts->y, pts->z, ws->kfwd, prm->m, ws->grid, ws->sf,
+                                                   ws->ns[0], ws->ns[1], ws->sup_lo, ws->sup_hi, ws->super_tile0,
+                                                   ws->tile_start, ws->tile_lo, ws->tile_hi, ws->cell_start, cps,
+                                                   kmajor->rowptr, nullptr);
         rc = launch_exscan_i64(kmajor->rowptr, m, s);
         if (rc) return rc;
         int64_t tot = 0;
@@ -282,8 +220,10 @@ extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params
         total = tot;
         if (tot > kmajor->cap) result = SERBF_ECAPACITY;
         else if (m > 0)
-            k_kmajor<true><<<m, 256, 0, s>>>(pts->x, pts->y, pts->z, ws->kfwd, prm->m, ws->grid, ws->cell_lo,
-                                             ws->cell_hi, ws->cell_start, kmajor->rowptr, kmajor->col);
+            k_kmajor<true><<<blocks, 256, 0, s>>>(pts->x, pts->y, pts->z, ws->kfwd, prm->m, ws->grid, ws->sf,
+                                                  ws->ns[0], ws->ns[1], ws->sup_lo, ws->sup_hi, ws->super_tile0,
+                                                  ws->tile_start, ws->tile_lo, ws->tile_hi, ws->cell_start, cps,
+                                                  kmajor->rowptr, kmajor->col);
         SERBF_CHECK_LAUNCH();
     }
     if (pmajor) {
@@ -291,9 +231,9 @@ extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params
         unsigned blocks = (unsigned)((nt * 32 + 255) / 256);
         k_zero_i64<<<64, 256, 0, s>>>(pmajor->rowptr, n + 1);
         if (nt > 0)
-            k_pmajor<false><<<blocks, 256, 0, s>>>(pts->x, pts->y, pts->z, ws->tile_cell, ws->tile_start,
-                                                   ws->cell_start, nt, ws->cell_list, ws->cell_cnt,
-                                                   ws->sz.cell_cap, ws->kfwd, pmajor->rowptr, nullptr);
+            k_pmajor<false><<<blocks, 256, 0, s>>>(pts->x, pts->y, pts->z, ws->tile_super, ws->tile_start,
+                                                   ws->tile_lo, ws->tile_hi, ws->cell_start, cps, nt, ws->sup_list,
+                                                   ws->sup_cnt, ws->sz.super_cap, ws->kfwd, pmajor->rowptr, nullptr);
         rc = launch_exscan_i64(pmajor->rowptr, n, s);
         if (rc) return rc;
         int64_t tot = 0;
@@ -303,9 +243,10 @@ extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params
         total = tot;
         if (tot > pmajor->cap) result = SERBF_ECAPACITY;
         else if (nt > 0)
-            k_pmajor<true><<<blocks, 256, 0, s>>>(pts->x, pts->y, pts->z, ws->tile_cell, ws->tile_start,
-                                                  ws->cell_start, nt, ws->cell_list, ws->cell_cnt, ws->sz.cell_cap,
-                                                  ws->kfwd, pmajor->rowptr, pmajor->col);
+            k_pmajor<true><<<blocks, 256, 0, s>>>(pts->x, pts->y, pts->z, ws->tile_super, ws->tile_start,
+                                                  ws->tile_lo, ws->tile_hi, ws->cell_start, cps, nt, ws->sup_list,
+                                                  ws->sup_cnt, ws->sz.super_cap, ws->kfwd, pmajor->rowptr,
+                                                  pmajor->col);
         SERBF_CHECK_LAUNCH();
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return SERBF_ECUDA;

@@ -11,148 +11,201 @@ using namespace serbf;
 
 namespace {
 
-constexpr int kStepThreads = 1024;
+constexpr int kStepThreads = 256;
 
-__device__ double block_sum_d(double v, double *sh) {
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x == 0) {
-        for (int w = 0; w < nw; ++w) r += sh[w];
-        sh[32] = r;
+// Block sums of NV float values with float-float trees (FP64 is slow here).
+template <int NV>
+__device__ void block_sums(const float (&v)[NV], ff (*sh)[NV], double (&out)[NV]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const ff s = warp_sum_ff(ff{v[k], 0.f});
+        if (lane == 0) sh[warp][k] = s;
     }
     __syncthreads();
-    r = sh[32];
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            ff t = lane < nw ? sh[lane][k] : ff{0.f, 0.f};
+            t = warp_sum_ff(t);
+            if (lane == 0) sh[32][k] = t;
+        }
+    }
     __syncthreads();
-    return r;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = (double)sh[32][k].hi + (double)sh[32][k].lo;
 }
 
 __device__ __forceinline__ float sgnf(float v) { return (float)((v > 0.f) - (v < 0.f)); }
 
 struct StepArgs {
-    float *p;
+    float *__restrict__ p;
     const int32_t *m;
     int cap;
-    const float *grad;
-    float *am, *av;
+    const float *__restrict__ grad;
+    float *__restrict__ am, *__restrict__ av;
     serbf_state *st;
     double *stats;
     serbf_config c;
 };
 
+constexpr int kStateWords = (int)(sizeof(serbf_state) / 4);
+static_assert(sizeof(serbf_state) % 8 == 0, "state is copied as 32-bit words");
+
 __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
-    __shared__ double sh[33];
-    __shared__ serbf_state st;
+    __shared__ ff sh3[33][3];
+    __shared__ ff sh1[33][1];
     __shared__ double s_alpha;
+    __shared__ float s_bc[2];
+    __shared__ __align__(8) uint32_t s_words[kStateWords];
+    serbf_state &st = *reinterpret_cast<serbf_state *>(s_words);
+    // the whole state comes in with one cooperative round trip
+    const uint32_t *gw = reinterpret_cast<const uint32_t *>(a.st);
+    for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) s_words[k] = gw[k];
     const int m = *a.m, cap = a.cap;
-    if (threadIdx.x == 0) st = *a.st;
+    const double l2 = a.stats[SERBF_STAT_L2], maxe = a.stats[SERBF_STAT_MAXE];
     __syncthreads();
-    const int e = st.epoch + 1;
-    const bool use_l1 = st.l1_optim && (a.stats[SERBF_STAT_MAXE] < a.c.tau_m);
-    // L1 = sum |w| before the update (Eq. 3-14_2)
-    double l1 = 0.0, num = 0.0, den = 0.0;
+    const int epoch = st.epoch, adam_t = st.adam_t, l1_optim = st.l1_optim;
+    const float lr = (float)st.lr;
+    const bool use_l1 = l1_optim && (maxe < a.c.tau_m);
+    // L1 = sum |w| before the update (Eq. 3-14_2) and the Eq. 3-21 dot products
+    float part[3] = {0.f, 0.f, 0.f};
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        const double w = a.p[PW * cap + j];
-        l1 += fabs(w);
+        const float w = a.p[PW * cap + j], g2 = a.grad[PW * cap + j];
+        part[0] += fabsf(w);
         if (use_l1) {
-            const double g1 = (w > 0) - (w < 0), g2 = a.grad[PW * cap + j];
-            num += (g1 - g2) * g1;
-            den += (g2 - g1) * (g2 - g1);
+            const float g1 = sgnf(w);
+            part[1] = fmaf(g1 - g2, g1, part[1]);
+            part[2] = fmaf(g2 - g1, g2 - g1, part[2]);
         }
     }
-    l1 = block_sum_d(l1, sh);
-    num = block_sum_d(num, sh);
-    den = block_sum_d(den, sh);
+    double sums[3];
+    block_sums<3>(part, sh3, sums);
+    const double l1 = sums[0], num = sums[1], den = sums[2];
     if (threadIdx.x == 0) {
         double al = 1.0;
         if (use_l1 && den > 0.0) al = fmin(1.0, fmax(0.0, num / den));
         s_alpha = al;
+        s_bc[0] = 1.f - powf((float)a.c.beta1, (float)(adam_t + 1));
+        s_bc[1] = 1.f - powf((float)a.c.beta2, (float)(adam_t + 1));
     }
     __syncthreads();
     const double alpha = s_alpha, beta = 1.0 - alpha;
-    const int t = st.adam_t + 1;
-    const float lr = (float)st.lr;
     const float b1 = (float)a.c.beta1, b2 = (float)a.c.beta2, eps = (float)a.c.adam_eps;
-    const float bc1 = (float)(1.0 - pow(a.c.beta1, t)), bc2 = (float)(1.0 - pow(a.c.beta2, t));
+    const float bc1 = s_bc[0], bc2 = s_bc[1];
     const float fa = (float)alpha, fb = (float)beta;
-    const int64_t total = 10ll * m;
-    for (int64_t idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int r = (int)(idx / m), j = (int)(idx - (int64_t)r * m);
-        const int64_t q = (int64_t)r * cap + j;
-        float g = fa * a.grad[q];
-        if (r == PW) g = fmaf(fb, sgnf(a.p[q]), g);
-        const float mo = fmaf(b1, a.am[q], (1.f - b1) * g);
-        const float vo = fmaf(b2, a.av[q], (1.f - b2) * g * g);
-        a.am[q] = mo;
-        a.av[q] = vo;
-        a.p[q] -= lr * (mo / bc1) / (sqrtf(vo / bc2) + eps);
+    // b_f: |w| >= tau_d decided in float with tau_d rounded up (same decision as in double)
+    float taud = (float)a.c.tau_d;
+    if ((double)taud < a.c.tau_d) taud = nextafterf(taud, INFINITY);
+    float bfc[1] = {0.f};
+    // Adam on all ten parameter rows (App. A gradient combination); every
+    // thread loads its kernel's 40 values before computing, so the memory
+    // latency is paid once per kernel rather than once per row
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        float g[SERBF_NPARAM], pv[SERBF_NPARAM], mv[SERBF_NPARAM], vv[SERBF_NPARAM];
+#pragma unroll
+        for (int r = 0; r < SERBF_NPARAM; ++r) {
+            const int64_t q = (int64_t)r * cap + j;
+            g[r] = a.grad[q];
+            pv[r] = a.p[q];
+            mv[r] = a.am[q];
+            vv[r] = a.av[q];
+        }
+#pragma unroll
+        for (int r = 0; r < SERBF_NPARAM; ++r) {
+            float gr = fa * g[r];
+            if (r == PW) gr = fmaf(fb, sgnf(pv[r]), gr);
+            mv[r] = fmaf(b1, mv[r], (1.f - b1) * gr);
+            vv[r] = fmaf(b2, vv[r], (1.f - b2) * gr * gr);
+            pv[r] -= lr * (mv[r] / bc1) / (sqrtf(vv[r] / bc2) + eps);
+        }
+#pragma unroll
+        for (int r = 0; r < SERBF_NPARAM; ++r) {
+            const int64_t q = (int64_t)r * cap + j;
+            a.am[q] = mv[r];
+            a.av[q] = vv[r];
+            a.p[q] = pv[r];
+        }
+        bfc[0] += fabsf(pv[PW]) >= taud ? 1.f : 0.f;
+    }
+    double bfs[1];
+    block_sums<1>(bfc, sh1, bfs);
+    const double bf = bfs[0];
+    // epoch tail in the order of Algorithm 3 (warp 0, on the shared copy);
+    // histories are rings indexed by (epoch - 1) mod window
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int e = epoch + 1;
+        const int kl2 = a.c.k_l2, kl1 = a.c.k_l1;
+        int l1n = l1_optim;
+        const int phase2 = st.phase2;
+        if (lane == 0) {
+            st.l2_hist[(e - 1) % kl2] = l2;
+            st.bf_hist[(e - 1) % kl1] = (int32_t)bf;
+            st.n_l2 = min(st.n_l2 + 1, kl2);
+            st.n_bf = min(st.n_bf + 1, kl1);
+        }
+        __syncwarp();
+        const int n_l2 = st.n_l2, n_bf = st.n_bf;
+        const int do_prune = (e % kl2 == 0) && l1n && (e < a.c.T_e);
+        if (!l1n && !phase2 && e >= kl2 && n_l2 == kl2) {
+            double v = 0.0;
+            for (int k = lane; k < kl2; k += 32) v += st.l2_hist[k];
+            const double mean = warp_sum(v) / kl2;
+            double var = 0.0;
+            for (int k = lane; k < kl2; k += 32) var += (st.l2_hist[k] - mean) * (st.l2_hist[k] - mean);
+            var = warp_sum(var) / kl2;
+            if (sqrt(var) < a.c.tau_l2) l1n = 1;
+        }
+        int do_add = 0;
+        if (l1n && !phase2 && n_bf == kl1) {
+            int lo = 0x7fffffff, hi = -0x7fffffff;
+            for (int k = lane; k < kl1; k += 32) {
+                lo = min(lo, st.bf_hist[k]);
+                hi = max(hi, st.bf_hist[k]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            if ((double)(hi - lo) < a.c.tau_l1) {
+                do_add = 1;
+                l1n = 0;
+            }
+        }
+        if (lane == 0) {
+            int ph = phase2;
+            if (e == a.c.T_e) {
+                ph = 1;
+                l1n = 0;
+            }
+            double lr_next = a.c.lr;
+            if (ph) {
+                const double span = (double)(a.c.M_e - a.c.T_e);
+                double pr = span > 0 ? (double)(e - a.c.T_e) / span : 1.0;
+                if (pr > 1.0) pr = 1.0;
+                lr_next = a.c.lr_min + (a.c.lr_p2 - a.c.lr_min) * 0.5 * (1.0 + cospi(pr));
+            }
+            st.alpha = alpha;
+            st.beta = beta;
+            st.adam_t = adam_t + 1;
+            st.do_prune = do_prune;
+            st.do_add = do_add;
+            st.l1_optim = l1n;
+            st.phase2 = ph;
+            st.lr = lr_next;
+            st.epoch = e;
+            a.stats[SERBF_STAT_L1] = l1;
+            a.stats[SERBF_STAT_ALPHA] = alpha;
+            a.stats[SERBF_STAT_BETA] = beta;
+            a.stats[SERBF_STAT_BF] = bf;
+            a.stats[SERBF_STAT_LOSS] = alpha * l2 + beta * l1;
+        }
     }
     __syncthreads();
-    double bf = 0.0;
-    for (int j = threadIdx.x; j < m; j += blockDim.x) bf += fabs((double)a.p[PW * cap + j]) >= a.c.tau_d;
-    bf = block_sum_d(bf, sh);
-    if (threadIdx.x != 0) return;
-    // epoch tail, in the order of Algorithm 3
-    st.alpha = alpha;
-    st.beta = beta;
-    st.adam_t = t;
-    st.do_prune = (e % a.c.k_l2 == 0) && st.l1_optim && (e < a.c.T_e);
-    const double l2 = a.stats[SERBF_STAT_L2];
-    const int kl2 = a.c.k_l2, kl1 = a.c.k_l1;
-    if (st.n_l2 < kl2) {
-        st.l2_hist[st.n_l2++] = l2;
-    } else {
-        for (int k = 0; k + 1 < kl2; ++k) st.l2_hist[k] = st.l2_hist[k + 1];
-        st.l2_hist[kl2 - 1] = l2;
-    }
-    if (st.n_bf < kl1) {
-        st.bf_hist[st.n_bf++] = (int32_t)bf;
-    } else {
-        for (int k = 0; k + 1 < kl1; ++k) st.bf_hist[k] = st.bf_hist[k + 1];
-        st.bf_hist[kl1 - 1] = (int32_t)bf;
-    }
-    if (!st.l1_optim && !st.phase2 && e >= kl2 && st.n_l2 == kl2) {
-        double mean = 0.0;
-        for (int k = 0; k < kl2; ++k) mean += st.l2_hist[k];
-        mean /= kl2;
-        double var = 0.0;
-        for (int k = 0; k < kl2; ++k) var += (st.l2_hist[k] - mean) * (st.l2_hist[k] - mean);
-        var /= kl2;
-        if (sqrt(var) < a.c.tau_l2) st.l1_optim = 1;
-    }
-    st.do_add = 0;
-    if (st.l1_optim && !st.phase2 && st.n_bf == kl1) {
-        int lo = st.bf_hist[0], hi = st.bf_hist[0];
-        for (int k = 1; k < kl1; ++k) {
-            lo = min(lo, st.bf_hist[k]);
-            hi = max(hi, st.bf_hist[k]);
-        }
-        if ((double)(hi - lo) < a.c.tau_l1) {
-            st.do_add = 1;
-            st.l1_optim = 0;
-        }
-    }
-    if (e == a.c.T_e) {
-        st.phase2 = 1;
-        st.l1_optim = 0;
-    }
-    if (st.phase2) {
-        const double span = (double)(a.c.M_e - a.c.T_e);
-        double pr = span > 0 ? (double)(e - a.c.T_e) / span : 1.0;
-        if (pr > 1.0) pr = 1.0;
-        st.lr = a.c.lr_min + (a.c.lr_p2 - a.c.lr_min) * 0.5 * (1.0 + cos(3.14159265358979323846 * pr));
-    } else {
-        st.lr = a.c.lr;
-    }
-    st.epoch = e;
-    *a.st = st;
-    a.stats[SERBF_STAT_L1] = l1;
-    a.stats[SERBF_STAT_ALPHA] = alpha;
-    a.stats[SERBF_STAT_BETA] = beta;
-    a.stats[SERBF_STAT_BF] = bf;
-    a.stats[SERBF_STAT_LOSS] = alpha * l2 + beta * l1;
+    uint32_t *gwo = reinterpret_cast<uint32_t *>(a.st);
+    for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) gwo[k] = s_words[k];
 }
 
 // Eq. 3-27: stable compaction of the kernels with |w| >= tau_d.
@@ -207,6 +260,8 @@ extern "C" int serbf_step(serbf_params *prm, const float *grad, float *adam_m, f
     if (!prm || !prm->p || !prm->m || prm->cap < 1 || !grad || !adam_m || !adam_v || !st_dev || !stats || !cfg)
         return SERBF_EINVAL;
     if (cfg->k_l2 < 1 || cfg->k_l2 > 64 || cfg->k_l1 < 1 || cfg->k_l1 > 256) return SERBF_EINVAL;
+    if (!(cfg->lr >= 0.0) || !(cfg->beta1 >= 0.0 && cfg->beta1 < 1.0) || !(cfg->beta2 >= 0.0 && cfg->beta2 < 1.0))
+        return SERBF_EINVAL;
     StepArgs a{prm->p, prm->m, prm->cap, grad, adam_m, adam_v, st_dev, stats, *cfg};
     k_step<<<1, kStepThreads, 0, (cudaStream_t)stream>>>(a);
     SERBF_CHECK_LAUNCH();

@@ -31,7 +31,7 @@ class Problem:
     """One field: training points, targets, kernels, optimiser state and scratch."""
 
     def __init__(self, x, y, z, S, P, m, spacing, cfg=None, cap=None, max_points=None, t=None,
-                 cell_cap=2048, super_cap=8192, super_factor=4, device="cuda"):
+                 super_cap=8192, super_factor=4, max_cells=None, device="cuda"):
         dev = torch.device(device)
         self.dev = dev
         self.cfg = cfg if cfg is not None else N.config_default()
@@ -75,7 +75,8 @@ class Problem:
         self.state = torch.zeros(N.STATE_BYTES, dtype=torch.uint8, device=dev)
         self.stats = torch.zeros(N.NSTATS, dtype=torch.float64, device=dev)
         ncell = self.grid.n[0] * self.grid.n[1] * self.grid.n[2]
-        self.sizes = N.WsSizes(self.max_points, self.cap, ncell, cell_cap, super_cap, super_factor, 0)
+        ncell = max(ncell, int(max_cells or 0))
+        self.sizes = N.WsSizes(self.max_points, self.cap, ncell, 0, super_cap, super_factor, 0)
         nbytes = N.serbf_workspace_bytes(self.sizes)
         self.ws_dev = torch.zeros(nbytes + 256, dtype=torch.uint8, device=dev)
         off = (-self.ws_dev.data_ptr()) % 256
@@ -155,6 +156,27 @@ class Problem:
         self.step()
         self.prune()
         self.add()
+
+    def capture(self):
+        """Capture one epoch as three CUDA graphs (neighbour rebuild | forward |
+        adjoint, step, deletion, addition) so that a step is three graph
+        launches.  Re-capture after binning changes (refinement)."""
+        self.epoch()  # warm up: lazy attribute setup happens outside capture
+        torch.cuda.synchronize()
+        parts = [self.build_neighbors, self.forward,
+                 lambda: (self.backward(), self.step(), self.prune(), self.add())]
+        self.graphs = []
+        for fn in parts:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                fn()
+            self.graphs.append(g)
+        torch.cuda.synchronize()
+        return self.graphs
+
+    def epoch_graph(self):
+        for g in self.graphs:
+            g.replay()
 
     # ------------------------------------------------------------ host views
     def status(self, clear=False):

@@ -233,7 +233,8 @@ def test_neighbors_match_numpy_bruteforce(orc):
 
 
 # ---------------------------------------------------------------- binning
-def test_binning_matches_lexsort(orc):
+@pytest.mark.parametrize("sf", [1, 3, 4])
+def test_binning_matches_lexsort(orc, sf):
     g = np.random.default_rng(7)
     x, y, z = (g.uniform(-1, 1, 5000).astype(np.float32) for _ in range(3))
     x[:10] = x[10:20]  # ties in the key
@@ -242,17 +243,18 @@ def test_binning_matches_lexsort(orc):
     o = np.float32(-1.05)
     h = np.float32(0.13)
     nc = 17
-    perm = orc.bin_points(x, y, z, (o, o, o), h, (nc, nc, nc))
-    f = np.float32
+    perm = orc.bin_points(x, y, z, (o, o, o), h, (nc, nc, nc), sf)
 
     def ax(v):
         k = np.floor((v - o) / h)
         return np.clip(k, 0, nc - 1).astype(np.int64)
 
-    key = (ax(z) * nc + ax(y)) * nc + ax(x)
-    ref = np.lexsort((np.arange(5000), key))
+    kx, ky, kz = ax(x), ax(y), ax(z)
+    ns = -(-nc // sf)
+    sup = ((kz // sf) * ns + ky // sf) * ns + kx // sf
+    loc = ((kz % sf) * sf + ky % sf) * sf + kx % sf
+    ref = np.lexsort((np.arange(5000), loc, sup))
     np.testing.assert_array_equal(perm, ref)
-    assert f(0.1).dtype == np.float32
 
 
 # ---------------------------------------------------------------- App. A gradients
