@@ -181,6 +181,22 @@ int serbf_state_init(serbf_state *st_dev, const serbf_config *cfg, void *stream)
 int serbf_normalize_sdf(const float *S, float *t, int64_t n, double *mh_dev, serbf_workspace *ws,
                         void *stream);
 
+/* Allocation-free form of serbf_normalize_sdf.  The paper has no counterpart;
+ * it exists for callers that cannot allocate device memory at the moment they
+ * need the normalisation, e.g. code running while a stream is being captured
+ * into a CUDA graph (cudaMalloc is not permitted during capture) or a host
+ * application that only hands out buffers from its own fixed pool.  No
+ * workspace is taken: the reduction scratch is a fixed array inside the
+ * library (16384 partial minima, 64 KiB on every device that loads it, kept
+ * until the process exits), so n is limited to 67,108,864 points; a larger n
+ * returns SERBF_ECAPACITY before anything is launched.  mh_dev (2 doubles) is
+ * required.  The first call on each device looks up the array's device
+ * address on the host; make that first call before any stream capture.
+ * Targets and m, h are identical to serbf_normalize_sdf.  All calls share the
+ * one array, so calls that can overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. */
+int serbf_normalize_sdf_noalloc(const float *S, float *t, int64_t n, double *mh_dev, void *stream);
+
 /* ------------------------------------------------------------------ a2 */
 /* Cell binning of the training points (the neighbour structure that serves
  * the support test of Eq. 3-15; the paper leaves its data structure open).

@@ -79,6 +79,7 @@ _SIGS = {
     "serbf_status": (C.c_int, [VP, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.c_int, VP]),
     "serbf_state_init": (C.c_int, [VP, C.POINTER(Config), VP]),
     "serbf_normalize_sdf": (C.c_int, [VP, VP, C.c_int64, VP, VP, VP]),
+    "serbf_normalize_sdf_noalloc": (C.c_int, [VP, VP, C.c_int64, VP, VP]),
     "serbf_bin_points": (C.c_int, [VP, VP, VP, C.c_int64, C.POINTER(Grid), VP, VP, VP, VP, VP, VP]),
     "serbf_gather": (C.c_int, [VP, VP, VP, C.c_int64, VP]),
     "serbf_build_neighbors": (C.c_int, [C.POINTER(Points), C.POINTER(Params), C.POINTER(Config),
@@ -168,6 +169,15 @@ def serbf_state_init(st, cfg, stream=None):
 def serbf_normalize_sdf(S, t, mh, ws_host, stream=None):
     return _check("serbf_normalize_sdf", _lib.serbf_normalize_sdf(_p(S), _p(t), S.numel(), _p(mh),
                                                                   C.addressof(ws_host), _stream(stream)))
+
+
+def serbf_normalize_sdf_noalloc(S, t, mh, stream=None, n=None):
+    """Eq. 3-10 without a workspace (for callers that cannot allocate device memory)."""
+    n = S.numel() if n is None else n
+    rc = _lib.serbf_normalize_sdf_noalloc(_p(S), _p(t), n, _p(mh), _stream(stream))
+    if rc == SERBF_ECAPACITY:
+        raise SerbfError("serbf_normalize_sdf_noalloc (n > 67,108,864 points)", rc)
+    return _check("serbf_normalize_sdf_noalloc", rc)
 
 
 def serbf_bin_points(x, y, z, grid, perm, xb, yb, zb, ws_host, stream=None):
