@@ -30,7 +30,7 @@ import synth  # noqa: E402
 METRIC = "ERBF fwd+bwd point-kernel pairs/s"
 UNIT = "pairs/s"
 FWD_INSTR_PER_PAIR = 17  # minimum FP32-pipe instructions of one forward pair
-LAUNCHES_PER_STEP = 13   # prep, super lists, forward, 4 adjoint, step, prune, 3 addition (3 graph launches)
+LAUNCHES_PER_STEP = 15   # prep, super lists, forward, 4 adjoint, 2 step, prune, 3 addition (3 graph launches)
 WORKLOADS = {
     "c1": ("sphere |x|-0.5 on 32^3, M=64 isotropic", None),
     "c2": ("torus R=0.5 r=0.2 on 32^3+64^3 union (after 32^3->64^3 refinement), M=512 anisotropic", [32, 64]),
@@ -115,7 +115,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def build_problem(name, device):
+SUPER_FACTOR = {"c1": 4, "c2": 4, "c3": 4, "c4": 4}
+
+
+def build_problem(name, device, sf=None):
     from paper_2505_02350_gb300 import field
     desc, layers = WORKLOADS[name]
     cfg, lay, P = synth.workload(name, layers=layers)
@@ -124,7 +127,9 @@ def build_problem(name, device):
     z = np.concatenate([l[2] for l in lay])
     S = np.concatenate([l[3] for l in lay])
     grids = cfg["grids"] if layers is None else layers
-    pb = field.Problem(x, y, z, S, P, cfg["m"], synth.spacing(max(grids)), cap=2 * cfg["m"], device=device)
+    sf = SUPER_FACTOR[name] if sf is None else sf
+    pb = field.Problem(x, y, z, S, P, cfg["m"], synth.spacing(max(grids)), cap=2 * cfg["m"], device=device,
+                       super_factor=sf)
     return pb, desc
 
 
@@ -133,7 +138,7 @@ def run_native(args, ws, rank, local):
     import torch.distributed as dist
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    pb, desc = build_problem(args.config, dev)
+    pb, desc = build_problem(args.config, dev, args.sf)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB of L2
     for _ in range(args.warmup):
         pb.epoch()
@@ -209,6 +214,7 @@ def run_native(args, ws, rank, local):
         "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "config": args.config, "points": n, "kernels": pb.m(),
+                   "super_factor": pb.sizes.super_factor,
                    "pairs_fwd_per_step": float(pf.mean()), "pairs_bwd_per_step": float(pbk.mean()),
                    "l2_flush": "256 MiB buffer written between timed steps", "parallelism": "replicas"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 128},
@@ -282,6 +288,7 @@ def main():
     ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sf", type=int, default=None, help="cells per super-cell edge (default per workload)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -261,9 +261,9 @@ int serbf_backward(const serbf_points *pts, const serbf_params *prm, const serbf
  * add_activate, switch to the L2-only phase with a cosine learning rate at
  * T^e).  grad holds the raw L2 gradients from serbf_backward and is not
  * modified.  adam_m / adam_v are 10 x cap.  Writes stats[L1, ALPHA, BETA, BF,
- * LOSS].  One launch. */
+ * LOSS].  Two launches; ws holds the reduction scratch. */
 int serbf_step(serbf_params *prm, const float *grad, float *adam_m, float *adam_v, serbf_state *st_dev,
-               double *stats, const serbf_config *cfg, void *stream);
+               double *stats, const serbf_config *cfg, serbf_workspace *ws, void *stream);
 
 /* ------------------------------------------------------------------ a7 */
 /* Eq. 3-27: when st->do_prune is set, removes every kernel with |w| < tau_d

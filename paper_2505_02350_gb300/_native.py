@@ -88,7 +88,7 @@ _SIGS = {
                                 VP, VP]),
     "serbf_backward": (C.c_int, [C.POINTER(Points), C.POINTER(Params), C.POINTER(Config), VP, VP, VP, VP,
                                  VP]),
-    "serbf_step": (C.c_int, [C.POINTER(Params), VP, VP, VP, VP, VP, C.POINTER(Config), VP]),
+    "serbf_step": (C.c_int, [C.POINTER(Params), VP, VP, VP, VP, VP, C.POINTER(Config), VP, VP]),
     "serbf_prune": (C.c_int, [C.POINTER(Params), VP, VP, VP, C.POINTER(Config), VP]),
     "serbf_add_kernels": (C.c_int, [C.POINTER(Points), VP, VP, VP, C.POINTER(Params), VP, VP, VP, VP,
                                     C.POINTER(Config), C.c_int, VP, VP]),
@@ -224,9 +224,9 @@ def serbf_backward(pts, prm, cfg, err, grad, stats, ws_host, stream=None):
                                                         _stream(stream)))
 
 
-def serbf_step(prm, grad, adam_m, adam_v, st, stats, cfg, stream=None):
+def serbf_step(prm, grad, adam_m, adam_v, st, stats, cfg, ws_host, stream=None):
     return _check("serbf_step", _lib.serbf_step(C.byref(prm), _p(grad), _p(adam_m), _p(adam_v), _p(st), _p(stats),
-                                                C.byref(cfg), _stream(stream)))
+                                                C.byref(cfg), C.addressof(ws_host), _stream(stream)))
 
 
 def serbf_prune(prm, adam_m, adam_v, st, cfg, stream=None):

@@ -71,6 +71,8 @@ void carve(Carver &c, serbf_workspace *w, const serbf_ws_sizes *s) {
     w->nzt = c.take<uint32_t>(T);
     w->nzt_cnt = c.take<uint32_t>(S);
     w->nz = c.take<float4>(T * kTile);
+    w->step_part = c.take<float>(6 * (SERBF_NPARAM * (K / 256 + 1) + 1));
+    w->step_scal = c.take<double>(8);
     w->sel_key = c.take<unsigned long long>(K8);
     w->sel_keep = c.take<uint32_t>(K8);
     w->add_info = c.take<int32_t>(16);

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_moments(BwdArgs a) {
     int head = 0, qn = 0;
     uint32_t *q = ring[warp];
     // the kernel's super cells are dealt round-robin to all warps of its kBwdSplit blocks
-    for (int sb = split * NW + warp; sb < nsb; sb += NW * kBwdSplit) {
+    for (int sb = split * NW + warp; sb < nsb; sb += NW * gridDim.y) {
         const int sx = sx0 + sb % nbx, sy = sy0 + (sb / nbx) % nby, sz = sz0 + sb / (nbx * nby);
         const int s = (sz * a.nsy + sy) * a.nsx + sx;
         if (!(box_d2(k0.x, k0.y, k0.z, a.slo[s], a.shi[s]) < k0.w)) continue;
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_moments(BwdArgs a) {
     if (lane + 32 < qn) accumulate<KAHAN>(a.nz[q[(head + 32 + lane) & (RING - 1)]], k0, k1, k2, k3, acc, cmp, pairs);
     // this warp's share of the kernel's moments: a float-float shuffle tree
     // over the lanes, written to the warp's slot (no atomics, no block barrier)
-    const int slot = split * NW + warp;
+    const int slot = split * NW + warp;  // < gridDim.y * NW <= kBwdWarpsPerKernel
     float *o = a.mom + ((int64_t)j * kBwdWarpsPerKernel + slot) * 22;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -193,21 +193,22 @@ __global__ void __launch_bounds__(kBwdThreads) k_moments(BwdArgs a) {
 // One warp per kernel: the kBwdWarpsPerKernel partial moments are summed in a
 // fixed order (float-float shuffle tree), then lane 0 evaluates the ten App. A
 // gradients; the pair count total is a fixed-order sum by the last block.
-__global__ void k_grad_epilogue(const float *p, const int32_t *m_dev, int cap, const float *mom, float *grad,
-                                unsigned long long *pairs, uint32_t *counter, double *stats) {
+__global__ void k_grad_epilogue(const float *p, const int32_t *m_dev, int cap, const float *mom, int nparts,
+                                float *grad, unsigned long long *pairs, uint32_t *counter, double *stats) {
     __shared__ bool s_last;
     __shared__ unsigned long long red[32];
     const int m = *m_dev;
     const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (j < m) {
         const float *o = mom + ((int64_t)j * kBwdWarpsPerKernel + lane) * 22;
+        const bool has = lane < nparts;
         float M[10];
 #pragma unroll
         for (int r = 0; r < 10; ++r) {
-            const ff v = warp_sum_ff(ff{o[2 * r], o[2 * r + 1]});
+            const ff v = warp_sum_ff(has ? ff{o[2 * r], o[2 * r + 1]} : ff{0.f, 0.f});
             M[r] = v.hi + v.lo;
         }
-        const uint32_t np = warp_sum(__float_as_uint(o[20]));
+        const uint32_t np = warp_sum(has ? __float_as_uint(o[20]) : 0u);
         if (lane == 0) {
             pairs[j] = np;
             const float w = p[PW * cap + j];
@@ -307,12 +308,18 @@ extern "C" int serbf_backward(const serbf_points *pts, const serbf_params *prm, 
     a.nzt_cnt = ws->nzt_cnt;
     a.nz = ws->nz;
     a.mom = ws->moments;
-    const dim3 grid((unsigned)prm->cap, kBwdSplit);
+    // enough warps in flight: split a kernel's super cells over more blocks when
+    // there are few kernels, fewer when there are many (each split adds a
+    // per-warp reduction of ten moments)
+    int splits = (int)(10240 / ((int64_t)prm->cap * (kBwdThreads / 32)));
+    splits = splits < 1 ? 1 : (splits > kBwdSplit ? kBwdSplit : splits);
+    const dim3 grid((unsigned)prm->cap, (unsigned)splits);
     if (cfg->kahan)
         k_moments<true><<<grid, kBwdThreads, 0, s>>>(a);
     else
         k_moments<false><<<grid, kBwdThreads, 0, s>>>(a);
-    k_grad_epilogue<<<(prm->cap + 7) / 8, 256, 0, s>>>(prm->p, prm->m, prm->cap, ws->moments, grad,
+    k_grad_epilogue<<<(prm->cap + 7) / 8, 256, 0, s>>>(prm->p, prm->m, prm->cap, ws->moments,
+                                                        splits * (kBwdThreads / 32), grad,
                                                            ws->bwd_pairs, ws->counters + 1, stats);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;

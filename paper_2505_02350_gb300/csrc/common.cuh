@@ -15,7 +15,7 @@ constexpr int kSortTile = 4096;                   // elements per radix-sort blo
 constexpr int kFwdWarps = 2;                      // warps (tiles) per forward block
 constexpr int kQueue = 64;                        // per-warp ring of staged candidates
 constexpr int kBwdThreads = 64;                   // threads per adjoint block
-constexpr int kBwdSplit = 16;                     // blocks per kernel in the adjoint
+constexpr int kBwdSplit = 16;                     // most blocks per kernel in the adjoint
 constexpr int kBwdWarpsPerKernel = kBwdSplit * kBwdThreads / 32;  // == 32, one epilogue lane each
 constexpr int kMaxRowsPerKernel = 1 << 16;        // cell rows a kernel support may span
 constexpr float kLog2e = 1.4426950408889634f;
@@ -70,6 +70,9 @@ struct serbf_workspace {
     uint32_t *nzt;      // per super cell: ids of its tiles with nonzero residuals (in its tile range)
     uint32_t *nzt_cnt;  // per super cell: number of such tiles
     float4 *nz;         // 32 slots per tile: (x, y, z, E) of its nonzero-residual points
+    // optimiser step scratch
+    float *step_part;   // per-block partial sums
+    double *step_scal;  // alpha, beta, Adam bias corrections
     // addition scratch
     unsigned long long *sel_key;  // max(max_kernels, 8192)
     uint32_t *sel_keep;           // max(max_kernels, 8192)

@@ -1,8 +1,9 @@
-// Algorithm 3 update for one full-batch epoch: Eq. 3-21 dynamic weighting
-// (double reductions), Adam, and the epoch-tail gates (Eq. 3-27 deletion due,
-// Eq. l1_activate, Eq. add_activate, L2-only phase with a cosine learning rate
-// from T^e).  A single block: the state machine lives on the device so that a
-// step needs no host round trip.  Also the Eq. 3-27 compaction.
+// Algorithm 3 update for one full-batch epoch: Eq. 3-21 dynamic weighting,
+// Adam, and the epoch-tail gates (Eq. 3-27 deletion due, Eq. l1_activate,
+// Eq. add_activate, L2-only phase with a cosine learning rate from T^e).  Two
+// grid-wide launches whose last blocks finish the reductions: the state
+// machine lives on the device so that a step needs no host round trip.  Also
+// the Eq. 3-27 compaction.
 #include <math.h>
 
 #include "common.cuh"
@@ -15,7 +16,7 @@ constexpr int kStepThreads = 256;
 
 // Block sums of NV float values with float-float trees (FP64 is slow here).
 template <int NV>
-__device__ void block_sums(const float (&v)[NV], ff (*sh)[NV], double (&out)[NV]) {
+__device__ void block_sums_ff(const float (&v)[NV], ff (*sh)[NV], ff (&out)[NV]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
@@ -33,7 +34,31 @@ __device__ void block_sums(const float (&v)[NV], ff (*sh)[NV], double (&out)[NV]
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < NV; ++k) out[k] = (double)sh[32][k].hi + (double)sh[32][k].lo;
+    for (int k = 0; k < NV; ++k) out[k] = sh[32][k];
+    __syncthreads();
+}
+
+// Same for three float-float inputs.
+__device__ void block_sums_ff3(const ff (&v)[3], ff (*sh)[3], ff (&out)[3]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const ff s = warp_sum_ff(v[k]);
+        if (lane == 0) sh[warp][k] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            ff t = lane < nw ? sh[lane][k] : ff{0.f, 0.f};
+            t = warp_sum_ff(t);
+            if (lane == 0) sh[32][k] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[k] = sh[32][k];
+    __syncthreads();
 }
 
 __device__ __forceinline__ float sgnf(float v) { return (float)((v > 0.f) - (v < 0.f)); }
@@ -47,97 +72,126 @@ struct StepArgs {
     serbf_state *st;
     double *stats;
     serbf_config c;
+    float *part;      // per block partial sums (float-float pairs)
+    double *scal;     // alpha, beta, bias corrections for the update kernel
+    uint32_t *counter;
 };
 
 constexpr int kStateWords = (int)(sizeof(serbf_state) / 4);
 static_assert(sizeof(serbf_state) % 8 == 0, "state is copied as 32-bit words");
 
-__global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
+// Stage 1 of the update (one thread per kernel, many blocks): L1 = sum |w|
+// (Eq. 3-14_2) and the two Eq. 3-21 dot products; the last block turns them
+// into alpha and beta and the Adam bias corrections.
+__global__ void __launch_bounds__(kStepThreads) k_step_alpha(StepArgs a) {
     __shared__ ff sh3[33][3];
-    __shared__ ff sh1[33][1];
-    __shared__ double s_alpha;
-    __shared__ float s_bc[2];
-    __shared__ __align__(8) uint32_t s_words[kStateWords];
-    serbf_state &st = *reinterpret_cast<serbf_state *>(s_words);
-    // the whole state comes in with one cooperative round trip
-    const uint32_t *gw = reinterpret_cast<const uint32_t *>(a.st);
-    for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) s_words[k] = gw[k];
+    __shared__ bool s_last;
     const int m = *a.m, cap = a.cap;
-    const double l2 = a.stats[SERBF_STAT_L2], maxe = a.stats[SERBF_STAT_MAXE];
-    __syncthreads();
-    const int epoch = st.epoch, adam_t = st.adam_t, l1_optim = st.l1_optim;
-    const float lr = (float)st.lr;
-    const bool use_l1 = l1_optim && (maxe < a.c.tau_m);
-    // L1 = sum |w| before the update (Eq. 3-14_2) and the Eq. 3-21 dot products
+    const bool use_l1 = a.st->l1_optim && (a.stats[SERBF_STAT_MAXE] < a.c.tau_m);
     float part[3] = {0.f, 0.f, 0.f};
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) {
         const float w = a.p[PW * cap + j], g2 = a.grad[PW * cap + j];
-        part[0] += fabsf(w);
+        part[0] = fabsf(w);
         if (use_l1) {
             const float g1 = sgnf(w);
-            part[1] = fmaf(g1 - g2, g1, part[1]);
-            part[2] = fmaf(g2 - g1, g2 - g1, part[2]);
+            part[1] = (g1 - g2) * g1;
+            part[2] = (g2 - g1) * (g2 - g1);
         }
     }
-    double sums[3];
-    block_sums<3>(part, sh3, sums);
-    const double l1 = sums[0], num = sums[1], den = sums[2];
+    ff tot[3];
+    block_sums_ff<3>(part, sh3, tot);
     if (threadIdx.x == 0) {
-        double al = 1.0;
-        if (use_l1 && den > 0.0) al = fmin(1.0, fmax(0.0, num / den));
-        s_alpha = al;
-        s_bc[0] = 1.f - powf((float)a.c.beta1, (float)(adam_t + 1));
-        s_bc[1] = 1.f - powf((float)a.c.beta2, (float)(adam_t + 1));
+        float *o = a.part + 6 * blockIdx.x;
+        for (int k = 0; k < 3; ++k) {
+            o[2 * k] = tot[k].hi;
+            o[2 * k + 1] = tot[k].lo;
+        }
+        __threadfence();
+        s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    const double alpha = s_alpha, beta = 1.0 - alpha;
+    if (!s_last) return;
+    __threadfence();
+    ff acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+        for (int k = 0; k < 3; ++k)
+            acc[k] = ff_add(acc[k], ff{__ldcg(a.part + 6 * b + 2 * k), __ldcg(a.part + 6 * b + 2 * k + 1)});
+    ff fin[3];
+    block_sums_ff3(acc, sh3, fin);
+    if (threadIdx.x == 0) {
+        const double l1 = (double)fin[0].hi + fin[0].lo, num = (double)fin[1].hi + fin[1].lo;
+        const double den = (double)fin[2].hi + fin[2].lo;
+        double al = 1.0;
+        if (use_l1 && den > 0.0) al = fmin(1.0, fmax(0.0, num / den));
+        const int t = a.st->adam_t + 1;
+        a.scal[0] = al;
+        a.scal[1] = 1.0 - al;
+        a.scal[2] = 1.0 - pow(a.c.beta1, t);
+        a.scal[3] = 1.0 - pow(a.c.beta2, t);
+        a.stats[SERBF_STAT_L1] = l1;
+        a.stats[SERBF_STAT_ALPHA] = al;
+        a.stats[SERBF_STAT_BETA] = 1.0 - al;
+        *a.counter = 0u;
+    }
+}
+
+// Stage 2 (one thread per parameter, many blocks): the combined gradient of
+// Eq. grad (App. A) and the Adam update; then the last block runs the epoch
+// tail of Algorithm 3 on a shared-memory copy of the state.
+__global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
+    __shared__ ff sh1[33][1];
+    __shared__ bool s_last;
+    __shared__ __align__(8) uint32_t s_words[kStateWords];
+    const int m = *a.m, cap = a.cap;
+    const int r = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+    const double alpha = a.scal[0], beta = a.scal[1];
+    const float bc1 = (float)a.scal[2], bc2 = (float)a.scal[3];
+    const float lr = (float)a.st->lr;
     const float b1 = (float)a.c.beta1, b2 = (float)a.c.beta2, eps = (float)a.c.adam_eps;
-    const float bc1 = s_bc[0], bc2 = s_bc[1];
-    const float fa = (float)alpha, fb = (float)beta;
     // b_f: |w| >= tau_d decided in float with tau_d rounded up (same decision as in double)
     float taud = (float)a.c.tau_d;
     if ((double)taud < a.c.tau_d) taud = nextafterf(taud, INFINITY);
     float bfc[1] = {0.f};
-    // Adam on all ten parameter rows (App. A gradient combination); every
-    // thread loads its kernel's 40 values before computing, so the memory
-    // latency is paid once per kernel rather than once per row
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        float g[SERBF_NPARAM], pv[SERBF_NPARAM], mv[SERBF_NPARAM], vv[SERBF_NPARAM];
-#pragma unroll
-        for (int r = 0; r < SERBF_NPARAM; ++r) {
-            const int64_t q = (int64_t)r * cap + j;
-            g[r] = a.grad[q];
-            pv[r] = a.p[q];
-            mv[r] = a.am[q];
-            vv[r] = a.av[q];
-        }
-#pragma unroll
-        for (int r = 0; r < SERBF_NPARAM; ++r) {
-            float gr = fa * g[r];
-            if (r == PW) gr = fmaf(fb, sgnf(pv[r]), gr);
-            mv[r] = fmaf(b1, mv[r], (1.f - b1) * gr);
-            vv[r] = fmaf(b2, vv[r], (1.f - b2) * gr * gr);
-            pv[r] -= lr * (mv[r] / bc1) / (sqrtf(vv[r] / bc2) + eps);
-        }
-#pragma unroll
-        for (int r = 0; r < SERBF_NPARAM; ++r) {
-            const int64_t q = (int64_t)r * cap + j;
-            a.am[q] = mv[r];
-            a.av[q] = vv[r];
-            a.p[q] = pv[r];
-        }
-        bfc[0] += fabsf(pv[PW]) >= taud ? 1.f : 0.f;
+    if (j < m) {
+        const int64_t q = (int64_t)r * cap + j;
+        const float pv = a.p[q];
+        float g = (float)alpha * a.grad[q];
+        if (r == PW) g = fmaf((float)beta, sgnf(pv), g);
+        const float mo = fmaf(b1, a.am[q], (1.f - b1) * g);
+        const float vo = fmaf(b2, a.av[q], (1.f - b2) * g * g);
+        const float pn = pv - lr * (mo / bc1) / (sqrtf(vo / bc2) + eps);
+        a.am[q] = mo;
+        a.av[q] = vo;
+        a.p[q] = pn;
+        if (r == PW) bfc[0] = fabsf(pn) >= taud ? 1.f : 0.f;
     }
-    double bfs[1];
-    block_sums<1>(bfc, sh1, bfs);
-    const double bf = bfs[0];
-    // epoch tail in the order of Algorithm 3 (warp 0, on the shared copy);
-    // histories are rings indexed by (epoch - 1) mod window
+    ff tot[1];
+    block_sums_ff<1>(bfc, sh1, tot);
+    const unsigned nblocks = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) {
+        a.part[bid] = tot[0].hi;
+        __threadfence();
+        s_last = atomicAdd(a.counter + 1, 1u) == nblocks - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the last block: b_f, then the epoch tail (warp 0) on a shared copy of the state
+    const uint32_t *gw = reinterpret_cast<const uint32_t *>(a.st);
+    for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) s_words[k] = gw[k];
+    float cnt = 0.f;
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) cnt += __ldcg(a.part + b);
+    float cc[1] = {cnt};
+    block_sums_ff<1>(cc, sh1, tot);
+    const double bf = (double)tot[0].hi + tot[0].lo;
+    serbf_state &st = *reinterpret_cast<serbf_state *>(s_words);
+    const double l2 = a.stats[SERBF_STAT_L2];
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x;
-        const int e = epoch + 1;
+        const int e = st.epoch + 1;
         const int kl2 = a.c.k_l2, kl1 = a.c.k_l1;
-        int l1n = l1_optim;
+        int l1n = st.l1_optim;
         const int phase2 = st.phase2;
         if (lane == 0) {
             st.l2_hist[(e - 1) % kl2] = l2;
@@ -189,18 +243,16 @@ __global__ void __launch_bounds__(kStepThreads) k_step(StepArgs a) {
             }
             st.alpha = alpha;
             st.beta = beta;
-            st.adam_t = adam_t + 1;
+            st.adam_t = st.adam_t + 1;
             st.do_prune = do_prune;
             st.do_add = do_add;
             st.l1_optim = l1n;
             st.phase2 = ph;
             st.lr = lr_next;
             st.epoch = e;
-            a.stats[SERBF_STAT_L1] = l1;
-            a.stats[SERBF_STAT_ALPHA] = alpha;
-            a.stats[SERBF_STAT_BETA] = beta;
             a.stats[SERBF_STAT_BF] = bf;
-            a.stats[SERBF_STAT_LOSS] = alpha * l2 + beta * l1;
+            a.stats[SERBF_STAT_LOSS] = alpha * l2 + beta * a.stats[SERBF_STAT_L1];
+            a.counter[1] = 0u;
         }
     }
     __syncthreads();
@@ -256,14 +308,19 @@ __global__ void __launch_bounds__(kStepThreads) k_prune(float *p, float *am, flo
 }  // namespace
 
 extern "C" int serbf_step(serbf_params *prm, const float *grad, float *adam_m, float *adam_v, serbf_state *st_dev,
-                          double *stats, const serbf_config *cfg, void *stream) {
+                          double *stats, const serbf_config *cfg, serbf_workspace *ws, void *stream) {
     if (!prm || !prm->p || !prm->m || prm->cap < 1 || !grad || !adam_m || !adam_v || !st_dev || !stats || !cfg)
         return SERBF_EINVAL;
+    if (!ws || ws->magic != kMagic || prm->cap > ws->sz.max_kernels) return SERBF_EINVAL;
     if (cfg->k_l2 < 1 || cfg->k_l2 > 64 || cfg->k_l1 < 1 || cfg->k_l1 > 256) return SERBF_EINVAL;
     if (!(cfg->lr >= 0.0) || !(cfg->beta1 >= 0.0 && cfg->beta1 < 1.0) || !(cfg->beta2 >= 0.0 && cfg->beta2 < 1.0))
         return SERBF_EINVAL;
-    StepArgs a{prm->p, prm->m, prm->cap, grad, adam_m, adam_v, st_dev, stats, *cfg};
-    k_step<<<1, kStepThreads, 0, (cudaStream_t)stream>>>(a);
+    StepArgs a{prm->p, prm->m, prm->cap, grad, adam_m, adam_v, st_dev, stats, *cfg,
+               ws->step_part, ws->step_scal, ws->counters + 2};
+    cudaStream_t s = (cudaStream_t)stream;
+    const unsigned nb = (unsigned)((prm->cap + kStepThreads - 1) / kStepThreads);
+    k_step_alpha<<<nb, kStepThreads, 0, s>>>(a);
+    k_step_adam<<<dim3(nb, SERBF_NPARAM), kStepThreads, 0, s>>>(a);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;
 }

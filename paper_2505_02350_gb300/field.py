@@ -138,7 +138,7 @@ class Problem:
                          self.stats, self.ws)
 
     def step(self):
-        N.serbf_step(self.prm, self.grad, self.adam_m, self.adam_v, self.state, self.stats, self.cfg)
+        N.serbf_step(self.prm, self.grad, self.adam_m, self.adam_v, self.state, self.stats, self.cfg, self.ws)
 
     def prune(self):
         N.serbf_prune(self.prm, self.adam_m, self.adam_v, self.state, self.cfg)

@@ -71,7 +71,7 @@ def test_entry_points_reject_null_arguments_before_any_launch(native):
     E = native.SERBF_EINVAL
     assert L.serbf_forward(None, None, None, None, None, None, None, None, None) == E
     assert L.serbf_backward(None, None, None, None, None, None, None, None) == E
-    assert L.serbf_step(None, None, None, None, None, None, None, None) == E
+    assert L.serbf_step(None, None, None, None, None, None, None, None, None) == E
     assert L.serbf_prune(None, None, None, None, None, None) == E
     assert L.serbf_build_neighbors(None, None, None, None, None, None, None, None) == E
     assert L.serbf_add_kernels(None, None, None, None, None, None, None, None, None, None, 0, None, None) == E

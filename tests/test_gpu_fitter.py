@@ -1,0 +1,75 @@
+"""Algorithm 3 trajectories (parity unpinned: FP32 and FP64 runs drift apart,
+so only the outcome is compared).  The device-side driver on the sphere
+workload must reduce the loss the way the FP64 oracle's Algorithm 3 does."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_run(orc, x, y, z, t, S, P0, m, epochs, cfg_dev):
+    cap = P0.shape[1]
+    P = P0.astype(np.float64).copy()
+    mo = np.zeros_like(P)
+    v = np.zeros_like(P)
+    cfg = orc.default_cfg()
+    st = orc.state_init(cfg)
+    hist = []
+    r2 = np.float32(cfg_dev.add_radius * cfg_dev.add_radius)
+    for e in range(epochs):
+        Pf = P[:, :m].astype(np.float32).astype(np.float64)
+        psi, err, mask, s = orc.forward(x, y, z, t, Pf, m)
+        g, _ = orc.backward(x, y, z, err, Pf, m)
+        hist.append(s[0] / max(s[3], 1))
+        orc.step(P, m, g, mo, v, s[0], s[2], cfg, st)
+        if st.do_prune:
+            m = orc.prune(P, m, cfg.tau_d, mo=mo, v=v)
+            st.do_prune = 0
+        if st.do_add:
+            Ef = err.astype(np.float32)
+            k = math.ceil(0.01 * s[3])
+            cand = orc.select_topk(Ef, mask, cfg.tau_m / 2, k)
+            ext = orc.local_max(x, y, z, Ef, mask, cand, r2)
+            for i in ext:
+                if m >= cap:
+                    break
+                dbar = max(abs(float(S[i])), cfg_dev.dbar_min)
+                P[:, m] = orc.new_kernel((x[i], y[i], z[i]), Ef[i], dbar)
+                m += 1
+            mo[:] = 0
+            v[:] = 0
+            st.adam_t = 0
+            st.do_add = 0
+    return np.array(hist), m
+
+
+def test_sphere_fit_tracks_oracle(orc):
+    torch = torch_cuda()
+    from paper_2505_02350_gb300 import build, field
+    from paper_2505_02350_gb300.fitter import Fitter
+    build.build()
+    cfg, lay, P = synth.workload("c1")
+    x, y, z, S = lay[0]
+    pb = field.Problem(x, y, z, S, P, cfg["m"], synth.spacing(32), cap=256)
+    fit = Fitter(pb)
+    hist = fit.run(200, log_every=1)
+    msq_gpu = np.array([h["l2"] / max(h["count"], 1) for h in hist])
+    assert np.all(np.isfinite(msq_gpu))
+    h = pb.binned_host()
+    P0 = np.zeros((10, 256))
+    P0[:, :cfg["m"]] = P[:, :cfg["m"]]
+    ref, m_or = _oracle_run(orc, h["x"], h["y"], h["z"], h["t"], h["S"], P0, cfg["m"], 200, pb.cfg)
+    # the loss falls by the same order of magnitude on both sides; additions
+    # make the loss jump for a few epochs at slightly different times, so the
+    # best value of the last 40 epochs is compared
+    assert msq_gpu[-40:].min() < 0.01 * msq_gpu[0]
+    assert ref[-40:].min() < 0.01 * ref[0]
+    ratio = msq_gpu[-40:].min() / ref[-40:].min()
+    assert 1 / 3 < ratio < 3.0, (msq_gpu[-40:].min(), ref[-40:].min())
+    # before the gates fire the two runs agree closely (FP32 vs FP64 drift)
+    np.testing.assert_allclose(msq_gpu[:40], ref[:40], rtol=1e-4)
