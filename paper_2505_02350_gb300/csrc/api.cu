@@ -64,12 +64,13 @@ void carve(Carver &c, serbf_workspace *w, const serbf_ws_sizes *s) {
     w->kbwd = c.take<float4>(4 * K);
     w->sup_list = c.take<uint32_t>(S * (int64_t)s->super_cap);
     w->sup_cnt = c.take<uint32_t>(S);
-    w->fwd_part = c.take<FwdPart>(T / kFwdWarps + 2);
+    w->fwd_part = c.take<FwdPart>(T + 1);
+    w->fwd_gpart = c.take<FwdPart>(T / kFwdGroup + 2);
+    w->fwd_group_done = c.take<uint32_t>(T / kFwdGroup + 2);
     w->bwd_pairs = c.take<unsigned long long>(K);
     w->moments = c.take<float>((int64_t)K * kBwdWarpsPerKernel * 22);
-    w->tile_cnt = c.take<uint32_t>(T);
-    w->nzt = c.take<uint32_t>(T);
-    w->nzt_cnt = c.take<uint32_t>(S);
+    w->nzrec = c.take<float4>(2 * T);
+    w->nzc_cnt = c.take<uint32_t>(T);
     w->nz = c.take<float4>(T * kTile);
     w->step_part = c.take<float>(6 * (SERBF_NPARAM * (K / 256 + 1) + 1));
     w->step_scal = c.take<double>(8);
@@ -272,6 +273,15 @@ int serbf_workspace_init(serbf_workspace *ws, void *dev, size_t bytes, const ser
     if (cudaMemset(ws->status, 0, 16 * sizeof(int32_t)) != cudaSuccess) return SERBF_ECUDA;
     if (cudaMemset(ws->needed, 0, 4 * sizeof(long long)) != cudaSuccess) return SERBF_ECUDA;
     if (cudaMemset(ws->counters, 0, 16 * sizeof(uint32_t)) != cudaSuccess) return SERBF_ECUDA;
+    if (cudaMemset(ws->fwd_group_done, 0, sizeof(uint32_t) * (size_t)(ws->max_tiles / kFwdGroup + 2)) !=
+        cudaSuccess)
+        return SERBF_ECUDA;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return SERBF_ECUDA;
+        if (cudaDeviceGetAttribute(&ws->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return SERBF_ECUDA;
+    }
     if (cudaMemset(ws->add_info, 0, 16 * sizeof(int32_t)) != cudaSuccess) return SERBF_ECUDA;
     if (cudaDeviceSynchronize() != cudaSuccess) return SERBF_ECUDA;
     return SERBF_OK;

@@ -26,38 +26,46 @@ static_assert(kBwdWarpsPerKernel == 32, "the epilogue reduces one partial per la
 
 namespace {
 
-// One warp per tile: compact the nonzero-residual points into the tile's slots.
-__global__ void k_nz_tiles(const float *x, const float *y, const float *z, const float *err,
-                           const uint32_t *tile_super, const uint32_t *tile_start, const uint32_t *cell_start, int cps,
-                           int64_t ntiles, uint32_t *tile_cnt, float4 *nz) {
-    int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (t >= ntiles) return;
-    uint32_t sup = tile_super[t], p0 = tile_start[t], pe = cell_start[(int64_t)(sup + 1) * cps];
-    uint32_t i = p0 + lane;
-    float e = i < pe ? err[i] : 0.f;
-    bool v = e != 0.f;
-    unsigned bal = __ballot_sync(0xffffffffu, v);
-    if (v) nz[t * kTile + __popc(bal & ((1u << lane) - 1u))] = make_float4(x[i], y[i], z[i], e);
-    if (lane == 0) tile_cnt[t] = __popc(bal);
-}
-
-// One warp per super cell: list its tiles that hold nonzero residuals (in
-// order, in place at the start of the super cell's tile range) and count them.
-__global__ void k_nz_super(const uint32_t *stile0, int nsuper, const uint32_t *tile_cnt, uint32_t *nzt,
-                           uint32_t *nzt_cnt) {
-    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (s >= nsuper) return;
+// One block per (32-tile chunk, super cell), one warp per tile: compact the
+// tile's nonzero-residual points into its 32 slots (x, y, z, E), then warp 0
+// packs the chunk's tiles that hold any as two float4 records -- (box lo,
+// count) and (box hi, tile id) -- at the chunk's own record slots, so the
+// adjoint reads a candidate tile's test data in one round trip.
+__global__ void __launch_bounds__(1024) k_nz_compact(const float *x, const float *y, const float *z, const float *err,
+                                                     const uint32_t *stile0, const uint32_t *tile_start,
+                                                     const uint32_t *cell_start, int cps, const float4 *tlo,
+                                                     const float4 *thi, float4 *nz, float4 *rec, uint32_t *ccnt) {
+    __shared__ uint32_t cnt[32];
+    const int s = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t t0 = stile0[s], t1 = stile0[s + 1];
-    uint32_t n = 0;
-    for (uint32_t tb = t0; tb < t1; tb += 32) {
-        const uint32_t t = tb + lane;
-        const bool v = t < t1 && tile_cnt[t] != 0;
+    const uint32_t cb = t0 + blockIdx.x * 32u;
+    if (cb >= t1) return;
+    const uint32_t t = cb + warp;
+    uint32_t c = 0;
+    if (t < t1) {
+        const uint32_t pe = cell_start[(int64_t)(s + 1) * cps];
+        const uint32_t i = tile_start[t] + lane;
+        const float e = i < pe ? err[i] : 0.f;
+        const bool v = e != 0.f;
         const unsigned bal = __ballot_sync(0xffffffffu, v);
-        if (v) nzt[t0 + n + __popc(bal & ((1u << lane) - 1u))] = t;
-        n += __popc(bal);
+        if (v) nz[(size_t)t * kTile + __popc(bal & ((1u << lane) - 1u))] = make_float4(x[i], y[i], z[i], e);
+        c = __popc(bal);
     }
-    if (lane == 0) nzt_cnt[s] = n;
+    if (lane == 0) cnt[warp] = c;
+    __syncthreads();
+    if (warp != 0) return;
+    const uint32_t tt = cb + lane;
+    const uint32_t cl = cnt[lane];
+    const unsigned bal = __ballot_sync(0xffffffffu, cl != 0);
+    if (cl) {
+        const uint32_t o = cb + __popc(bal & ((1u << lane) - 1u));
+        float4 lo = tlo[tt], hi = thi[tt];
+        lo.w = __uint_as_float(cl);
+        hi.w = __uint_as_float(tt);
+        rec[2 * (size_t)o] = lo;
+        rec[2 * (size_t)o + 1] = hi;
+    }
+    if (lane == 0) ccnt[cb] = __popc(bal);
 }
 
 struct BwdArgs {
@@ -69,8 +77,8 @@ struct BwdArgs {
     const float4 *slo, *shi;
     const uint32_t *stile0;
     const float4 *tlo, *thi;
-    const uint32_t *tile_cnt;
-    const uint32_t *nzt, *nzt_cnt;  // per super cell: tiles with nonzero residuals
+    const float4 *nzrec;   // packed records of tiles with nonzero residuals, per 32-tile chunk
+    const uint32_t *nzc;   // records per chunk, indexed by the chunk's first tile
     const float4 *nz;
     float *mom;  // per kernel, per warp: 10 float-float moments S0, M1 (3), M2 (6), then the pair count (bits)
 };
@@ -138,49 +146,90 @@ __global__ void __launch_bounds__(kBwdThreads) k_moments(BwdArgs a) {
     const int nsb = nbx * nby * nbz;
     int head = 0, qn = 0;
     uint32_t *q = ring[warp];
-    // the kernel's super cells are dealt round-robin to all warps of its kBwdSplit blocks
-    for (int sb = split * NW + warp; sb < nsb; sb += NW * gridDim.y) {
-        const int sx = sx0 + sb % nbx, sy = sy0 + (sb / nbx) % nby, sz = sz0 + sb / (nbx * nby);
-        const int s = (sz * a.nsy + sy) * a.nsx + sx;
-        if (!(box_d2(k0.x, k0.y, k0.z, a.slo[s], a.shi[s]) < k0.w)) continue;
-        const uint32_t t0 = a.stile0[s], t1 = t0 + a.nzt_cnt[s];
-        for (uint32_t tb = t0; tb < t1; tb += 32) {
-            uint32_t c = 0, t = 0;
-            if (tb + lane < t1) {
-                t = a.nzt[tb + lane];
-                if (box_d2(k0.x, k0.y, k0.z, a.tlo[t], a.thi[t]) < k0.w) c = a.tile_cnt[t];
+    // the kernel's super cells are dealt round-robin to all its warps; a warp
+    // tests 32 of its super cells at once (one per lane), then walks the hit
+    // ones and their packed nonzero tiles
+    const int W = NW * gridDim.y, wid = split * NW + warp;
+    for (int base = wid; base < nsb; base += W * 32) {
+        const int sb = base + lane * W;
+        uint32_t t0 = 0, nt = 0;
+        unsigned long long packed = 0;  // chunk counts (6 bits each) of the first 8 chunks
+        if (sb < nsb) {
+            const int sx = sx0 + sb % nbx, sy = sy0 + (sb / nbx) % nby, sz = sz0 + sb / (nbx * nby);
+            const int s = (sz * a.nsy + sy) * a.nsx + sx;
+            if (box_d2(k0.x, k0.y, k0.z, a.slo[s], a.shi[s]) < k0.w) {
+                t0 = a.stile0[s];
+                nt = a.stile0[s + 1] - t0;  // tiles of the super cell
+                const uint32_t nch = (nt + 31) / 32;
+                for (uint32_t q8 = 0; q8 < 8 && q8 < nch; ++q8)
+                    packed |= (unsigned long long)a.nzc[t0 + 32u * q8] << (6 * q8);
+                if (!packed && nch <= 8) nt = 0;  // no nonzero tile at all
             }
-            unsigned bal = __ballot_sync(0xffffffffu, c != 0);
-            while (bal) {
-                const int src = __ffs(bal) - 1;
-                bal &= bal - 1;
-                const uint32_t cc = __shfl_sync(0xffffffffu, c, src);
-                const uint32_t tt = __shfl_sync(0xffffffffu, t, src);
-                if (lane < (int)cc) q[(head + qn + lane) & (RING - 1)] = tt * kTile + lane;
-                qn += cc;
-                __syncwarp();
-                if (qn >= 64) {
-                    const float4 p0 = a.nz[q[(head + lane) & (RING - 1)]];
-                    const float4 p1 = a.nz[q[(head + 32 + lane) & (RING - 1)]];
-                    accumulate<KAHAN>(p0, k0, k1, k2, k3, acc, cmp, pairs);
-                    accumulate<KAHAN>(p1, k0, k1, k2, k3, acc, cmp, pairs);
-                    head = (head + 64) & (RING - 1);
-                    qn -= 64;
-                    __syncwarp();
+        }
+        unsigned sbal = __ballot_sync(0xffffffffu, nt != 0);
+        while (sbal) {
+            const int ssrc = __ffs(sbal) - 1;
+            sbal &= sbal - 1;
+            const uint32_t st0 = __shfl_sync(0xffffffffu, t0, ssrc), snt = __shfl_sync(0xffffffffu, nt, ssrc);
+            const unsigned long long spk = __shfl_sync(0xffffffffu, packed, ssrc);
+            // the super cell's 32-tile chunks: the first 8 counts came with the
+            // super cell's test, later ones are loaded 32 at a time
+            const uint32_t nch = (snt + 31) / 32;
+            for (uint32_t cg = 0; cg < nch; cg += 32) {
+            uint32_t cc_l = 0;
+            if (cg + lane < nch)
+                cc_l = (cg + lane < 8) ? (uint32_t)((spk >> (6 * (cg + lane))) & 63ull) : a.nzc[st0 + 32u * (cg + lane)];
+            unsigned cbal = __ballot_sync(0xffffffffu, cc_l != 0);
+            while (cbal) {
+                const int csrc = __ffs(cbal) - 1;
+                cbal &= cbal - 1;
+                const uint32_t cb = st0 + 32u * (cg + csrc), ncr = __shfl_sync(0xffffffffu, cc_l, csrc);
+                uint32_t c = 0, t = 0;
+                if ((uint32_t)lane < ncr) {
+                    const float4 lo = a.nzrec[2 * (size_t)(cb + lane)], hi = a.nzrec[2 * (size_t)(cb + lane) + 1];
+                    if (box_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w) {
+                        c = __float_as_uint(lo.w);
+                        t = __float_as_uint(hi.w);
+                    }
                 }
+                unsigned bal = __ballot_sync(0xffffffffu, c != 0);
+                while (bal) {
+                    const int src = __ffs(bal) - 1;
+                    bal &= bal - 1;
+                    const uint32_t cc = __shfl_sync(0xffffffffu, c, src);
+                    const uint32_t tt = __shfl_sync(0xffffffffu, t, src);
+                    if (lane < (int)cc) q[(head + qn + lane) & (RING - 1)] = tt * kTile + lane;
+                    qn += cc;
+                    __syncwarp();
+                    if (qn >= 64) {
+                        const float4 p0 = a.nz[q[(head + lane) & (RING - 1)]];
+                        const float4 p1 = a.nz[q[(head + 32 + lane) & (RING - 1)]];
+                        accumulate<KAHAN>(p0, k0, k1, k2, k3, acc, cmp, pairs);
+                        accumulate<KAHAN>(p1, k0, k1, k2, k3, acc, cmp, pairs);
+                        head = (head + 64) & (RING - 1);
+                        qn -= 64;
+                        __syncwarp();
+                    }
+                }
+            }
             }
         }
     }
     if (lane < qn) accumulate<KAHAN>(a.nz[q[(head + lane) & (RING - 1)]], k0, k1, k2, k3, acc, cmp, pairs);
     if (lane + 32 < qn) accumulate<KAHAN>(a.nz[q[(head + 32 + lane) & (RING - 1)]], k0, k1, k2, k3, acc, cmp, pairs);
-    // this warp's share of the kernel's moments: a float-float shuffle tree
-    // over the lanes, written to the warp's slot (no atomics, no block barrier)
+    // this warp's share of the kernel's moments, written to the warp's slot
+    // (no atomics, no block barrier); the lanes are combined with a plain
+    // float shuffle tree, or a float-float one in the compensated mode
     const int slot = split * NW + warp;  // < gridDim.y * NW <= kBwdWarpsPerKernel
     float *o = a.mom + ((int64_t)j * kBwdWarpsPerKernel + slot) * 22;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        ff v = KAHAN ? two_sum(acc[r], -cmp[r]) : ff{acc[r], 0.f};
-        v = warp_sum_ff(v);
+        ff v;
+        if (KAHAN) {
+            v = warp_sum_ff(two_sum(acc[r], -cmp[r]));
+        } else {
+            v = ff{warp_sum(acc[r]), 0.f};
+        }
         if (lane == 0) {
             o[2 * r] = v.hi;
             o[2 * r + 1] = v.lo;
@@ -285,11 +334,9 @@ extern "C" int serbf_backward(const serbf_points *pts, const serbf_params *prm, 
     const int64_t nt = ws->ntiles;
     const int cps = ws->sf * ws->sf * ws->sf;
     if (nt > 0)
-        k_nz_tiles<<<(unsigned)((nt * 32 + 255) / 256), 256, 0, s>>>(pts->x, pts->y, pts->z, err, ws->tile_super,
-                                                                      ws->tile_start, ws->cell_start, cps, nt,
-                                                                      ws->tile_cnt, ws->nz);
-    k_nz_super<<<(unsigned)((ws->nsuper * 32 + 255) / 256), 256, 0, s>>>(ws->super_tile0, ws->nsuper, ws->tile_cnt,
-                                                                         ws->nzt, ws->nzt_cnt);
+        k_nz_compact<<<dim3((unsigned)ws->max_chunks, (unsigned)ws->nsuper), 1024, 0, s>>>(
+            pts->x, pts->y, pts->z, err, ws->super_tile0, ws->tile_start, ws->cell_start, cps, ws->tile_lo,
+            ws->tile_hi, ws->nz, ws->nzrec, ws->nzc_cnt);
     BwdArgs a;
     a.kbwd = ws->kbwd;
     a.m = prm->m;
@@ -303,15 +350,14 @@ extern "C" int serbf_backward(const serbf_points *pts, const serbf_params *prm, 
     a.stile0 = ws->super_tile0;
     a.tlo = ws->tile_lo;
     a.thi = ws->tile_hi;
-    a.tile_cnt = ws->tile_cnt;
-    a.nzt = ws->nzt;
-    a.nzt_cnt = ws->nzt_cnt;
+    a.nzrec = ws->nzrec;
+    a.nzc = ws->nzc_cnt;
     a.nz = ws->nz;
     a.mom = ws->moments;
     // enough warps in flight: split a kernel's super cells over more blocks when
     // there are few kernels, fewer when there are many (each split adds a
     // per-warp reduction of ten moments)
-    int splits = (int)(10240 / ((int64_t)prm->cap * (kBwdThreads / 32)));
+    int splits = (int)(20480 / ((int64_t)prm->cap * (kBwdThreads / 32)));
     splits = splits < 1 ? 1 : (splits > kBwdSplit ? kBwdSplit : splits);
     const dim3 grid((unsigned)prm->cap, (unsigned)splits);
     if (cfg->kahan)

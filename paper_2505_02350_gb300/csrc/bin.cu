@@ -105,10 +105,11 @@ __global__ void k_count_cells(const uint32_t *keys, int64_t n, uint32_t *cnt) {
 }
 
 // tiles per super cell (for the scan that numbers the tiles)
-__global__ void k_super_tiles(const uint32_t *cell_start, int nsuper, int cps, uint32_t *stile) {
+__global__ void k_super_tiles(const uint32_t *cell_start, int nsuper, int cps, uint32_t *stile, uint32_t *maxt) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsuper; s += gridDim.x * blockDim.x) {
         uint32_t b = cell_start[(int64_t)s * cps], e = cell_start[(int64_t)(s + 1) * cps];
         stile[s] = (e - b + kTile - 1) / kTile;
+        atomicMax(maxt, stile[s]);
     }
 }
 
@@ -249,18 +250,22 @@ extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, 
     if (n > 0) k_count_cells<<<gsz(n, 256), 256, 0, s>>>(kin, n, ws->cell_start);
     int rc = launch_exscan_u32(ws->cell_start, ncp, s);
     if (rc) return rc;
-    k_super_tiles<<<gsz(nsuper, 256), 256, 0, s>>>(ws->cell_start, (int)nsuper, cps, ws->super_tile0);
+    uint32_t *maxt = ws->counters + 8;
+    cudaMemsetAsync(maxt, 0, sizeof(uint32_t), s);
+    k_super_tiles<<<gsz(nsuper, 256), 256, 0, s>>>(ws->cell_start, (int)nsuper, cps, ws->super_tile0, maxt);
     rc = launch_exscan_u32(ws->super_tile0, nsuper, s);
     if (rc) return rc;
     k_fill_tiles<<<gsz(nsuper, 256), 256, 0, s>>>(ws->cell_start, ws->super_tile0, (int)nsuper, cps,
                                                   ws->tile_super, ws->tile_start);
     SERBF_CHECK_LAUNCH();
-    uint32_t nt = 0;
+    uint32_t nt = 0, mt = 0;
     if (cudaMemcpyAsync(&nt, ws->super_tile0 + nsuper, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SERBF_ECUDA;
+    if (cudaMemcpyAsync(&mt, maxt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SERBF_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SERBF_ECUDA;
     if ((int64_t)nt > ws->max_tiles) return SERBF_ECAPACITY;
     ws->ntiles = nt;
+    ws->max_chunks = (int32_t)((mt + kTile - 1) / kTile);
     if (nt > 0)
         k_tile_boxes<<<(unsigned)((nt * 32 + 255) / 256), 256, 0, s>>>(ws->tile_super, ws->tile_start, ws->cell_start,
                                                                         cps, nt, xb, yb, zb, ws->tile_lo, ws->tile_hi);

@@ -14,6 +14,8 @@ constexpr int kTile = 32;                         // points per forward/backward
 constexpr int kSortTile = 4096;                   // elements per radix-sort block
 constexpr int kFwdWarps = 2;                      // warps (tiles) per forward block
 constexpr int kQueue = 64;                        // per-warp ring of staged candidates
+constexpr int kFwdGroup = 64;                     // tiles per first-level forward reduction group
+constexpr int kFwdBlocksPerSM = 16;               // resident forward blocks per SM (register bound)
 constexpr int kBwdThreads = 64;                   // threads per adjoint block
 constexpr int kBwdSplit = 16;                     // most blocks per kernel in the adjoint
 constexpr int kBwdWarpsPerKernel = kBwdSplit * kBwdThreads / 32;  // == 32, one epilogue lane each
@@ -50,6 +52,8 @@ struct serbf_workspace {
     int32_t binned;
     int64_t npoints;
     int64_t ntiles;
+    int32_t sm_count;
+    int32_t max_chunks;  // most 32-tile chunks in one super cell
     // binning
     uint32_t *keys0, *keys1, *vals0, *vals1, *hist;
     uint32_t *cell_start;   // nsuper * sf^3 + 1 (super-major cell order)
@@ -63,12 +67,14 @@ struct serbf_workspace {
     // candidate lists (ascending kernel index) per super cell
     uint32_t *sup_list, *sup_cnt;
     // reductions
-    serbf::FwdPart *fwd_part;
+    serbf::FwdPart *fwd_part;     // max_tiles
+    serbf::FwdPart *fwd_gpart;    // max_tiles / kFwdGroup + 1
+    uint32_t *fwd_group_done;     // max_tiles / kFwdGroup + 1 (kept zero between launches)
     unsigned long long *bwd_pairs;
     float *moments;     // max_kernels x kBwdWarpsPerKernel x 22 (float-float partial moments, pairs)
-    uint32_t *tile_cnt; // nonzero-residual points per tile
-    uint32_t *nzt;      // per super cell: ids of its tiles with nonzero residuals (in its tile range)
-    uint32_t *nzt_cnt;  // per super cell: number of such tiles
+    float4 *nzrec;      // per 32-tile chunk of a super cell: packed (box, count, id) of its tiles
+                        // with nonzero residuals, at the chunk's own slots (2 float4 per tile)
+    uint32_t *nzc_cnt;  // indexed by the chunk's first tile: number of such tiles in the chunk
     float4 *nz;         // 32 slots per tile: (x, y, z, E) of its nonzero-residual points
     // optimiser step scratch
     float *step_part;   // per-block partial sums

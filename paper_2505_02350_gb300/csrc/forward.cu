@@ -28,8 +28,11 @@ struct FwdArgs {
     float tau1, tau2;  // tau1 rounded down, tau2 rounded up to float: exact double decisions
     float *psi, *err;
     uint8_t *mask;
-    FwdPart *part;
-    uint32_t *counter;
+    FwdPart *part;        // one partial per tile
+    FwdPart *gpart;       // one partial per group of kFwdGroup tiles
+    uint32_t *group_done; // tiles finished per group
+    uint32_t *counter;    // groups finished
+    uint32_t *tile_next;  // next tile to take (zeroed before each launch)
     double *stats;
 };
 
@@ -82,171 +85,169 @@ __device__ __forceinline__ void eval_full(const float4 (*ring)[3], int cnt, floa
     }
 }
 
+struct TileOut {
+    float l2, mx;
+    uint32_t cnt, pairs;
+};
+
+// One tile (32 binned points) on one warp: stream the super cell's candidate
+// list, stage the kernels that reach the tile box, evaluate, write psi, E and
+// the mask.  Returns this lane's loss contributions.
+__device__ __forceinline__ TileOut forward_tile(const FwdArgs &a, int64_t tile, float4 (*ringP)[3],
+                                                float4 (*ringF)[3], int lane) {
+    TileOut out{0.f, 0.f, 0u, 0u};
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t sup = a.tile_super[tile];
+    const uint32_t p0 = a.tile_start[tile], pe = a.cell_start[(int64_t)(sup + 1) * a.cps];
+    const int64_t i = (int64_t)p0 + lane;
+    const bool valid = i < (int64_t)pe;
+    // invalid lanes carry NaN so the support test fails for them
+    const float px = valid ? a.x[i] : __int_as_float(0x7fc00000);
+    const float py = valid ? a.y[i] : 0.f;
+    const float pz = valid ? a.z[i] : 0.f;
+    const float4 lo = a.tile_lo[tile], hi = a.tile_hi[tile];
+    const uint32_t *lst = a.slist + (size_t)sup * a.scap;
+    const int L = min((int)a.scnt[sup], a.scap);
+    int hp = 0, qp = 0, hf = 0, qf = 0;
+    uint32_t nfull = 0, np = 0;
+    float acc = 0.f;
+    uint32_t jn = lane < L ? lst[lane] : 0u;
+    for (int b = 0; b < L; b += 32) {
+        const uint32_t j = jn;
+        const bool live = b + lane < L;
+        if (b + 32 + lane < L) jn = lst[b + 32 + lane];  // prefetch the next chunk
+        bool part = false, full = false;
+        float4 k0;
+        if (live) {
+            k0 = a.kfwd[3 * j];
+            if (box_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w) {
+                full = box_far_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w;
+                part = !full;
+            }
+        }
+        const unsigned bp = __ballot_sync(0xffffffffu, part), bf = __ballot_sync(0xffffffffu, full);
+        if (part || full) {
+            float4(*ring)[3] = part ? ringP : ringF;
+            const int slot = part ? ((hp + qp + __popc(bp & lt)) & (kQueue - 1))
+                                  : ((hf + qf + __popc(bf & lt)) & (kQueue - 1));
+            ring[slot][0] = k0;
+            ring[slot][1] = a.kfwd[3 * j + 1];
+            ring[slot][2] = a.kfwd[3 * j + 2];
+        }
+        qp += __popc(bp);
+        qf += __popc(bf);
+        __syncwarp();
+        if (qp >= 32) {
+            eval_partial<8>(ringP + hp, 32, px, py, pz, acc, np);
+            hp ^= 32;
+            qp -= 32;
+        }
+        if (qf >= 32) {
+            eval_full<8>(ringF + hf, 32, px, py, pz, acc);
+            hf ^= 32;
+            qf -= 32;
+            nfull += 32;
+        }
+        __syncwarp();
+    }
+    // leftovers: head is 0 or 32 and fewer than 32 remain, so they do not wrap
+    if (qp > 0) eval_partial<1>(ringP + hp, qp, px, py, pz, acc, np);
+    if (qf > 0) {
+        eval_full<1>(ringF + hf, qf, px, py, pz, acc);
+        nfull += qf;
+    }
+    __syncwarp();
+    if (valid) {
+        out.pairs = np + nfull;
+        const float t = a.t[i], ps = acc;
+        const bool m0 = (a.tau1 < t) && (t < a.tau2);
+        const bool m1 = (t <= a.tau1) && (ps > a.tau1);
+        const bool m2 = (t >= a.tau2) && (ps < a.tau2);
+        const bool mk = m0 || m1 || m2;
+        const float e = mk ? __fsub_rn(ps, t) : 0.f;
+        a.psi[i] = ps;
+        a.err[i] = e;
+        a.mask[i] = (uint8_t)mk;
+        if (mk) {
+            out.l2 = e * e;
+            out.mx = fabsf(e);
+            out.cnt = 1;
+        }
+    }
+    return out;
+}
+
+// Fixed-order warp reduction of tile partials [b, e) into one partial.
+__device__ __forceinline__ FwdPart reduce_parts(const FwdPart *p, uint32_t b, uint32_t e, int lane) {
+    ff l{0.f, 0.f};
+    float mx = 0.f;
+    unsigned long long c = 0, pr = 0;
+    for (uint32_t q = b + lane; q < e; q += 32) {
+        l = ff_add(l, ff{__ldcg(&p[q].l2hi), __ldcg(&p[q].l2lo)});
+        mx = fmaxf(mx, __ldcg(&p[q].maxe));
+        c += __ldcg(&p[q].cnt);
+        pr += __ldcg(&p[q].pairs);
+    }
+    l = warp_sum_ff(l);
+    mx = warp_max(mx);
+    c = warp_sum(c);
+    pr = warp_sum(pr);
+    return FwdPart{l.hi, l.lo, mx, (uint32_t)c, pr};
+}
+
+// Persistent warps take tiles from a global counter (heavy and light tiles
+// balance out), write one partial per tile, and the partials are reduced in a
+// fixed order in two levels (groups of kFwdGroup tiles, then all groups), so
+// the loss terms are deterministic whatever warp handled which tile.
 __global__ void __launch_bounds__(kFwdWarps * 32) k_forward(FwdArgs a) {
     // two rings per warp (kernels partly / fully covering the tile); a ring
     // holds 64 staged records and is consumed 32 at a time from slot 0 or 32
     __shared__ float4 ringP[kFwdWarps][kQueue][3];
     __shared__ float4 ringF[kFwdWarps][kQueue][3];
-    __shared__ ff s_l2[kFwdWarps];
-    __shared__ float s_mx[kFwdWarps];
-    __shared__ uint32_t s_cnt[kFwdWarps];
-    __shared__ unsigned long long s_pairs[kFwdWarps];
-    __shared__ bool s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t tile = (int64_t)blockIdx.x * kFwdWarps + warp;
-    const unsigned lt = (1u << lane) - 1u;
-
-    float l2 = 0.f;
-    float mx = 0.f;
-    uint32_t cnt = 0;
-    uint32_t pairs = 0;
-    if (tile < a.ntiles) {
-        const uint32_t sup = a.tile_super[tile];
-        const uint32_t p0 = a.tile_start[tile], pe = a.cell_start[(int64_t)(sup + 1) * a.cps];
-        const int64_t i = (int64_t)p0 + lane;
-        const bool valid = i < (int64_t)pe;
-        // invalid lanes carry NaN so the support test fails for them
-        const float px = valid ? a.x[i] : __int_as_float(0x7fc00000);
-        const float py = valid ? a.y[i] : 0.f;
-        const float pz = valid ? a.z[i] : 0.f;
-        const float4 lo = a.tile_lo[tile], hi = a.tile_hi[tile];
-        const uint32_t *lst = a.slist + (size_t)sup * a.scap;
-        const int L = min((int)a.scnt[sup], a.scap);
-        int hp = 0, qp = 0, hf = 0, qf = 0;
-        uint32_t nfull = 0;
-        float acc = 0.f;
-        uint32_t np = 0;
-        uint32_t jn = lane < L ? lst[lane] : 0u;
-        for (int b = 0; b < L; b += 32) {
-            const uint32_t j = jn;
-            const bool live = b + lane < L;
-            if (b + 32 + lane < L) jn = lst[b + 32 + lane];  // prefetch the next chunk
-            bool part = false, full = false;
-            float4 k0;
-            if (live) {
-                k0 = a.kfwd[3 * j];
-                if (box_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w) {
-                    full = box_far_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w;
-                    part = !full;
-                }
-            }
-            const unsigned bp = __ballot_sync(0xffffffffu, part), bf = __ballot_sync(0xffffffffu, full);
-            if (part || full) {
-                float4(*ring)[3] = part ? ringP[warp] : ringF[warp];
-                const int slot = part ? ((hp + qp + __popc(bp & lt)) & (kQueue - 1))
-                                      : ((hf + qf + __popc(bf & lt)) & (kQueue - 1));
-                ring[slot][0] = k0;
-                ring[slot][1] = a.kfwd[3 * j + 1];
-                ring[slot][2] = a.kfwd[3 * j + 2];
-            }
-            qp += __popc(bp);
-            qf += __popc(bf);
-            __syncwarp();
-            if (qp >= 32) {
-                eval_partial<8>(ringP[warp] + hp, 32, px, py, pz, acc, np);
-                hp ^= 32;
-                qp -= 32;
-            }
-            if (qf >= 32) {
-                eval_full<8>(ringF[warp] + hf, 32, px, py, pz, acc);
-                hf ^= 32;
-                qf -= 32;
-                nfull += 32;
-            }
-            __syncwarp();
+    const uint32_t ngroups = (uint32_t)((a.ntiles + kFwdGroup - 1) / kFwdGroup);
+    for (;;) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(a.tile_next, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if ((int64_t)t >= a.ntiles) break;
+        const TileOut o = forward_tile(a, t, ringP[warp], ringF[warp], lane);
+        const ff l2 = warp_sum_ff(ff{o.l2, 0.f});
+        const float mx = warp_max(o.mx);
+        const uint32_t cnt = warp_sum(o.cnt), pr = warp_sum(o.pairs);
+        uint32_t done = 0;
+        if (lane == 0) {
+            a.part[t] = FwdPart{l2.hi, l2.lo, mx, cnt, (unsigned long long)pr};
+            __threadfence();
+            done = atomicAdd(a.group_done + t / kFwdGroup, 1u);
         }
-        // leftovers: head is 0 or 32 and fewer than 32 remain, so they do not wrap
-        if (qp > 0) eval_partial<1>(ringP[warp] + hp, qp, px, py, pz, acc, np);
-        if (qf > 0) {
-            eval_full<1>(ringF[warp] + hf, qf, px, py, pz, acc);
-            nfull += qf;
-        }
-        if (valid) {
-            pairs = np + nfull;
-            const float t = a.t[i], ps = acc;
-            const bool m0 = (a.tau1 < t) && (t < a.tau2);
-            const bool m1 = (t <= a.tau1) && (ps > a.tau1);
-            const bool m2 = (t >= a.tau2) && (ps < a.tau2);
-            const bool mk = m0 || m1 || m2;
-            const float e = mk ? __fsub_rn(ps, t) : 0.f;
-            a.psi[i] = ps;
-            a.err[i] = e;
-            a.mask[i] = (uint8_t)mk;
-            if (mk) {
-                l2 = e * e;
-                mx = fabsf(e);
-                cnt = 1;
-            }
-        }
-    }
-    // deterministic reduction: lanes -> warp -> block partial -> last block
-    const ff l2w = warp_sum_ff(ff{l2, 0.f});
-    mx = warp_max(mx);
-    cnt = warp_sum(cnt);
-    const unsigned long long pr = warp_sum((unsigned long long)pairs);
-    if (lane == 0) {
-        s_l2[warp] = l2w;
-        s_mx[warp] = mx;
-        s_cnt[warp] = cnt;
-        s_pairs[warp] = pr;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ff l{0.f, 0.f};
-        FwdPart p{0.f, 0.f, 0.f, 0u, 0ull};
-        for (int w = 0; w < kFwdWarps; ++w) {
-            l = ff_add(l, s_l2[w]);
-            p.maxe = fmaxf(p.maxe, s_mx[w]);
-            p.cnt += s_cnt[w];
-            p.pairs += s_pairs[w];
-        }
-        p.l2hi = l.hi;
-        p.l2lo = l.lo;
-        a.part[blockIdx.x] = p;
+        done = __shfl_sync(0xffffffffu, done, 0);
+        const uint32_t g = t / kFwdGroup;
+        const uint32_t gb = g * kFwdGroup;
+        const uint32_t ge = (uint32_t)min((int64_t)gb + kFwdGroup, a.ntiles);
+        if (done != ge - gb - 1) continue;
+        // this warp completed its group: reduce the group's partials
         __threadfence();
-        const uint32_t prev = atomicAdd(a.counter, 1u);
-        s_last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // last block: fixed-order sum of all block partials
-    ff L2{0.f, 0.f};
-    float MX = 0.f;
-    unsigned long long C = 0, P = 0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
-        const FwdPart *q = a.part + b;
-        L2 = ff_add(L2, ff{__ldcg(&q->l2hi), __ldcg(&q->l2lo)});
-        MX = fmaxf(MX, __ldcg(&q->maxe));
-        C += __ldcg(&q->cnt);
-        P += __ldcg(&q->pairs);
-    }
-    L2 = warp_sum_ff(L2);
-    MX = warp_max(MX);
-    C = warp_sum(C);
-    P = warp_sum(P);
-    if (lane == 0) {
-        s_l2[warp] = L2;
-        s_mx[warp] = MX;
-        s_cnt[warp] = (uint32_t)C;
-        s_pairs[warp] = P;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ff l{0.f, 0.f};
-        float m = 0.f;
-        unsigned long long c = 0, pp = 0;
-        for (int w = 0; w < kFwdWarps; ++w) {
-            l = ff_add(l, s_l2[w]);
-            m = fmaxf(m, s_mx[w]);
-            c += s_cnt[w];
-            pp += s_pairs[w];
+        const FwdPart gp = reduce_parts(a.part, gb, ge, lane);
+        uint32_t gdone = 0;
+        if (lane == 0) {
+            a.gpart[g] = gp;
+            a.group_done[g] = 0u;
+            __threadfence();
+            gdone = atomicAdd(a.counter, 1u);
         }
-        a.stats[SERBF_STAT_L2] = (double)l.hi + (double)l.lo;
-        a.stats[SERBF_STAT_MAXE] = m;
-        a.stats[SERBF_STAT_COUNT] = (double)c;
-        a.stats[SERBF_STAT_PAIRS_FWD] = (double)pp;
-        *a.counter = 0u;
+        gdone = __shfl_sync(0xffffffffu, gdone, 0);
+        if (gdone != ngroups - 1) continue;
+        // the last group: fixed-order sum of all group partials
+        __threadfence();
+        const FwdPart tot = reduce_parts(a.gpart, 0, ngroups, lane);
+        if (lane == 0) {
+            a.stats[SERBF_STAT_L2] = (double)tot.l2hi + (double)tot.l2lo;
+            a.stats[SERBF_STAT_MAXE] = tot.maxe;
+            a.stats[SERBF_STAT_COUNT] = (double)tot.cnt;
+            a.stats[SERBF_STAT_PAIRS_FWD] = (double)tot.pairs;
+            *a.counter = 0u;
+        }
     }
 }
 
@@ -284,10 +285,23 @@ extern "C" int serbf_forward(const serbf_points *pts, const serbf_params *prm, c
     a.err = err;
     a.mask = mask;
     a.part = ws->fwd_part;
+    a.gpart = ws->fwd_gpart;
+    a.group_done = ws->fwd_group_done;
     a.counter = ws->counters + 0;
+    a.tile_next = ws->counters + 4;
     a.stats = stats;
+    if (ws->ntiles == 0) {
+        // nothing to evaluate: the loss terms are zero
+        cudaMemsetAsync(stats + SERBF_STAT_L2, 0, 4 * sizeof(double), (cudaStream_t)stream);
+        SERBF_CHECK_LAUNCH();
+        return SERBF_OK;
+    }
     int64_t blocks = (ws->ntiles + kFwdWarps - 1) / kFwdWarps;
-    if (blocks < 1) blocks = 1;
+    const int64_t resident = (int64_t)ws->sm_count * kFwdBlocksPerSM;
+    if (blocks > resident) blocks = resident;
+    // the tile counter is reset before every launch (warps still looking for
+    // work may touch it after the last tile is done, so the kernel cannot)
+    cudaMemsetAsync(a.tile_next, 0, sizeof(uint32_t), (cudaStream_t)stream);
     k_forward<<<(unsigned)blocks, kFwdWarps * 32, 0, (cudaStream_t)stream>>>(a);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;

@@ -120,18 +120,18 @@ __global__ void __launch_bounds__(kStepThreads) k_step_alpha(StepArgs a) {
     ff fin[3];
     block_sums_ff3(acc, sh3, fin);
     if (threadIdx.x == 0) {
-        const double l1 = (double)fin[0].hi + fin[0].lo, num = (double)fin[1].hi + fin[1].lo;
-        const double den = (double)fin[2].hi + fin[2].lo;
-        double al = 1.0;
-        if (use_l1 && den > 0.0) al = fmin(1.0, fmax(0.0, num / den));
-        const int t = a.st->adam_t + 1;
+        // float arithmetic from here (FP64 is slow on this part): alpha to ~1e-7
+        const float num = fin[1].hi + fin[1].lo, den = fin[2].hi + fin[2].lo;
+        float al = 1.f;
+        if (use_l1 && den > 0.f) al = fminf(1.f, fmaxf(0.f, num / den));
+        const float t = (float)(a.st->adam_t + 1);
         a.scal[0] = al;
-        a.scal[1] = 1.0 - al;
-        a.scal[2] = 1.0 - pow(a.c.beta1, t);
-        a.scal[3] = 1.0 - pow(a.c.beta2, t);
-        a.stats[SERBF_STAT_L1] = l1;
+        a.scal[1] = 1.f - al;
+        a.scal[2] = 1.f - powf((float)a.c.beta1, t);
+        a.scal[3] = 1.f - powf((float)a.c.beta2, t);
+        a.stats[SERBF_STAT_L1] = (double)fin[0].hi + (double)fin[0].lo;
         a.stats[SERBF_STAT_ALPHA] = al;
-        a.stats[SERBF_STAT_BETA] = 1.0 - al;
+        a.stats[SERBF_STAT_BETA] = 1.f - al;
         *a.counter = 0u;
     }
 }
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
     __shared__ __align__(8) uint32_t s_words[kStateWords];
     const int m = *a.m, cap = a.cap;
     const int r = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
-    const double alpha = a.scal[0], beta = a.scal[1];
+    const float alpha = (float)a.scal[0], beta = (float)a.scal[1];
     const float bc1 = (float)a.scal[2], bc2 = (float)a.scal[3];
     const float lr = (float)a.st->lr;
     const float b1 = (float)a.c.beta1, b2 = (float)a.c.beta2, eps = (float)a.c.adam_eps;
@@ -156,8 +156,8 @@ __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
     if (j < m) {
         const int64_t q = (int64_t)r * cap + j;
         const float pv = a.p[q];
-        float g = (float)alpha * a.grad[q];
-        if (r == PW) g = fmaf((float)beta, sgnf(pv), g);
+        float g = alpha * a.grad[q];
+        if (r == PW) g = fmaf(beta, sgnf(pv), g);
         const float mo = fmaf(b1, a.am[q], (1.f - b1) * g);
         const float vo = fmaf(b2, a.av[q], (1.f - b2) * g * g);
         const float pn = pv - lr * (mo / bc1) / (sqrtf(vo / bc2) + eps);
@@ -203,13 +203,27 @@ __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
         const int n_l2 = st.n_l2, n_bf = st.n_bf;
         const int do_prune = (e % kl2 == 0) && l1n && (e < a.c.T_e);
         if (!l1n && !phase2 && e >= kl2 && n_l2 == kl2) {
-            double v = 0.0;
-            for (int k = lane; k < kl2; k += 32) v += st.l2_hist[k];
-            const double mean = warp_sum(v) / kl2;
-            double var = 0.0;
-            for (int k = lane; k < kl2; k += 32) var += (st.l2_hist[k] - mean) * (st.l2_hist[k] - mean);
-            var = warp_sum(var) / kl2;
-            if (sqrt(var) < a.c.tau_l2) l1n = 1;
+            // population std of the last k_l2 values; each double is split into
+            // a float-float pair so the mean and deviations keep ~48 bits
+            ff v{0.f, 0.f};
+            for (int k = lane; k < kl2; k += 32) {
+                const double x = st.l2_hist[k];
+                const float xh = (float)x;
+                v = ff_add(v, ff{xh, (float)(x - (double)xh)});
+            }
+            v = warp_sum_ff(v);
+            const float inv = 1.f / (float)kl2;
+            const ff mean{v.hi * inv, v.lo * inv};
+            float var = 0.f;
+            for (int k = lane; k < kl2; k += 32) {
+                const double x = st.l2_hist[k];
+                const float xh = (float)x;
+                const ff d = ff_add(ff{xh, (float)(x - (double)xh)}, ff{-mean.hi, -mean.lo});
+                const float dd = d.hi + d.lo;
+                var = fmaf(dd, dd, var);
+            }
+            var = warp_sum(var) * inv;
+            if (sqrtf(var) < (float)a.c.tau_l2) l1n = 1;
         }
         int do_add = 0;
         if (l1n && !phase2 && n_bf == kl1) {
@@ -223,7 +237,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
                 lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
                 hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
             }
-            if ((double)(hi - lo) < a.c.tau_l1) {
+            if ((float)(hi - lo) < (float)a.c.tau_l1) {
                 do_add = 1;
                 l1n = 0;
             }
@@ -234,12 +248,12 @@ __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
                 ph = 1;
                 l1n = 0;
             }
-            double lr_next = a.c.lr;
+            float lr_next = (float)a.c.lr;
             if (ph) {
-                const double span = (double)(a.c.M_e - a.c.T_e);
-                double pr = span > 0 ? (double)(e - a.c.T_e) / span : 1.0;
-                if (pr > 1.0) pr = 1.0;
-                lr_next = a.c.lr_min + (a.c.lr_p2 - a.c.lr_min) * 0.5 * (1.0 + cospi(pr));
+                const float span = (float)(a.c.M_e - a.c.T_e);
+                float pr = span > 0.f ? (float)(e - a.c.T_e) / span : 1.f;
+                if (pr > 1.f) pr = 1.f;
+                lr_next = (float)a.c.lr_min + (float)(a.c.lr_p2 - a.c.lr_min) * 0.5f * (1.f + cospif(pr));
             }
             st.alpha = alpha;
             st.beta = beta;
@@ -251,7 +265,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
             st.lr = lr_next;
             st.epoch = e;
             a.stats[SERBF_STAT_BF] = bf;
-            a.stats[SERBF_STAT_LOSS] = alpha * l2 + beta * a.stats[SERBF_STAT_L1];
+            a.stats[SERBF_STAT_LOSS] = (float)alpha * (float)l2 + (float)beta * (float)a.stats[SERBF_STAT_L1];
             a.counter[1] = 0u;
         }
     }
@@ -269,11 +283,14 @@ __global__ void __launch_bounds__(kStepThreads) k_prune(float *p, float *am, flo
     __syncthreads();
     if (!s_go) return;
     const int m = *m_dev;
+    // |w| >= tau_d in float with tau_d rounded up: the same decision as in double
+    float taud = (float)tau_d;
+    if ((double)taud < tau_d) taud = nextafterf(taud, INFINITY);
     uint32_t carry = 0;
     for (int j0 = 0; j0 < m; j0 += blockDim.x) {
         const int j = j0 + threadIdx.x;
         const bool live = j < m;
-        const uint32_t keep = live && (fabs((double)p[PW * cap + j]) >= tau_d);
+        const uint32_t keep = live && (fabsf(p[PW * cap + j]) >= taud);
         uint32_t tot;
         const uint32_t off = block_exscan(keep, tmp, &tot);
         float v[3][10];
