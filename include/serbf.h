@@ -164,6 +164,14 @@ int serbf_workspace_bytes(const serbf_ws_sizes *sz, size_t *bytes);
  * ENOMEM if `bytes` is too small, EINVAL on bad sizes or alignment. */
 int serbf_workspace_init(serbf_workspace *ws, void *dev, size_t bytes, const serbf_ws_sizes *sz);
 
+/* Releases the workspace's host-side CUDA objects (a side stream and two
+ * events created by serbf_workspace_init; some calls fork work onto that
+ * stream and join it before they return).  The device buffer stays the
+ * caller's.  Call it once when the workspace is no longer used, after the
+ * work queued with it has been synchronised; the workspace is invalid
+ * afterwards (calls return EINVAL).  EINVAL on an uninitialised workspace. */
+int serbf_workspace_release(serbf_workspace *ws);
+
 /* Reads and optionally clears the device status flags (synchronises `stream`).
  * needed[0] = largest super-cell list, needed[3] = kernel count an addition
  * asked for, both since the last clear.  Returns SERBF_ECAPACITY when a flag is
@@ -252,6 +260,20 @@ int serbf_forward(const serbf_points *pts, const serbf_params *prm, const serbf_
  * err = g / 2.  Uses the lists of the last serbf_build_neighbors call. */
 int serbf_backward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg,
                    const float *err, float *grad, double *stats, serbf_workspace *ws, void *stream);
+
+/* Forward and adjoint in one pass (Eq. 3-26, 3-18, 3-19, App. A): the
+ * outputs of serbf_forward, and the gradients of L2 = sum_i E_i^2 of
+ * serbf_backward with err = the forward's own E (grad is 10 x cap, rows of
+ * kernels >= m untouched; stats[PAIRS_BWD] as there).  Each work item's
+ * points with E != 0 are taken against its candidate kernels right after
+ * its residuals are known; per-kernel moments are accumulated across items
+ * in 64-bit fixed point (unit 2^-36, integer atomics), so the result is
+ * deterministic; it equals serbf_backward's up to float rounding (the
+ * kahan option does not apply).  Two launches.  EINVAL as serbf_forward, or
+ * when grad is NULL. */
+int serbf_forward_backward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi,
+                           float *err, uint8_t *mask, float *grad, double *stats, serbf_workspace *ws,
+                           void *stream);
 
 /* ------------------------------------------------------------------ a6 */
 /* One Algorithm 3 parameter update for the full batch: if l1_optim and

@@ -524,7 +524,7 @@ int32_t oracle_prune(double *P, double *mo, double *v, int32_t cap, int32_t m, d
 }
 
 /* ---------------------------------------------------------------------------
- * Algorithm 2, line 1 (I_add = {|E_i| > tau_m / 2} over id_all) followed by the
+ * Algorithm 2, candidate set (I_add = {|E_i| > tau_m / 2} over id_all), then the
  * top-k restriction used by this project (k largest |E|, ties by ascending
  * index; output in that order).  thresh = tau_m / 2.
  * Pinned by: Python sorted() on the same keys. */
@@ -551,7 +551,7 @@ int32_t oracle_select_topk(const float *E, const uint8_t *mask, int64_t n, doubl
     return take;
 }
 
-/* Algorithm 2, lines 2-8: keep candidate i if |E_i| >= |E_n| for every id_all
+/* Algorithm 2, local-maximum test: keep candidate i if |E_i| >= |E_n| for every id_all
  * point n within radius r of v_i (distance test in float, same operation
  * order as the support predicate, <= r2).  Brute force over all points.
  * Pinned by: numpy brute force. */

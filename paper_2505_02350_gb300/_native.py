@@ -76,6 +76,7 @@ _SIGS = {
     "serbf_workspace_struct_size": (C.c_size_t, []),
     "serbf_workspace_bytes": (C.c_int, [C.POINTER(WsSizes), C.POINTER(C.c_size_t)]),
     "serbf_workspace_init": (C.c_int, [VP, VP, C.c_size_t, C.POINTER(WsSizes)]),
+    "serbf_workspace_release": (C.c_int, [VP]),
     "serbf_status": (C.c_int, [VP, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.c_int, VP]),
     "serbf_state_init": (C.c_int, [VP, C.POINTER(Config), VP]),
     "serbf_normalize_sdf": (C.c_int, [VP, VP, C.c_int64, VP, VP, VP]),
@@ -86,6 +87,8 @@ _SIGS = {
                                         C.POINTER(Csr), C.POINTER(Csr), C.POINTER(C.c_int64), VP, VP]),
     "serbf_forward": (C.c_int, [C.POINTER(Points), C.POINTER(Params), C.POINTER(Config), VP, VP, VP, VP,
                                 VP, VP]),
+    "serbf_forward_backward": (C.c_int, [C.POINTER(Points), C.POINTER(Params), C.POINTER(Config), VP, VP, VP, VP,
+                                         VP, VP, VP]),
     "serbf_backward": (C.c_int, [C.POINTER(Points), C.POINTER(Params), C.POINTER(Config), VP, VP, VP, VP,
                                  VP]),
     "serbf_step": (C.c_int, [C.POINTER(Params), VP, VP, VP, VP, VP, C.POINTER(Config), VP, VP]),
@@ -154,6 +157,10 @@ def serbf_workspace_init(ws_host, dev, sizes):
                                             C.byref(sizes)))
 
 
+def serbf_workspace_release(ws_host):
+    return _check("serbf_workspace_release", _lib.serbf_workspace_release(C.addressof(ws_host)))
+
+
 def serbf_status(ws_host, clear=False, stream=None):
     f = C.c_int32()
     nd = (C.c_int64 * 4)()
@@ -216,6 +223,12 @@ def serbf_build_neighbors(pts, prm, cfg, ws_host, kmajor=None, pmajor=None, stre
 def serbf_forward(pts, prm, cfg, psi, err, mask, stats, ws_host, stream=None):
     return _check("serbf_forward", _lib.serbf_forward(C.byref(pts), C.byref(prm), C.byref(cfg), _p(psi), _p(err),
                                                       _p(mask), _p(stats), C.addressof(ws_host), _stream(stream)))
+
+
+def serbf_forward_backward(pts, prm, cfg, psi, err, mask, grad, stats, ws_host, stream=None):
+    return _check("serbf_forward_backward",
+                  _lib.serbf_forward_backward(C.byref(pts), C.byref(prm), C.byref(cfg), _p(psi), _p(err), _p(mask),
+                                              _p(grad), _p(stats), C.addressof(ws_host), _stream(stream)))
 
 
 def serbf_backward(pts, prm, cfg, err, grad, stats, ws_host, stream=None):

@@ -1,10 +1,10 @@
 // Adaptive basis addition, Algorithm 2 in its top-k form, with the new
 // kernel parameters of Eq. 3-24 appended as in Eq. 3-25:
-//   1. candidates: id_all points with |E| > tau_m / 2 (Algorithm 2, line 1);
+//   1. candidates: id_all points with |E| > tau_m / 2 (Algorithm 2, candidate set);
 //   2. keep the k = ceil(topk_frac |id_all|) largest |E| (ties: ascending
 //      binned index) with an exact radix select on the float bits of |E|;
 //   3. drop a candidate if an id_all point within add_radius has a larger |E|
-//      (Algorithm 2, lines 2-8);
+//      (Algorithm 2, local-maximum test);
 //   4. append c = v, w = -E, d = sqrt(-ln(eps / |E|) / dbar^2) on all axes,
 //      theta = 0, in selection order; reset the Adam moments.
 #include <math.h>

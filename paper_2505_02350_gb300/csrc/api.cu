@@ -56,6 +56,11 @@ void carve(Carver &c, serbf_workspace *w, const serbf_ws_sizes *s) {
     w->super_tile0 = c.take<uint32_t>(S + 1);
     w->tile_super = c.take<uint32_t>(T);
     w->tile_start = c.take<uint32_t>(T);
+    const int64_t I = T / 2 + S + 2;
+    w->super_item0 = c.take<uint32_t>(S + 1);
+    w->item_rec = c.take<uint4>(I);
+    w->item_cost = c.take<uint32_t>(I);
+    w->order_rec = c.take<uint4>(I);
     w->tile_lo = c.take<float4>(T);
     w->tile_hi = c.take<float4>(T);
     w->sup_lo = c.take<float4>(S);
@@ -68,6 +73,8 @@ void carve(Carver &c, serbf_workspace *w, const serbf_ws_sizes *s) {
     w->fwd_gpart = c.take<FwdPart>(T / kFwdGroup + 2);
     w->fwd_group_done = c.take<uint32_t>(T / kFwdGroup + 2);
     w->bwd_pairs = c.take<unsigned long long>(K);
+    w->adj_fix = c.take<unsigned long long>(K * 10);
+    w->adj_pairs = c.take<unsigned long long>(8);
     w->moments = c.take<float>((int64_t)K * kBwdWarpsPerKernel * 22);
     w->nzrec = c.take<float4>(2 * T);
     w->nzc_cnt = c.take<uint32_t>(T);
@@ -283,8 +290,27 @@ int serbf_workspace_init(serbf_workspace *ws, void *dev, size_t bytes, const ser
             return SERBF_ECUDA;
     }
     if (cudaMemset(ws->add_info, 0, 16 * sizeof(int32_t)) != cudaSuccess) return SERBF_ECUDA;
+    if (cudaMemset(ws->adj_fix, 0, sizeof(unsigned long long) * 10 * (size_t)sz->max_kernels) != cudaSuccess)
+        return SERBF_ECUDA;
+    if (cudaMemset(ws->adj_pairs, 0, sizeof(unsigned long long) * 8) != cudaSuccess) return SERBF_ECUDA;
+    if (cudaStreamCreateWithFlags(&ws->aux, cudaStreamNonBlocking) != cudaSuccess) return SERBF_ECUDA;
+    if (cudaEventCreateWithFlags(&ws->ev_fork, cudaEventDisableTiming) != cudaSuccess) return SERBF_ECUDA;
+    if (cudaEventCreateWithFlags(&ws->ev_join, cudaEventDisableTiming) != cudaSuccess) return SERBF_ECUDA;
     if (cudaDeviceSynchronize() != cudaSuccess) return SERBF_ECUDA;
     return SERBF_OK;
+}
+
+int serbf_workspace_release(serbf_workspace *ws) {
+    if (!ws || ws->magic != kMagic) return SERBF_EINVAL;
+    int rc = SERBF_OK;
+    if (ws->aux && cudaStreamSynchronize(ws->aux) != cudaSuccess) rc = SERBF_ECUDA;
+    if (ws->aux && cudaStreamDestroy(ws->aux) != cudaSuccess) rc = SERBF_ECUDA;
+    if (ws->ev_fork && cudaEventDestroy(ws->ev_fork) != cudaSuccess) rc = SERBF_ECUDA;
+    if (ws->ev_join && cudaEventDestroy(ws->ev_join) != cudaSuccess) rc = SERBF_ECUDA;
+    ws->aux = nullptr;
+    ws->ev_fork = ws->ev_join = nullptr;
+    ws->magic = 0;
+    return rc;
 }
 
 int serbf_status(serbf_workspace *ws, int32_t *flags, int64_t needed[4], int clear, void *stream) {

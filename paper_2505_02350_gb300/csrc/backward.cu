@@ -83,50 +83,6 @@ struct BwdArgs {
     float *mom;  // per kernel, per warp: 10 float-float moments S0, M1 (3), M2 (6), then the pair count (bits)
 };
 
-__device__ __forceinline__ void kadd(float &s, float &c, float v) {
-    float y = __fsub_rn(v, c);
-    float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-}
-
-template <bool KAHAN>
-__device__ __forceinline__ void accumulate(const float4 &pt, const float4 &k0, const float4 &k1, const float4 &k2,
-                                           const float4 &k3, float (&acc)[10], float (&cmp)[10], uint32_t &pairs) {
-    const float dx = __fsub_rn(pt.x, k0.x), dy = __fsub_rn(pt.y, k0.y), dz = __fsub_rn(pt.z, k0.z);
-    const bool in = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) < k0.w;
-    const float u1 = fmaf(k1.z, dz, fmaf(k1.y, dy, k1.x * dx));
-    const float u2 = fmaf(k2.z, dz, fmaf(k2.y, dy, k2.x * dx));
-    const float u3 = fmaf(k3.z, dz, fmaf(k3.y, dy, k3.x * dx));
-    const float q = fmaf(k3.w * u3, u3, fmaf(k2.w * u2, u2, k1.w * u1 * u1));
-    const float s = in ? ex2_approx(-q) * pt.w : 0.f;
-    pairs += in;
-    const float s1 = s * u1, s2 = s * u2, s3 = s * u3;
-    if (KAHAN) {
-        kadd(acc[0], cmp[0], s);
-        kadd(acc[1], cmp[1], s1);
-        kadd(acc[2], cmp[2], s2);
-        kadd(acc[3], cmp[3], s3);
-        kadd(acc[4], cmp[4], s1 * u1);
-        kadd(acc[5], cmp[5], s1 * u2);
-        kadd(acc[6], cmp[6], s1 * u3);
-        kadd(acc[7], cmp[7], s2 * u2);
-        kadd(acc[8], cmp[8], s2 * u3);
-        kadd(acc[9], cmp[9], s3 * u3);
-    } else {
-        acc[0] += s;
-        acc[1] += s1;
-        acc[2] += s2;
-        acc[3] += s3;
-        acc[4] = fmaf(s1, u1, acc[4]);
-        acc[5] = fmaf(s1, u2, acc[5]);
-        acc[6] = fmaf(s1, u3, acc[6]);
-        acc[7] = fmaf(s2, u2, acc[7]);
-        acc[8] = fmaf(s2, u3, acc[8]);
-        acc[9] = fmaf(s3, u3, acc[9]);
-    }
-}
-
 template <bool KAHAN>
 __global__ void __launch_bounds__(kBwdThreads) k_moments(BwdArgs a) {
     constexpr int NW = kBwdThreads / 32;
@@ -260,45 +216,7 @@ __global__ void k_grad_epilogue(const float *p, const int32_t *m_dev, int cap, c
         const uint32_t np = warp_sum(has ? __float_as_uint(o[20]) : 0u);
         if (lane == 0) {
             pairs[j] = np;
-            const float w = p[PW * cap + j];
-            const float d[3] = {p[PD1 * cap + j], p[PD2 * cap + j], p[PD3 * cap + j]};
-            float sx, cx, sy, cy, sz, cz;
-            sincosf(p[PTX * cap + j], &sx, &cx);
-            sincosf(p[PTY * cap + j], &sy, &cy);
-            sincosf(p[PTZ * cap + j], &sz, &cz);
-            const float R[9] = {cx * cy, -cz * sx - sy * sz * cx, sx * sz - cx * cz * sy,
-                                cy * sx, cx * cz - sx * sy * sz, -sz * cx - cz * sx * sy,
-                                sy,      cy * sz,                cy * cz};
-            // derivatives of the App. A entries with respect to theta_y and theta_z
-            const float Ry[9] = {-cx * sy, -cx * cy * sz, -cx * cy * cz, -sx * sy, -sx * cy * sz,
-                                 -sx * cy * cz, cy, -sy * sz, -sy * cz};
-            const float Rz[9] = {0.f, R[2], -R[1], 0.f, R[5], -R[4], 0.f, R[8], -R[7]};
-            const float aw = w * fabsf(w);
-            const float M2[3][3] = {{M[4], M[5], M[6]}, {M[5], M[7], M[8]}, {M[6], M[8], M[9]}};
-            grad[PW * cap + j] = 4.f * fabsf(w) * M[0];
-            for (int k = 0; k < 3; ++k) grad[(PD1 + k) * cap + j] = -4.f * aw * d[k] * M2[k][k];
-            for (int k = 0; k < 3; ++k) {
-                float v = 0.f;
-                for (int l = 0; l < 3; ++l) v = fmaf(R[3 * l + k] * d[l] * d[l], M[1 + l], v);
-                grad[(PCX + k) * cap + j] = 4.f * aw * v;
-            }
-            // dtheta = -4 a sum_kl d_k^2 K_kl M2_kl with K = (dR/dtheta) R^T;
-            // for theta_x, K is the constant generator [[0,-1,0],[1,0,0],[0,0,0]].
-            float gy = 0.f, gz = 0.f;
-            for (int r = 0; r < 3; ++r)
-                for (int c = 0; c < 3; ++c) {
-                    const float Ky =
-                        Ry[3 * r] * R[3 * c] + Ry[3 * r + 1] * R[3 * c + 1] + Ry[3 * r + 2] * R[3 * c + 2];
-                    const float Kz =
-                        Rz[3 * r] * R[3 * c] + Rz[3 * r + 1] * R[3 * c + 1] + Rz[3 * r + 2] * R[3 * c + 2];
-                    const float f = d[r] * d[r] * M2[r][c];
-                    gy = fmaf(f, Ky, gy);
-                    gz = fmaf(f, Kz, gz);
-                }
-            const float gx = (d[1] * d[1] - d[0] * d[0]) * M2[0][1];
-            grad[PTX * cap + j] = -4.f * aw * gx;
-            grad[PTY * cap + j] = -4.f * aw * gy;
-            grad[PTZ * cap + j] = -4.f * aw * gz;
+            grad_from_moments(p, cap, j, M, grad);
         }
     }
     __syncthreads();

@@ -104,22 +104,39 @@ __global__ void k_count_cells(const uint32_t *keys, int64_t n, uint32_t *cnt) {
         atomicAdd(&cnt[keys[k]], 1u);
 }
 
-// tiles per super cell (for the scan that numbers the tiles)
-__global__ void k_super_tiles(const uint32_t *cell_start, int nsuper, int cps, uint32_t *stile, uint32_t *maxt) {
+// tiles and forward work items per super cell (for the scans that number them)
+__global__ void k_super_tiles(const uint32_t *cell_start, int nsuper, int cps, uint32_t *stile, uint32_t *sitem,
+                              uint32_t *maxt) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsuper; s += gridDim.x * blockDim.x) {
         uint32_t b = cell_start[(int64_t)s * cps], e = cell_start[(int64_t)(s + 1) * cps];
-        stile[s] = (e - b + kTile - 1) / kTile;
-        atomicMax(maxt, stile[s]);
+        const uint32_t nt = (e - b + kTile - 1) / kTile;
+        stile[s] = nt;
+        sitem[s] = (nt + 1) / 2;
+        atomicMax(maxt, nt);
     }
 }
 
-__global__ void k_fill_tiles(const uint32_t *cell_start, const uint32_t *stile0, int nsuper, int cps,
-                             uint32_t *tile_super, uint32_t *tile_start) {
+// Tiles of each super cell, and its work items: the tiles at even offsets
+// (with the following tile, if any, as the item's second tile).  Items start
+// in natural order with zero cost.
+__global__ void k_fill_tiles(const uint32_t *cell_start, const uint32_t *stile0, const uint32_t *sitem0, int nsuper,
+                             int cps, uint32_t *tile_super, uint32_t *tile_start, uint4 *item_rec,
+                             uint32_t *item_cost, uint4 *order_rec) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsuper; s += gridDim.x * blockDim.x) {
-        uint32_t t0 = stile0[s], t1 = stile0[s + 1], p0 = cell_start[(int64_t)s * cps];
+        const uint32_t t0 = stile0[s], t1 = stile0[s + 1], i0 = sitem0[s];
+        const uint32_t p0 = cell_start[(int64_t)s * cps], pe = cell_start[(int64_t)(s + 1) * cps];
         for (uint32_t t = t0; t < t1; ++t) {
+            const uint32_t ps = p0 + (t - t0) * kTile;
             tile_super[t] = (uint32_t)s;
-            tile_start[t] = p0 + (t - t0) * kTile;
+            tile_start[t] = ps;
+            if (((t - t0) & 1u) == 0) {
+                const uint32_t it = i0 + (t - t0) / 2;
+                const uint32_t np = min(pe - ps, 2u * kTile);
+                const uint4 r = make_uint4(t, (uint32_t)s, ps, np | (it << 7));
+                item_rec[it] = r;
+                item_cost[it] = 0u;
+                order_rec[it] = r;
+            }
         }
     }
 }
@@ -252,18 +269,25 @@ extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, 
     if (rc) return rc;
     uint32_t *maxt = ws->counters + 8;
     cudaMemsetAsync(maxt, 0, sizeof(uint32_t), s);
-    k_super_tiles<<<gsz(nsuper, 256), 256, 0, s>>>(ws->cell_start, (int)nsuper, cps, ws->super_tile0, maxt);
+    k_super_tiles<<<gsz(nsuper, 256), 256, 0, s>>>(ws->cell_start, (int)nsuper, cps, ws->super_tile0,
+                                                   ws->super_item0, maxt);
     rc = launch_exscan_u32(ws->super_tile0, nsuper, s);
     if (rc) return rc;
-    k_fill_tiles<<<gsz(nsuper, 256), 256, 0, s>>>(ws->cell_start, ws->super_tile0, (int)nsuper, cps,
-                                                  ws->tile_super, ws->tile_start);
+    rc = launch_exscan_u32(ws->super_item0, nsuper, s);
+    if (rc) return rc;
+    k_fill_tiles<<<gsz(nsuper, 256), 256, 0, s>>>(ws->cell_start, ws->super_tile0, ws->super_item0, (int)nsuper, cps,
+                                                  ws->tile_super, ws->tile_start, ws->item_rec, ws->item_cost,
+                                                  ws->order_rec);
     SERBF_CHECK_LAUNCH();
-    uint32_t nt = 0, mt = 0;
+    uint32_t nt = 0, mt = 0, ni = 0;
     if (cudaMemcpyAsync(&nt, ws->super_tile0 + nsuper, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SERBF_ECUDA;
+    if (cudaMemcpyAsync(&ni, ws->super_item0 + nsuper, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return SERBF_ECUDA;
     if (cudaMemcpyAsync(&mt, maxt, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess) return SERBF_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return SERBF_ECUDA;
-    if ((int64_t)nt > ws->max_tiles) return SERBF_ECAPACITY;
+    if ((int64_t)nt > ws->max_tiles || ni >= (1u << 25)) return SERBF_ECAPACITY;  // item ids have 25 bits
+    ws->nitems = ni;
     ws->ntiles = nt;
     ws->max_chunks = (int32_t)((mt + kTile - 1) / kTile);
     if (nt > 0)

@@ -12,10 +12,11 @@ namespace serbf {
 constexpr uint64_t kMagic = 0x53455242465753ull;  // "SERBFWS"
 constexpr int kTile = 32;                         // points per forward/backward tile (one warp)
 constexpr int kSortTile = 4096;                   // elements per radix-sort block
-constexpr int kFwdWarps = 2;                      // warps (tiles) per forward block
 constexpr int kQueue = 64;                        // per-warp ring of staged candidates
 constexpr int kFwdGroup = 64;                     // tiles per first-level forward reduction group
-constexpr int kFwdBlocksPerSM = 16;               // resident forward blocks per SM (register bound)
+constexpr int kItemBuckets = 129;                 // cost classes of the forward's heavy-first order
+constexpr float kFixScale = 68719476736.f;        // 2^36: fixed-point unit of the fused adjoint's moments
+constexpr double kFixUnit = 1.0 / 68719476736.0;
 constexpr int kBwdThreads = 64;                   // threads per adjoint block
 constexpr int kBwdSplit = 16;                     // most blocks per kernel in the adjoint
 constexpr int kBwdWarpsPerKernel = kBwdSplit * kBwdThreads / 32;  // == 32, one epilogue lane each
@@ -52,14 +53,26 @@ struct serbf_workspace {
     int32_t binned;
     int64_t npoints;
     int64_t ntiles;
+    int64_t nitems;      // forward work items (one or two tiles of one super cell)
     int32_t sm_count;
     int32_t max_chunks;  // most 32-tile chunks in one super cell
+    // side stream for work that overlaps the main stream inside one call
+    // (fork and join through the two events; capturable into a CUDA graph)
+    cudaStream_t aux;
+    cudaEvent_t ev_fork, ev_join;
     // binning
     uint32_t *keys0, *keys1, *vals0, *vals1, *hist;
     uint32_t *cell_start;   // nsuper * sf^3 + 1 (super-major cell order)
     uint32_t *super_tile0;  // nsuper + 1: first tile of each super cell
     uint32_t *tile_super, *tile_start;
     float4 *tile_lo, *tile_hi;
+    // forward work items: tiles at even offsets within their super cell,
+    // taken together with the next tile of the same super cell if any.
+    // Item record: (first tile, super cell, first point, points | item << 7).
+    uint32_t *super_item0;  // nsuper + 1: first item of each super cell
+    uint4 *item_rec;        // record of each item, in item order
+    uint32_t *item_cost;    // work measured by the last forward (0 after binning)
+    uint4 *order_rec;       // item records by decreasing cost (heavy first)
     float4 *sup_lo, *sup_hi;
     // per-kernel records
     float4 *kfwd;  // 3 per kernel
@@ -71,6 +84,8 @@ struct serbf_workspace {
     serbf::FwdPart *fwd_gpart;    // max_tiles / kFwdGroup + 1
     uint32_t *fwd_group_done;     // max_tiles / kFwdGroup + 1 (kept zero between launches)
     unsigned long long *bwd_pairs;
+    unsigned long long *adj_fix;    // max_kernels x 10: fixed-point moments of the fused adjoint
+    unsigned long long *adj_pairs;  // [8]: [0] adjoint pairs of the fused adjoint
     float *moments;     // max_kernels x kBwdWarpsPerKernel x 22 (float-float partial moments, pairs)
     float4 *nzrec;      // per 32-tile chunk of a super cell: packed (box, count, id) of its tiles
                         // with nonzero residuals, at the chunk's own slots (2 float4 per tile)
@@ -220,6 +235,187 @@ __device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t *tmp, uint
     if (total) *total = tmp[32];
     __syncthreads();
     return r;
+}
+
+// Cost class of a forward work item: 4 classes per octave of the measured cost.
+__device__ __forceinline__ int cost_bucket(uint32_t c) {
+    if (!c) return 0;
+    const int e = 31 - __clz(c);
+    const uint32_t f = e >= 2 ? (c >> (e - 2)) & 3u : (c << (2 - e)) & 3u;
+    return 1 + 4 * e + (int)f;  // 1 .. 128
+}
+
+// Heavy-first order of the forward's work items from the costs the last
+// forward measured: a counting sort by cost class, descending, run by one
+// block of blockDim.x = 32 * kOrderWarps threads.  Any order is correct --
+// each item is evaluated by one group of warps and the loss partials are
+// reduced by tile index -- the order only balances the persistent forward.
+// Each warp counts its share of the items in a private histogram, so the
+// shared-memory atomics only collide within a warp; each warp loads 8 x 32
+// costs and records at a time.
+constexpr int kOrderWarps = 32;
+struct OrderSmem {
+    uint32_t wh[kItemBuckets][kOrderWarps];  // per class, per warp: counts, then cursors
+    uint32_t tot[kItemBuckets];              // per class: count, then first position
+};
+
+__device__ __forceinline__ void order_items(const uint32_t *cost, const uint4 *rec, uint4 *order, int64_t nitems,
+                                            OrderSmem &sm) {
+    constexpr int U = 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < kItemBuckets * kOrderWarps; q += blockDim.x) (&sm.wh[0][0])[q] = 0u;
+    __syncthreads();
+    const int64_t per_round = (int64_t)kOrderWarps * 32 * U;
+    for (int64_t base = (int64_t)warp * 32 * U; base < nitems; base += per_round) {
+        int bk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = base + 32 * u + lane;
+            bk[u] = i < nitems ? cost_bucket(__ldcg(cost + i)) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (bk[u] >= 0) atomicAdd(&sm.wh[bk[u]][warp], 1u);
+    }
+    __syncthreads();
+    // class totals (warp w handles classes w, w + 32, ...; lanes are warps)
+    for (int b = warp; b < kItemBuckets; b += kOrderWarps) {
+        const uint32_t v = sm.wh[b][lane];
+        const uint32_t inc = warp_iscan(v);
+        sm.wh[b][lane] = inc - v;  // exclusive prefix over warps
+        if (lane == 31) sm.tot[b] = inc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // first position of each class: classes in descending order; lane l
+        // owns classes kItemBuckets-1-5l ... kItemBuckets-5-5l
+        uint32_t v[5], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const int b = kItemBuckets - 1 - (5 * lane + q);
+            v[q] = b >= 0 ? sm.tot[b] : 0u;
+            sum += v[q];
+        }
+        uint32_t run = warp_iscan(sum) - sum;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const int b = kItemBuckets - 1 - (5 * lane + q);
+            if (b >= 0) sm.tot[b] = run;
+            run += v[q];
+        }
+    }
+    __syncthreads();
+    for (int b = warp; b < kItemBuckets; b += kOrderWarps) sm.wh[b][lane] += sm.tot[b];
+    __syncthreads();
+    for (int64_t base = (int64_t)warp * 32 * U; base < nitems; base += per_round) {
+        int bk[U];
+        uint4 r[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = base + 32 * u + lane;
+            bk[u] = -1;
+            if (i < nitems) {
+                bk[u] = cost_bucket(__ldcg(cost + i));
+                r[u] = rec[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (bk[u] >= 0) order[atomicAdd(&sm.wh[bk[u]][warp], 1u)] = r[u];
+    }
+}
+
+// ---------------------------------------------------------------- adjoint helpers
+// One adjoint pair: point (x, y, z, E) against a kernel record k0 = (c, r2),
+// k1..k3 = rows of R with e_k = log2(e) d_k^2 in .w.  Adds s = phi E and its
+// moments in the rotated frame u = R (v - c): S0, M1 (3), M2 (6, upper).
+__device__ __forceinline__ void kadd(float &s, float &c, float v) {
+    float y = __fsub_rn(v, c);
+    float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+template <bool KAHAN>
+__device__ __forceinline__ void accumulate(const float4 &pt, const float4 &k0, const float4 &k1, const float4 &k2,
+                                           const float4 &k3, float (&acc)[10], float (&cmp)[10], uint32_t &pairs) {
+    const float dx = __fsub_rn(pt.x, k0.x), dy = __fsub_rn(pt.y, k0.y), dz = __fsub_rn(pt.z, k0.z);
+    const bool in = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) < k0.w;
+    const float u1 = fmaf(k1.z, dz, fmaf(k1.y, dy, k1.x * dx));
+    const float u2 = fmaf(k2.z, dz, fmaf(k2.y, dy, k2.x * dx));
+    const float u3 = fmaf(k3.z, dz, fmaf(k3.y, dy, k3.x * dx));
+    const float q = fmaf(k3.w * u3, u3, fmaf(k2.w * u2, u2, k1.w * u1 * u1));
+    const float s = in ? ex2_approx(-q) * pt.w : 0.f;
+    pairs += in;
+    const float s1 = s * u1, s2 = s * u2, s3 = s * u3;
+    if (KAHAN) {
+        kadd(acc[0], cmp[0], s);
+        kadd(acc[1], cmp[1], s1);
+        kadd(acc[2], cmp[2], s2);
+        kadd(acc[3], cmp[3], s3);
+        kadd(acc[4], cmp[4], s1 * u1);
+        kadd(acc[5], cmp[5], s1 * u2);
+        kadd(acc[6], cmp[6], s1 * u3);
+        kadd(acc[7], cmp[7], s2 * u2);
+        kadd(acc[8], cmp[8], s2 * u3);
+        kadd(acc[9], cmp[9], s3 * u3);
+    } else {
+        acc[0] += s;
+        acc[1] += s1;
+        acc[2] += s2;
+        acc[3] += s3;
+        acc[4] = fmaf(s1, u1, acc[4]);
+        acc[5] = fmaf(s1, u2, acc[5]);
+        acc[6] = fmaf(s1, u3, acc[6]);
+        acc[7] = fmaf(s2, u2, acc[7]);
+        acc[8] = fmaf(s2, u3, acc[8]);
+        acc[9] = fmaf(s3, u3, acc[9]);
+    }
+}
+
+// The ten App. A gradients of kernel j from its moments (a = w|w|):
+//     dL2/dw     =  4 |w| S0
+//     dL2/dd_k   = -4 a d_k (M2)_kk
+//     dL2/dc     =  4 a R^T (d^2 . M1)
+//     dL2/dtheta = -4 a sum_kl d_k^2 K_kl (M2)_kl,   K = (dR/dtheta) R^T
+// (theta_x: K is constant and the sum is (d_2^2 - d_1^2) (M2)_12).
+__device__ __forceinline__ void grad_from_moments(const float *p, int cap, int j, const float (&M)[10], float *grad) {
+    const float w = p[PW * cap + j];
+    const float d[3] = {p[PD1 * cap + j], p[PD2 * cap + j], p[PD3 * cap + j]};
+    float sx, cx, sy, cy, sz, cz;
+    sincosf(p[PTX * cap + j], &sx, &cx);
+    sincosf(p[PTY * cap + j], &sy, &cy);
+    sincosf(p[PTZ * cap + j], &sz, &cz);
+    const float R[9] = {cx * cy, -cz * sx - sy * sz * cx, sx * sz - cx * cz * sy,
+                        cy * sx, cx * cz - sx * sy * sz, -sz * cx - cz * sx * sy,
+                        sy,      cy * sz,                cy * cz};
+    // derivatives of the App. A entries with respect to theta_y and theta_z
+    const float Ry[9] = {-cx * sy, -cx * cy * sz, -cx * cy * cz, -sx * sy, -sx * cy * sz,
+                         -sx * cy * cz, cy, -sy * sz, -sy * cz};
+    const float Rz[9] = {0.f, R[2], -R[1], 0.f, R[5], -R[4], 0.f, R[8], -R[7]};
+    const float aw = w * fabsf(w);
+    const float M2[3][3] = {{M[4], M[5], M[6]}, {M[5], M[7], M[8]}, {M[6], M[8], M[9]}};
+    grad[PW * cap + j] = 4.f * fabsf(w) * M[0];
+    for (int k = 0; k < 3; ++k) grad[(PD1 + k) * cap + j] = -4.f * aw * d[k] * M2[k][k];
+    for (int k = 0; k < 3; ++k) {
+        float v = 0.f;
+        for (int l = 0; l < 3; ++l) v = fmaf(R[3 * l + k] * d[l] * d[l], M[1 + l], v);
+        grad[(PCX + k) * cap + j] = 4.f * aw * v;
+    }
+    // for theta_x, K is the constant generator [[0,-1,0],[1,0,0],[0,0,0]]
+    float gy = 0.f, gz = 0.f;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            const float Ky = Ry[3 * r] * R[3 * c] + Ry[3 * r + 1] * R[3 * c + 1] + Ry[3 * r + 2] * R[3 * c + 2];
+            const float Kz = Rz[3 * r] * R[3 * c] + Rz[3 * r + 1] * R[3 * c + 1] + Rz[3 * r + 2] * R[3 * c + 2];
+            const float f = d[r] * d[r] * M2[r][c];
+            gy = fmaf(f, Ky, gy);
+            gz = fmaf(f, Kz, gz);
+        }
+    const float gx = (d[1] * d[1] - d[0] * d[0]) * M2[0][1];
+    grad[PTX * cap + j] = -4.f * aw * gx;
+    grad[PTY * cap + j] = -4.f * aw * gy;
+    grad[PTZ * cap + j] = -4.f * aw * gz;
 }
 
 // Cell-index bounding box of a kernel's support sphere (with one cell of

@@ -1,14 +1,21 @@
 // Point-major forward (Eq. 3-26) over the support pairs of Eq. 3-15-1, the
 // point filter of Eq. 3-18 and the loss terms of Eq. 3-19.
 //
-// One warp per 32-point tile; lanes are points.  The warp streams its super
-// cell's candidate list (ascending kernel index), keeps the kernels whose
-// support reaches the tile's bounding box (one candidate per lane, ballot),
-// and gathers their records with float4 loads into a per-warp shared-memory
-// ring.  Each full batch of 32 staged kernels is then evaluated with warp-wide
-// broadcast reads: every lane applies the exact support predicate to its own
-// point, so the pairs summed are exactly the point-major neighbour rows, in
-// ascending kernel order.
+// Work item = up to two consecutive 32-point tiles of one super cell; each
+// lane holds one point of each tile.  The warp streams
+// its super cell's candidate list (ascending kernel index), keeps the kernels
+// whose support reaches the item's bounding box (one candidate per lane,
+// ballot), and stages their records in a per-warp shared-memory ring, in
+// pairs.  Each batch of 32 staged kernels is then evaluated with broadcast
+// 16-byte loads and packed f32x2 arithmetic (two kernels per instruction,
+// two points per lane), so every shared-memory load serves four pairs.  A
+// kernel whose support covers the whole box skips the predicate; otherwise
+// every lane applies the exact support predicate to its own points, so the
+// pairs summed are exactly the point-major neighbour rows.
+//
+// Persistent blocks take items heaviest first (order from the costs measured
+// by the previous launch) to keep the tail short; the warps of a block split
+// an item's candidate list and combine their sums in a fixed order.
 #include <math.h>
 
 #include "common.cuh"
@@ -19,11 +26,16 @@ namespace {
 
 struct FwdArgs {
     const float *x, *y, *z, *t;
-    const uint32_t *tile_super, *tile_start, *cell_start;
+    const uint32_t *tile_super, *tile_start, *cell_start, *stile0;
     const float4 *tile_lo, *tile_hi;
     const uint32_t *slist, *scnt;
     const float4 *kfwd;
-    int64_t ntiles;
+    const float4 *kbwd;      // adjoint records (c, r2), rows of R with log2(e) d_k^2
+    const uint4 *order_rec;  // item records, heaviest first
+    unsigned long long *adj_fix;    // fixed-point moments (fused adjoint)
+    unsigned long long *adj_pairs;  // adjoint pair count (fused adjoint)
+    uint32_t *item_cost;
+    int64_t ntiles, nitems;
     int scap, cps;
     float tau1, tau2;  // tau1 rounded down, tau2 rounded up to float: exact double decisions
     float *psi, *err;
@@ -32,9 +44,73 @@ struct FwdArgs {
     FwdPart *gpart;       // one partial per group of kFwdGroup tiles
     uint32_t *group_done; // tiles finished per group
     uint32_t *counter;    // groups finished
-    uint32_t *tile_next;  // next tile to take (zeroed before each launch)
+    uint32_t *item_next;  // next work item to take (zeroed before each launch)
     double *stats;
 };
+
+// Two float32 lanes in one 64-bit register: the packed f32x2 arithmetic of
+// sm_100+ does two IEEE round-to-nearest operations per instruction, each
+// bit-identical to its scalar counterpart.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Staged kernels are stored in pairs, interleaved so that one 16-byte load
+// gives the same field of both kernels (a packed f32x2 operand).  Field v of
+// the kernel in ring slot s is at float 24 (s / 2) + 2 v + s % 2, with fields
+// cx, cy, cz, r2, Q11, Q22, Q33, a = w|w|, 2Q12, 2Q13, 2Q23 (v = 0 .. 10).
+constexpr int kPairFloats = 24;
+
+__device__ __forceinline__ void stage(float *ring, int slot, float4 k0, float4 k1, float4 k2) {
+    float *b = ring + kPairFloats * (slot >> 1) + (slot & 1);
+    b[0] = k0.x;
+    b[2] = k0.y;
+    b[4] = k0.z;
+    b[6] = k0.w;
+    b[8] = k1.x;
+    b[10] = k1.y;
+    b[12] = k1.z;
+    b[14] = k1.w;
+    b[16] = k2.x;
+    b[18] = k2.y;
+    b[20] = k2.z;
+}
+
+// The empty partner of an odd last kernel: q = 0, a = 0 and r2 < 0, so it
+// adds exactly zero and is never counted.
+__device__ __forceinline__ void stage_empty(float *ring, int slot) {
+    float *b = ring + kPairFloats * (slot >> 1) + (slot & 1);
+#pragma unroll
+    for (int v = 0; v < 11; ++v) b[2 * v] = 0.f;
+    b[6] = -1.f;
+}
 
 // Squared distance from c to the farthest corner of a box, rounded so that
 // it is never below the float squared distance of any point inside the box:
@@ -46,135 +122,41 @@ __device__ __forceinline__ float box_far_d2(float cx, float cy, float cz, float4
     return __fadd_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)), __fmul_rn(az, az));
 }
 
-// Up to 32 kernels whose support only partly covers the tile: exact predicate per lane.
-template <int UNROLL>
-__device__ __forceinline__ void eval_partial(const float4 (*ring)[3], int cnt, float px, float py, float pz,
-                                            float &acc, uint32_t &n) {
+// npairs staged kernel pairs from pair index pb against the lane's two
+// points.  PARTIAL: the support only partly covers the item box, so each
+// pair takes the exact Eq. 3-15-1 predicate (same float operations as the
+// scalar test: fl(fl(fl(dx^2) + fl(dy^2)) + fl(dz^2)) < r2).
+template <bool PARTIAL, int UNROLL>
+__device__ __forceinline__ void eval_pairs(const float *ring, int pb, int npairs, const f2 (&P)[2][3], f2 (&acc)[2],
+                                           uint32_t (&n)[2]) {
 #pragma unroll UNROLL
-    for (int q = 0; q < cnt; ++q) {
-        {
-            const float4 k0 = ring[q][0], k1 = ring[q][1], k2 = ring[q][2];
-            const float dx = __fsub_rn(px, k0.x), dy = __fsub_rn(py, k0.y), dz = __fsub_rn(pz, k0.z);
-            const float xx = __fmul_rn(dx, dx), yy = __fmul_rn(dy, dy), zz = __fmul_rn(dz, dz);
-            const bool in = __fadd_rn(__fadd_rn(xx, yy), zz) < k0.w;
+    for (int q = 0; q < npairs; ++q) {
+        const ulonglong2 *r = reinterpret_cast<const ulonglong2 *>(ring + kPairFloats * (pb + q));
+        const ulonglong2 F0 = r[0], F1 = r[1], F2 = r[2], F3 = r[3], F4 = r[4], F5 = r[5];
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const f2 dx = f2_sub(P[p][0], F0.x), dy = f2_sub(P[p][1], F0.y), dz = f2_sub(P[p][2], F1.x);
+            const f2 zz = f2_mul(dz, dz);
             // q = dv^T Q dv (log2 units): dx (Q11 dx + 2Q12 dy + 2Q13 dz) + dy (Q22 dy + 2Q23 dz) + Q33 dz^2
-            const float ra = fmaf(k2.y, dz, fmaf(k2.x, dy, k1.x * dx));
-            const float rb = fmaf(k2.z, dz, k1.y * dy);
-            const float qv = fmaf(k1.z, zz, fmaf(dy, rb, dx * ra));
-            const float phi = ex2_approx(-qv);
-            acc = in ? fmaf(k1.w, phi, acc) : acc;
-            n += in;
-        }
-    }
-}
-
-// Up to 32 kernels whose support covers the whole tile box: no predicate needed.
-template <int UNROLL>
-__device__ __forceinline__ void eval_full(const float4 (*ring)[3], int cnt, float px, float py, float pz,
-                                         float &acc) {
-#pragma unroll UNROLL
-    for (int q = 0; q < cnt; ++q) {
-        {
-            const float4 k0 = ring[q][0], k1 = ring[q][1], k2 = ring[q][2];
-            const float dx = px - k0.x, dy = py - k0.y, dz = pz - k0.z;
-            const float ra = fmaf(k2.y, dz, fmaf(k2.x, dy, k1.x * dx));
-            const float rb = fmaf(k2.z, dz, k1.y * dy);
-            const float qv = fmaf(k1.z, dz * dz, fmaf(dy, rb, dx * ra));
-            acc = fmaf(k1.w, ex2_approx(-qv), acc);
-        }
-    }
-}
-
-struct TileOut {
-    float l2, mx;
-    uint32_t cnt, pairs;
-};
-
-// One tile (32 binned points) on one warp: stream the super cell's candidate
-// list, stage the kernels that reach the tile box, evaluate, write psi, E and
-// the mask.  Returns this lane's loss contributions.
-__device__ __forceinline__ TileOut forward_tile(const FwdArgs &a, int64_t tile, float4 (*ringP)[3],
-                                                float4 (*ringF)[3], int lane) {
-    TileOut out{0.f, 0.f, 0u, 0u};
-    const unsigned lt = (1u << lane) - 1u;
-    const uint32_t sup = a.tile_super[tile];
-    const uint32_t p0 = a.tile_start[tile], pe = a.cell_start[(int64_t)(sup + 1) * a.cps];
-    const int64_t i = (int64_t)p0 + lane;
-    const bool valid = i < (int64_t)pe;
-    // invalid lanes carry NaN so the support test fails for them
-    const float px = valid ? a.x[i] : __int_as_float(0x7fc00000);
-    const float py = valid ? a.y[i] : 0.f;
-    const float pz = valid ? a.z[i] : 0.f;
-    const float4 lo = a.tile_lo[tile], hi = a.tile_hi[tile];
-    const uint32_t *lst = a.slist + (size_t)sup * a.scap;
-    const int L = min((int)a.scnt[sup], a.scap);
-    int hp = 0, qp = 0, hf = 0, qf = 0;
-    uint32_t nfull = 0, np = 0;
-    float acc = 0.f;
-    uint32_t jn = lane < L ? lst[lane] : 0u;
-    for (int b = 0; b < L; b += 32) {
-        const uint32_t j = jn;
-        const bool live = b + lane < L;
-        if (b + 32 + lane < L) jn = lst[b + 32 + lane];  // prefetch the next chunk
-        bool part = false, full = false;
-        float4 k0;
-        if (live) {
-            k0 = a.kfwd[3 * j];
-            if (box_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w) {
-                full = box_far_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w;
-                part = !full;
+            const f2 ra = f2_fma(F4.y, dz, f2_fma(F4.x, dy, f2_mul(F2.x, dx)));
+            const f2 rb = f2_fma(F5.x, dz, f2_mul(F2.y, dy));
+            const f2 qv = f2_fma(F3.x, zz, f2_fma(dy, rb, f2_mul(dx, ra)));
+            float q0, q1;
+            f2_unpack(qv, q0, q1);
+            float e0 = ex2_approx(-q0), e1 = ex2_approx(-q1);
+            if (PARTIAL) {
+                const f2 d2 = f2_add(f2_add(f2_mul(dx, dx), f2_mul(dy, dy)), zz);
+                float d0, d1, r0, r1;
+                f2_unpack(d2, d0, d1);
+                f2_unpack(F1.y, r0, r1);
+                const bool i0 = d0 < r0, i1 = d1 < r1;
+                e0 = i0 ? e0 : 0.f;
+                e1 = i1 ? e1 : 0.f;
+                n[p] += (uint32_t)i0 + (uint32_t)i1;
             }
-        }
-        const unsigned bp = __ballot_sync(0xffffffffu, part), bf = __ballot_sync(0xffffffffu, full);
-        if (part || full) {
-            float4(*ring)[3] = part ? ringP : ringF;
-            const int slot = part ? ((hp + qp + __popc(bp & lt)) & (kQueue - 1))
-                                  : ((hf + qf + __popc(bf & lt)) & (kQueue - 1));
-            ring[slot][0] = k0;
-            ring[slot][1] = a.kfwd[3 * j + 1];
-            ring[slot][2] = a.kfwd[3 * j + 2];
-        }
-        qp += __popc(bp);
-        qf += __popc(bf);
-        __syncwarp();
-        if (qp >= 32) {
-            eval_partial<8>(ringP + hp, 32, px, py, pz, acc, np);
-            hp ^= 32;
-            qp -= 32;
-        }
-        if (qf >= 32) {
-            eval_full<8>(ringF + hf, 32, px, py, pz, acc);
-            hf ^= 32;
-            qf -= 32;
-            nfull += 32;
-        }
-        __syncwarp();
-    }
-    // leftovers: head is 0 or 32 and fewer than 32 remain, so they do not wrap
-    if (qp > 0) eval_partial<1>(ringP + hp, qp, px, py, pz, acc, np);
-    if (qf > 0) {
-        eval_full<1>(ringF + hf, qf, px, py, pz, acc);
-        nfull += qf;
-    }
-    __syncwarp();
-    if (valid) {
-        out.pairs = np + nfull;
-        const float t = a.t[i], ps = acc;
-        const bool m0 = (a.tau1 < t) && (t < a.tau2);
-        const bool m1 = (t <= a.tau1) && (ps > a.tau1);
-        const bool m2 = (t >= a.tau2) && (ps < a.tau2);
-        const bool mk = m0 || m1 || m2;
-        const float e = mk ? __fsub_rn(ps, t) : 0.f;
-        a.psi[i] = ps;
-        a.err[i] = e;
-        a.mask[i] = (uint8_t)mk;
-        if (mk) {
-            out.l2 = e * e;
-            out.mx = fabsf(e);
-            out.cnt = 1;
+            acc[p] = f2_fma(F3.y, f2_pack(e0, e1), acc[p]);
         }
     }
-    return out;
 }
 
 // Fixed-order warp reduction of tile partials [b, e) into one partial.
@@ -195,76 +177,522 @@ __device__ __forceinline__ FwdPart reduce_parts(const FwdPart *p, uint32_t b, ui
     return FwdPart{l.hi, l.lo, mx, (uint32_t)c, pr};
 }
 
-// Persistent warps take tiles from a global counter (heavy and light tiles
-// balance out), write one partial per tile, and the partials are reduced in a
-// fixed order in two levels (groups of kFwdGroup tiles, then all groups), so
-// the loss terms are deterministic whatever warp handled which tile.
-__global__ void __launch_bounds__(kFwdWarps * 32) k_forward(FwdArgs a) {
-    // two rings per warp (kernels partly / fully covering the tile); a ring
-    // holds 64 staged records and is consumed 32 at a time from slot 0 or 32
-    __shared__ float4 ringP[kFwdWarps][kQueue][3];
-    __shared__ float4 ringF[kFwdWarps][kQueue][3];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// Loss terms of one tile: stored as the tile's partial.  The warp that
+// completes a group of kFwdGroup tiles reduces the group; the warp that
+// completes the last group writes the totals.  Sums run in tile order, so
+// they do not depend on which warp handled which tile.
+__device__ __forceinline__ void finish_tile(const FwdArgs &a, uint32_t t, float l2, float mx_l, uint32_t cnt_l,
+                                            uint32_t pairs_l, int lane) {
+    const ff l2s = warp_sum_ff(ff{l2, 0.f});
+    const float mx = warp_max(mx_l);
+    const uint32_t cnt = warp_sum(cnt_l), pr = warp_sum(pairs_l);
+    uint32_t done = 0;
+    if (lane == 0) {
+        a.part[t] = FwdPart{l2s.hi, l2s.lo, mx, cnt, (unsigned long long)pr};
+        __threadfence();
+        done = atomicAdd(a.group_done + t / kFwdGroup, 1u);
+    }
+    done = __shfl_sync(0xffffffffu, done, 0);
+    const uint32_t g = t / kFwdGroup;
+    const uint32_t gb = g * kFwdGroup;
+    const uint32_t ge = (uint32_t)min((int64_t)gb + kFwdGroup, a.ntiles);
+    if (done != ge - gb - 1) return;
+    __threadfence();
+    const FwdPart gp = reduce_parts(a.part, gb, ge, lane);
     const uint32_t ngroups = (uint32_t)((a.ntiles + kFwdGroup - 1) / kFwdGroup);
-    for (;;) {
-        uint32_t t = 0;
-        if (lane == 0) t = atomicAdd(a.tile_next, 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if ((int64_t)t >= a.ntiles) break;
-        const TileOut o = forward_tile(a, t, ringP[warp], ringF[warp], lane);
-        const ff l2 = warp_sum_ff(ff{o.l2, 0.f});
-        const float mx = warp_max(o.mx);
-        const uint32_t cnt = warp_sum(o.cnt), pr = warp_sum(o.pairs);
-        uint32_t done = 0;
-        if (lane == 0) {
-            a.part[t] = FwdPart{l2.hi, l2.lo, mx, cnt, (unsigned long long)pr};
-            __threadfence();
-            done = atomicAdd(a.group_done + t / kFwdGroup, 1u);
-        }
-        done = __shfl_sync(0xffffffffu, done, 0);
-        const uint32_t g = t / kFwdGroup;
-        const uint32_t gb = g * kFwdGroup;
-        const uint32_t ge = (uint32_t)min((int64_t)gb + kFwdGroup, a.ntiles);
-        if (done != ge - gb - 1) continue;
-        // this warp completed its group: reduce the group's partials
+    uint32_t gdone = 0;
+    if (lane == 0) {
+        a.gpart[g] = gp;
+        a.group_done[g] = 0u;
         __threadfence();
-        const FwdPart gp = reduce_parts(a.part, gb, ge, lane);
-        uint32_t gdone = 0;
-        if (lane == 0) {
-            a.gpart[g] = gp;
-            a.group_done[g] = 0u;
-            __threadfence();
-            gdone = atomicAdd(a.counter, 1u);
-        }
-        gdone = __shfl_sync(0xffffffffu, gdone, 0);
-        if (gdone != ngroups - 1) continue;
-        // the last group: fixed-order sum of all group partials
-        __threadfence();
-        const FwdPart tot = reduce_parts(a.gpart, 0, ngroups, lane);
-        if (lane == 0) {
-            a.stats[SERBF_STAT_L2] = (double)tot.l2hi + (double)tot.l2lo;
-            a.stats[SERBF_STAT_MAXE] = tot.maxe;
-            a.stats[SERBF_STAT_COUNT] = (double)tot.cnt;
-            a.stats[SERBF_STAT_PAIRS_FWD] = (double)tot.pairs;
-            *a.counter = 0u;
-        }
+        gdone = atomicAdd(a.counter, 1u);
+    }
+    gdone = __shfl_sync(0xffffffffu, gdone, 0);
+    if (gdone != ngroups - 1) return;
+    __threadfence();
+    const FwdPart tot = reduce_parts(a.gpart, 0, ngroups, lane);
+    if (lane == 0) {
+        a.stats[SERBF_STAT_L2] = (double)tot.l2hi + (double)tot.l2lo;
+        a.stats[SERBF_STAT_MAXE] = tot.maxe;
+        a.stats[SERBF_STAT_COUNT] = (double)tot.cnt;
+        a.stats[SERBF_STAT_PAIRS_FWD] = (double)tot.pairs;
+        *a.counter = 0u;
     }
 }
 
-}  // namespace
+// Eq. 3-18 filter and residual of one point; returns its loss contributions.
+__device__ __forceinline__ float point_out(const FwdArgs &a, int64_t i, bool valid, float ps, uint32_t np, float &l2,
+                                           float &mx, uint32_t &cnt, uint32_t &pairs) {
+    l2 = 0.f;
+    mx = 0.f;
+    cnt = 0u;
+    pairs = 0u;
+    if (!valid) return 0.f;
+    const float t = a.t[i];
+    const bool m0 = (a.tau1 < t) && (t < a.tau2);
+    const bool m1 = (t <= a.tau1) && (ps > a.tau1);
+    const bool m2 = (t >= a.tau2) && (ps < a.tau2);
+    const bool mk = m0 || m1 || m2;
+    const float e = mk ? __fsub_rn(ps, t) : 0.f;
+    a.psi[i] = ps;
+    a.err[i] = e;
+    a.mask[i] = (uint8_t)mk;
+    pairs = np;
+    if (mk) {
+        l2 = e * e;
+        mx = fabsf(e);
+        cnt = 1u;
+    }
+    return e;
+}
 
-extern "C" int serbf_forward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi,
-                             float *err, uint8_t *mask, double *stats, serbf_workspace *ws, void *stream) {
+// Item geometry shared by the warps of a block.
+struct ItemInfo {
+    uint32_t t0, sup, item;
+    int two;
+    int64_t i0, i1;
+    int v0, v1;
+};
+
+// Decode an item record (first tile, super cell, first point, points | item << 7).
+__device__ __forceinline__ ItemInfo item_info(uint4 r, int lane) {
+    ItemInfo it;
+    const uint32_t np = r.w & 127u;
+    it.t0 = r.x;
+    it.sup = r.y;
+    it.two = np > (uint32_t)kTile;
+    it.i0 = (int64_t)r.z + lane;
+    it.i1 = it.i0 + kTile;  // the second tile starts kTile points later
+    it.v0 = (uint32_t)lane < np;
+    it.v1 = (uint32_t)(lane + kTile) < np;
+    it.item = r.w >> 7;
+    return it;
+}
+
+// One warp's share of a work item: candidate chunks w, w + W, w + 2W, ... of
+// the super cell's list (32 candidates each) are filtered against the item
+// box, staged in pairs and evaluated against the lane's two points.
+// Returns the lane's partial sums and pair counts; *cost gets the warp's
+// measured work.
+template <int G>
+__device__ __forceinline__ void forward_share(const FwdArgs &a, const ItemInfo &it, int w, float *ringP, float *ringF,
+                                              int lane, f2 (&acc)[2], uint32_t (&n)[2], uint32_t &cost) {
+    const unsigned lt = (1u << lane) - 1u;
+    // invalid lanes carry NaN so the support test fails for them
+    const float qnan = __int_as_float(0x7fc00000);
+    f2 P[2][3];
+    {
+        const float x0 = it.v0 ? a.x[it.i0] : qnan, y0 = it.v0 ? a.y[it.i0] : 0.f, z0 = it.v0 ? a.z[it.i0] : 0.f;
+        const float x1 = it.v1 ? a.x[it.i1] : qnan, y1 = it.v1 ? a.y[it.i1] : 0.f, z1 = it.v1 ? a.z[it.i1] : 0.f;
+        P[0][0] = f2_pack(x0, x0);
+        P[0][1] = f2_pack(y0, y0);
+        P[0][2] = f2_pack(z0, z0);
+        P[1][0] = f2_pack(x1, x1);
+        P[1][1] = f2_pack(y1, y1);
+        P[1][2] = f2_pack(z1, z1);
+    }
+    float4 lo = a.tile_lo[it.t0], hi = a.tile_hi[it.t0];
+    if (it.two) {
+        const float4 l1 = a.tile_lo[it.t0 + 1], h1 = a.tile_hi[it.t0 + 1];
+        lo = make_float4(fminf(lo.x, l1.x), fminf(lo.y, l1.y), fminf(lo.z, l1.z), 0.f);
+        hi = make_float4(fmaxf(hi.x, h1.x), fmaxf(hi.y, h1.y), fmaxf(hi.z, h1.z), 0.f);
+    }
+    const uint32_t *lst = a.slist + (size_t)it.sup * a.scap;
+    const int L = min((int)a.scnt[it.sup], a.scap);
+    constexpr int kStride = 32 * G;
+    int hp = 0, qp = 0, hf = 0, qf = 0;
+    uint32_t nfull = 0, npart = 0;
+    acc[0] = 0ull;
+    acc[1] = 0ull;
+    n[0] = 0u;
+    n[1] = 0u;
+    // software pipeline: records of the next chunk and indices of the one
+    // after it are in flight while a chunk is filtered
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int b0 = 32 * w;
+    uint32_t jc = b0 + lane < L ? lst[b0 + lane] : 0u;
+    float4 c0 = zero4, c1 = zero4, c2 = zero4;
+    if (b0 + lane < L) {
+        c0 = a.kfwd[3 * jc];
+        c1 = a.kfwd[3 * jc + 1];
+        c2 = a.kfwd[3 * jc + 2];
+    }
+    uint32_t jn = b0 + kStride + lane < L ? lst[b0 + kStride + lane] : 0u;
+    int nchunks = 0;
+    for (int b = b0; b < L; b += kStride) {
+        const float4 k0 = c0, k1 = c1, k2 = c2;
+        const bool live = b + lane < L;
+        if (b + kStride + lane < L) {
+            c0 = a.kfwd[3 * jn];
+            c1 = a.kfwd[3 * jn + 1];
+            c2 = a.kfwd[3 * jn + 2];
+        }
+        if (b + 2 * kStride + lane < L) jn = lst[b + 2 * kStride + lane];
+        ++nchunks;
+        bool part = false, full = false;
+        if (live && box_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w) {
+            full = box_far_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w;
+            part = !full;
+        }
+        const unsigned bp = __ballot_sync(0xffffffffu, part), bf = __ballot_sync(0xffffffffu, full);
+        if (part) stage(ringP, (hp + qp + __popc(bp & lt)) & (kQueue - 1), k0, k1, k2);
+        if (full) stage(ringF, (hf + qf + __popc(bf & lt)) & (kQueue - 1), k0, k1, k2);
+        qp += __popc(bp);
+        qf += __popc(bf);
+        npart += __popc(bp);
+        nfull += __popc(bf);
+        __syncwarp();
+        if (qp >= 32) {
+            eval_pairs<true, 2>(ringP, hp >> 1, 16, P, acc, n);
+            hp ^= 32;
+            qp -= 32;
+        }
+        if (qf >= 32) {
+            eval_pairs<false, 2>(ringF, hf >> 1, 16, P, acc, n);
+            hf ^= 32;
+            qf -= 32;
+        }
+        __syncwarp();
+    }
+    // leftovers: the head is 0 or 32 and fewer than 32 remain, so they do not
+    // wrap; an odd count gets an empty partner
+    if (qp & 1) {
+        if (lane == 0) stage_empty(ringP, hp + qp);
+        __syncwarp();
+    }
+    if (qf & 1) {
+        if (lane == 0) stage_empty(ringF, hf + qf);
+        __syncwarp();
+    }
+    if (qp > 0) eval_pairs<true, 1>(ringP, hp >> 1, (qp + 1) >> 1, P, acc, n);
+    if (qf > 0) eval_pairs<false, 1>(ringF, hf >> 1, (qf + 1) >> 1, P, acc, n);
+    __syncwarp();
+    n[0] += nfull;
+    n[1] += nfull;
+    // about one unit per filtered candidate, ~6 per fully and ~9 per partly
+    // covering kernel
+    cost = 32u * (uint32_t)nchunks + 6u * nfull + 9u * npart;
+}
+
+// ---------------------------------------------------------------- fused adjoint
+// After an item's residuals are known, its points with E != 0 (at most 64,
+// in shared memory as (x, y, z, E)) are taken against the kernels of the
+// same candidate chunks whose support reaches their box: lanes are kernels,
+// each lane loops over the points and accumulates the ten App. A moments of
+// its kernel (the pair arithmetic of the kernel-major adjoint).  The item's
+// float partial moments go to per-kernel 64-bit fixed-point accumulators
+// (unit 2^-36) by integer atomics: integer addition is associative, so the
+// totals do not depend on the order in which items finish.
+
+// Lane = kernel q[(head + lane) % 64] for lane < cnt; all nz points.
+__device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *q, int head, int cnt,
+                                              const float4 *nzl, int nc0, int nc1, int lane, uint32_t &pairs) {
+    if (lane >= cnt) return;
+    const uint32_t j = q[(head + lane) & (kQueue - 1)];
+    const float4 k0 = a.kbwd[4 * j], k1 = a.kbwd[4 * j + 1], k2 = a.kbwd[4 * j + 2], k3 = a.kbwd[4 * j + 3];
+    float acc[10], cmp[10];
+#pragma unroll
+    for (int r = 0; r < 10; ++r) acc[r] = cmp[r] = 0.f;
+    uint32_t np = 0;
+    for (int p = 0; p < nc0; ++p) accumulate<false>(nzl[p], k0, k1, k2, k3, acc, cmp, np);
+    for (int p = 0; p < nc1; ++p) accumulate<false>(nzl[kTile + p], k0, k1, k2, k3, acc, cmp, np);
+    if (np) {
+        unsigned long long *o = a.adj_fix + 10 * (size_t)j;
+#pragma unroll
+        for (int r = 0; r < 10; ++r)
+            if (acc[r] != 0.f) atomicAdd(o + r, (unsigned long long)__float2ll_rn(acc[r] * kFixScale));
+        pairs += np;
+    }
+}
+
+// One warp's share of an item's adjoint: candidate chunks w, w + G, ... of
+// the super cell's list, filtered against the box of the nz points.
+template <int G>
+__device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &it, int w, const float4 *nzl, int nc0,
+                                              int nc1, float4 lo, float4 hi, uint32_t *q, int lane,
+                                              uint32_t &cost) {
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t *lst = a.slist + (size_t)it.sup * a.scap;
+    const int L = min((int)a.scnt[it.sup], a.scap);
+    constexpr int kStride = 32 * G;
+    int head = 0, qn = 0, nk = 0;
+    uint32_t pairs = 0;
+    for (int b = 32 * w; b < L; b += kStride) {
+        const bool live = b + lane < L;
+        const uint32_t j = live ? lst[b + lane] : 0u;
+        bool hit = false;
+        if (live) {
+            const float4 k0 = a.kbwd[4 * j];
+            hit = box_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) q[(head + qn + __popc(bal & lt)) & (kQueue - 1)] = j;
+        qn += __popc(bal);
+        nk += __popc(bal);
+        __syncwarp();
+        if (qn >= 32) {
+            adjoint_batch(a, q, head, 32, nzl, nc0, nc1, lane, pairs);
+            head = (head + 32) & (kQueue - 1);
+            qn -= 32;
+            __syncwarp();
+        }
+    }
+    if (qn > 0) adjoint_batch(a, q, head, qn, nzl, nc0, nc1, lane, pairs);
+    __syncwarp();
+    const uint32_t tot = warp_sum(pairs);
+    if (lane == 0 && tot) atomicAdd(a.adj_pairs, (unsigned long long)tot);
+    cost += (uint32_t)(nk * (nc0 + nc1)) / 4u + 32u;
+}
+
+// The nz points of one 32-point tile (lanes = points): compacted to nzl in
+// lane order; returns their count and box (empty: +inf / -inf).
+__device__ __forceinline__ int nz_tile(float4 *nzl, bool nz, float x, float y, float z, float e, int lane,
+                                       float4 &lo, float4 &hi) {
+    const unsigned bal = __ballot_sync(0xffffffffu, nz);
+    if (nz) nzl[__popc(bal & ((1u << lane) - 1u))] = make_float4(x, y, z, e);
+    float mnx = nz ? x : INFINITY, mny = nz ? y : INFINITY, mnz = nz ? z : INFINITY;
+    float mxx = nz ? x : -INFINITY, mxy = nz ? y : -INFINITY, mxz = nz ? z : -INFINITY;
+    if (bal) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+            mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+            mnz = fminf(mnz, __shfl_xor_sync(0xffffffffu, mnz, o));
+            mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+            mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+            mxz = fmaxf(mxz, __shfl_xor_sync(0xffffffffu, mxz, o));
+        }
+    }
+    lo = make_float4(mnx, mny, mnz, 0.f);
+    hi = make_float4(mxx, mxy, mxz, 0.f);
+    return __popc(bal);
+}
+
+__device__ __forceinline__ float4 box_min(float4 a, float4 b) {
+    return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), 0.f);
+}
+__device__ __forceinline__ float4 box_max(float4 a, float4 b) {
+    return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), 0.f);
+}
+
+// Persistent blocks take work items, heaviest first, from a global counter.
+// The G warps of a block share an item (its candidate list split by 32-entry
+// chunks); their partial sums are combined in warp order, so Psi does not
+// depend on timing.  G = 1 when there are enough items to balance the warps,
+// 2 or 4 for small problems.
+template <int G, bool ADJ>
+__global__ void __launch_bounds__(G * 32, 24 / G) k_forward(FwdArgs a) {
+    // two rings per warp (kernels partly / fully covering the item box); a
+    // ring holds 64 staged kernels (32 pairs), consumed 32 at a time from
+    // slot 0 or 32
+    __shared__ __align__(16) float ringP[G][(kQueue / 2) * kPairFloats];
+    __shared__ __align__(16) float ringF[G][(kQueue / 2) * kPairFloats];
+    __shared__ float2 red_psi[G][32];
+    __shared__ uint2 red_n[G][32];
+    __shared__ uint32_t red_cost[G];
+    __shared__ uint32_t s_k;
+    // fused adjoint: the item's nz points (tile 0 at 0, tile 1 at 32), their
+    // counts and boxes, and a per-warp queue of kernel indices
+    __shared__ float4 nzl[ADJ ? 2 * kTile : 1];
+    __shared__ int s_nc[2];
+    __shared__ float4 s_box[2][2];
+    __shared__ uint32_t adjq[ADJ ? G : 1][ADJ ? kQueue : 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_k = atomicAdd(a.item_next, 1u);
+    __syncthreads();
+    uint32_t k = s_k;
+    while ((int64_t)k < a.nitems) {
+        const ItemInfo it = item_info(a.order_rec[k], lane);
+        // the next item is claimed now; its index is only needed at the end
+        uint32_t knext = 0;
+        if (threadIdx.x == 0) knext = atomicAdd(a.item_next, 1u);
+        f2 acc[2];
+        uint32_t n[2], cost;
+        forward_share<G>(a, it, warp, ringP[warp], ringF[warp], lane, acc, n, cost);
+        if (G == 1) {
+            // one warp: finish both tiles directly
+            float l0, h0, l1, h1;
+            f2_unpack(acc[0], l0, h0);
+            f2_unpack(acc[1], l1, h1);
+            float l2, mx;
+            uint32_t cnt, pr;
+            const float e0 = point_out(a, it.i0, it.v0, l0 + h0, n[0], l2, mx, cnt, pr);
+            finish_tile(a, it.t0, l2, mx, cnt, pr, lane);
+            float e1 = 0.f;
+            if (it.two) {
+                e1 = point_out(a, it.i1, it.v1, l1 + h1, n[1], l2, mx, cnt, pr);
+                finish_tile(a, it.t0 + 1, l2, mx, cnt, pr, lane);
+            }
+            if (ADJ) {
+                float4 lo0, hi0, lo1, hi1;
+                const int nc0 = nz_tile(nzl, e0 != 0.f, a.x[it.v0 ? it.i0 : 0], a.y[it.v0 ? it.i0 : 0],
+                                        a.z[it.v0 ? it.i0 : 0], e0, lane, lo0, hi0);
+                const int nc1 = nz_tile(nzl + kTile, e1 != 0.f, a.x[it.v1 ? it.i1 : 0], a.y[it.v1 ? it.i1 : 0],
+                                        a.z[it.v1 ? it.i1 : 0], e1, lane, lo1, hi1);
+                __syncwarp();
+                if (nc0 + nc1 > 0)
+                    adjoint_share<1>(a, it, 0, nzl, nc0, nc1, box_min(lo0, lo1), box_max(hi0, hi1), adjq[0], lane,
+                                     cost);
+                __syncwarp();
+            }
+            if (lane == 0) a.item_cost[it.item] = cost;
+            k = __shfl_sync(0xffffffffu, knext, 0);
+            continue;
+        }
+        {
+            float l0, h0, l1, h1;
+            f2_unpack(acc[0], l0, h0);
+            f2_unpack(acc[1], l1, h1);
+            red_psi[warp][lane] = make_float2(l0 + h0, l1 + h1);
+            red_n[warp][lane] = make_uint2(n[0], n[1]);
+            if (lane == 0) red_cost[warp] = cost;
+        }
+        __syncthreads();
+        // warp 0 finishes the first tile, warp 1 the second (if any)
+        if (warp < 2 && (warp == 0 || it.two)) {
+            float ps = 0.f;
+            uint32_t np = 0;
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const float2 v = red_psi[q][lane];
+                const uint2 c = red_n[q][lane];
+                ps += warp ? v.y : v.x;
+                np += warp ? c.y : c.x;
+            }
+            float l2, mx;
+            uint32_t cnt, pr;
+            const int64_t i = warp ? it.i1 : it.i0;
+            const bool v = warp ? it.v1 : it.v0;
+            const float e = point_out(a, i, v, ps, np, l2, mx, cnt, pr);
+            finish_tile(a, it.t0 + warp, l2, mx, cnt, pr, lane);
+            if (ADJ) {
+                float4 lo, hi;
+                const int nc = nz_tile(nzl + kTile * warp, e != 0.f, a.x[v ? i : 0], a.y[v ? i : 0], a.z[v ? i : 0],
+                                       e, lane, lo, hi);
+                if (lane == 0) {
+                    s_nc[warp] = nc;
+                    s_box[warp][0] = lo;
+                    s_box[warp][1] = hi;
+                    if (warp == 0 && !it.two) s_nc[1] = 0;
+                }
+            }
+            if (warp == 0 && lane == 0) {
+                if (!ADJ) {
+                    uint32_t c = 0;
+#pragma unroll
+                    for (int q = 0; q < G; ++q) c += red_cost[q];
+                    a.item_cost[it.item] = c;
+                }
+                s_k = knext;
+            }
+        }
+        if (ADJ) {
+            __syncthreads();
+            const int nc0 = s_nc[0], nc1 = s_nc[1];
+            if (nc0 + nc1 > 0) {
+                const float4 lo = nc1 ? (nc0 ? box_min(s_box[0][0], s_box[1][0]) : s_box[1][0]) : s_box[0][0];
+                const float4 hi = nc1 ? (nc0 ? box_max(s_box[0][1], s_box[1][1]) : s_box[1][1]) : s_box[0][1];
+                uint32_t c = 0;
+                adjoint_share<G>(a, it, warp, nzl, nc0, nc1, lo, hi, adjq[warp], lane, c);
+                if (lane == 0) red_cost[warp] += c;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t c = 0;
+#pragma unroll
+                for (int q = 0; q < G; ++q) c += red_cost[q];
+                a.item_cost[it.item] = c;
+            }
+        }
+        __syncthreads();
+        k = s_k;
+    }
+}
+
+template <int G, bool ADJ>
+int launch_forward(const FwdArgs &a, int64_t nitems, int sm_count, cudaStream_t s) {
+    static int per_sm = 0;  // resident blocks per SM (same for every device of one kind)
+    if (per_sm == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forward<G, ADJ>, G * 32, 0) != cudaSuccess ||
+            nb < 1)
+            return SERBF_ECUDA;
+        per_sm = nb;
+    }
+    int64_t blocks = nitems;
+    const int64_t resident = (int64_t)sm_count * per_sm;
+    if (blocks > resident) blocks = resident;
+    // the item counter is reset before every launch (blocks still looking for
+    // work may touch it after the last item is done, so the kernel cannot)
+    cudaMemsetAsync(a.item_next, 0, sizeof(uint32_t), s);
+    k_forward<G, ADJ><<<(unsigned)blocks, G * 32, 0, s>>>(a);
+    SERBF_CHECK_LAUNCH();
+    return SERBF_OK;
+}
+
+template <int G>
+int64_t forward_groups(int sm_count) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forward<G, false>, G * 32, 0) != cudaSuccess ||
+            nb < 1)
+            nb = 1;
+        per_sm = nb;
+    }
+    return (int64_t)sm_count * per_sm;
+}
+
+// Fused adjoint epilogue: one thread per kernel turns its fixed-point moments
+// into the ten App. A gradients and clears the accumulators; the last block
+// publishes the adjoint pair count.
+__global__ void k_adj_epilogue(const float *p, const int32_t *m_dev, int cap, unsigned long long *fix,
+                               unsigned long long *pairs, uint32_t *counter, float *grad, double *stats) {
+    __shared__ bool s_last;
+    const int m = *m_dev;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) {
+        unsigned long long *o = fix + 10 * (size_t)j;
+        float M[10];
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            M[r] = (float)((double)(long long)o[r] * kFixUnit);
+            o[r] = 0ull;
+        }
+        grad_from_moments(p, cap, j, M, grad);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    stats[SERBF_STAT_PAIRS_BWD] = (double)__ldcg(pairs);
+    *pairs = 0ull;
+    *counter = 0u;
+}
+
+int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi, float *err,
+                 uint8_t *mask, float *grad, double *stats, serbf_workspace *ws, void *stream) {
     if (!pts || !prm || !cfg || !ws || ws->magic != kMagic || !ws->binned) return SERBF_EINVAL;
     if (pts->n != ws->npoints || !prm->m || !prm->p) return SERBF_EINVAL;
     if (pts->n > 0 && (!pts->x || !pts->y || !pts->z || !pts->t || !psi || !err || !mask)) return SERBF_EINVAL;
     if (!stats) return SERBF_EINVAL;
+    const bool adj = grad != nullptr;
+    if (adj && (prm->cap < 1 || prm->cap > ws->sz.max_kernels)) return SERBF_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
     FwdArgs a;
     a.x = pts->x;
     a.y = pts->y;
     a.z = pts->z;
     a.t = pts->t;
     a.tile_super = ws->tile_super;
+    a.stile0 = ws->super_tile0;
+    a.order_rec = ws->order_rec;
+    a.item_cost = ws->item_cost;
+    a.nitems = ws->nitems;
     a.tile_start = ws->tile_start;
     a.cell_start = ws->cell_start;
     a.tile_lo = ws->tile_lo;
@@ -272,6 +700,9 @@ extern "C" int serbf_forward(const serbf_points *pts, const serbf_params *prm, c
     a.slist = ws->sup_list;
     a.scnt = ws->sup_cnt;
     a.kfwd = ws->kfwd;
+    a.kbwd = ws->kbwd;
+    a.adj_fix = ws->adj_fix;
+    a.adj_pairs = ws->adj_pairs;
     a.ntiles = ws->ntiles;
     a.scap = ws->sz.super_cap;
     a.cps = ws->sf * ws->sf * ws->sf;
@@ -288,21 +719,44 @@ extern "C" int serbf_forward(const serbf_points *pts, const serbf_params *prm, c
     a.gpart = ws->fwd_gpart;
     a.group_done = ws->fwd_group_done;
     a.counter = ws->counters + 0;
-    a.tile_next = ws->counters + 4;
+    a.item_next = ws->counters + 4;
     a.stats = stats;
+    int rc = SERBF_OK;
     if (ws->ntiles == 0) {
         // nothing to evaluate: the loss terms are zero
-        cudaMemsetAsync(stats + SERBF_STAT_L2, 0, 4 * sizeof(double), (cudaStream_t)stream);
+        cudaMemsetAsync(stats + SERBF_STAT_L2, 0, 4 * sizeof(double), s);
         SERBF_CHECK_LAUNCH();
-        return SERBF_OK;
+    } else {
+        // warps per item: the fewest that still leave about four items per
+        // group of warps for the heavy-first balancing
+        const int64_t ni = ws->nitems;
+        const int G = ni >= 4 * forward_groups<1>(ws->sm_count) ? 1 : (ni >= 4 * forward_groups<2>(ws->sm_count) ? 2 : 4);
+        if (adj)
+            rc = G == 1 ? launch_forward<1, true>(a, ni, ws->sm_count, s)
+                        : (G == 2 ? launch_forward<2, true>(a, ni, ws->sm_count, s)
+                                  : launch_forward<4, true>(a, ni, ws->sm_count, s));
+        else
+            rc = G == 1 ? launch_forward<1, false>(a, ni, ws->sm_count, s)
+                        : (G == 2 ? launch_forward<2, false>(a, ni, ws->sm_count, s)
+                                  : launch_forward<4, false>(a, ni, ws->sm_count, s));
     }
-    int64_t blocks = (ws->ntiles + kFwdWarps - 1) / kFwdWarps;
-    const int64_t resident = (int64_t)ws->sm_count * kFwdBlocksPerSM;
-    if (blocks > resident) blocks = resident;
-    // the tile counter is reset before every launch (warps still looking for
-    // work may touch it after the last tile is done, so the kernel cannot)
-    cudaMemsetAsync(a.tile_next, 0, sizeof(uint32_t), (cudaStream_t)stream);
-    k_forward<<<(unsigned)blocks, kFwdWarps * 32, 0, (cudaStream_t)stream>>>(a);
+    if (rc || !adj) return rc;
+    k_adj_epilogue<<<(prm->cap + 255) / 256, 256, 0, s>>>(prm->p, prm->m, prm->cap, ws->adj_fix, ws->adj_pairs,
+                                                          ws->counters + 5, grad, stats);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;
+}
+
+}  // namespace
+
+extern "C" int serbf_forward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi,
+                             float *err, uint8_t *mask, double *stats, serbf_workspace *ws, void *stream) {
+    return forward_impl(pts, prm, cfg, psi, err, mask, nullptr, stats, ws, stream);
+}
+
+extern "C" int serbf_forward_backward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg,
+                                      float *psi, float *err, uint8_t *mask, float *grad, double *stats,
+                                      serbf_workspace *ws, void *stream) {
+    if (!grad) return SERBF_EINVAL;
+    return forward_impl(pts, prm, cfg, psi, err, mask, grad, stats, ws, stream);
 }

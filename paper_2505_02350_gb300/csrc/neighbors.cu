@@ -53,6 +53,15 @@ __global__ void k_prep(const float *p, int cap, const int32_t *m_dev, float nle,
     }
 }
 
+// The forward's heavy-first item order for its next launch, from the costs
+// the last forward measured.  Runs on the workspace's side stream, next to
+// the (small) neighbour-rebuild kernels.
+__global__ void __launch_bounds__(kOrderWarps * 32) k_order_items(const uint32_t *item_cost, const uint4 *item_rec,
+                                                                  uint4 *order_rec, int64_t nitems) {
+    __shared__ OrderSmem sm;
+    order_items(item_cost, item_rec, order_rec, nitems, sm);
+}
+
 // One block per super cell: every kernel whose support may reach the box.
 __global__ void __launch_bounds__(256) k_super_lists(const float4 *kfwd, const int32_t *m_dev, const float4 *slo,
                                                      const float4 *shi, uint32_t *list, uint32_t *cnt, int cap,
@@ -184,11 +193,22 @@ extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params
     if (kmajor && (!kmajor->rowptr || (kmajor->cap > 0 && !kmajor->col))) return SERBF_EINVAL;
     if (pmajor && (!pmajor->rowptr || (pmajor->cap > 0 && !pmajor->col))) return SERBF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
+    // fork: the item order for the next forward overlaps the rebuild
+    const bool fork = ws->nitems > 0 && ws->aux;
+    if (fork) {
+        if (cudaEventRecord(ws->ev_fork, s) != cudaSuccess) return SERBF_ECUDA;
+        if (cudaStreamWaitEvent(ws->aux, ws->ev_fork, 0) != cudaSuccess) return SERBF_ECUDA;
+        k_order_items<<<1, kOrderWarps * 32, 0, ws->aux>>>(ws->item_cost, ws->item_rec, ws->order_rec, ws->nitems);
+        SERBF_CHECK_LAUNCH();
+        if (cudaEventRecord(ws->ev_join, ws->aux) != cudaSuccess) return SERBF_ECUDA;
+    }
     int rc = launch_prep(prm, cfg, ws, s);
     if (rc) return rc;
     k_super_lists<<<ws->nsuper, 256, 0, s>>>(ws->kfwd, prm->m, ws->sup_lo, ws->sup_hi, ws->sup_list, ws->sup_cnt,
                                               ws->sz.super_cap, ws->status, ws->needed);
     SERBF_CHECK_LAUNCH();
+    // join the side stream
+    if (fork && cudaStreamWaitEvent(s, ws->ev_join, 0) != cudaSuccess) return SERBF_ECUDA;
     if (!kmajor && !pmajor) return SERBF_OK;
 
     // Explicit lists: an overflowing candidate list would make them silently

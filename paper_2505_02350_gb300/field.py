@@ -31,9 +31,10 @@ class Problem:
     """One field: training points, targets, kernels, optimiser state and scratch."""
 
     def __init__(self, x, y, z, S, P, m, spacing, cfg=None, cap=None, max_points=None, t=None,
-                 super_cap=8192, super_factor=4, max_cells=None, device="cuda"):
+                 super_cap=8192, super_factor=4, max_cells=None, device="cuda", fused=True):
         dev = torch.device(device)
         self.dev = dev
+        self.fused = fused  # epochs use the one-pass forward + adjoint
         self.cfg = cfg if cfg is not None else N.config_default()
         if self.cfg.add_radius == 0.0:
             self.cfg.add_radius = 2.0 * spacing
@@ -90,6 +91,19 @@ class Problem:
             self.t_all[:n] = torch.as_tensor(np.asarray(t, np.float32), device=dev)
         self.bin()
 
+    def close(self):
+        """Release the workspace's CUDA objects (the device buffers are torch's)."""
+        if getattr(self, "ws", None) is not None and self.ws_dev is not None:
+            torch.cuda.synchronize(self.dev)
+            N.serbf_workspace_release(self.ws)
+            self.ws_dev = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
     # ------------------------------------------------------------ structure
     def bin(self):
         n = self.n
@@ -132,6 +146,12 @@ class Problem:
         N.serbf_forward(self.pts, self.prm, self.cfg, self.psi[:n], self.err[:n], self.mask[:n], self.stats,
                         self.ws)
 
+    def forward_backward(self):
+        """Forward and the adjoint of its own residual in one pass."""
+        n = self.n
+        N.serbf_forward_backward(self.pts, self.prm, self.cfg, self.psi[:n], self.err[:n], self.mask[:n],
+                                 self.grad, self.stats, self.ws)
+
     def backward(self, err=None):
         n = self.n
         N.serbf_backward(self.pts, self.prm, self.cfg, self.err[:n] if err is None else err, self.grad,
@@ -151,20 +171,26 @@ class Problem:
     def epoch(self):
         """One Algorithm 3 epoch with the full batch: no host synchronisation."""
         self.build_neighbors()
-        self.forward()
-        self.backward()
+        if self.fused:
+            self.forward_backward()
+        else:
+            self.forward()
+            self.backward()
         self.step()
         self.prune()
         self.add()
 
     def capture(self):
-        """Capture one epoch as three CUDA graphs (neighbour rebuild | forward |
-        adjoint, step, deletion, addition) so that a step is three graph
+        """Capture one epoch as three CUDA graphs (neighbour rebuild | forward
+        and adjoint | step, deletion, addition) so that a step is three graph
         launches.  Re-capture after binning changes (refinement)."""
         self.epoch()  # warm up: lazy attribute setup happens outside capture
         torch.cuda.synchronize()
-        parts = [self.build_neighbors, self.forward,
-                 lambda: (self.backward(), self.step(), self.prune(), self.add())]
+        if self.fused:
+            parts = [self.build_neighbors, self.forward_backward, lambda: (self.step(), self.prune(), self.add())]
+        else:
+            parts = [self.build_neighbors, self.forward,
+                     lambda: (self.backward(), self.step(), self.prune(), self.add())]
         self.graphs = []
         for fn in parts:
             g = torch.cuda.CUDAGraph()

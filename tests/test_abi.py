@@ -82,6 +82,8 @@ def test_entry_points_reject_null_arguments_before_any_launch(native):
     assert L.serbf_bin_points(None, None, None, 1, C.byref(g), None, None, None, None, None, None) == E
     ws = native.workspace_struct()
     assert L.serbf_status(C.addressof(ws), None, None, 0, None) == E  # uninitialised workspace
+    assert L.serbf_workspace_release(None) == E
+    assert L.serbf_workspace_release(C.addressof(ws)) == E
 
 
 def test_uninitialised_workspace_is_rejected(native):

@@ -214,6 +214,46 @@ def test_backward_arbitrary_upstream_weights(torch, orc, c1):
     assert rel_l2(c1.grad[:, :m].cpu().numpy(), g_o) <= GRAD_TOL
 
 
+def _fused_check(torch, orc, pb):
+    """serbf_forward_backward: the forward outputs bit-equal to serbf_forward,
+    the same adjoint pairs, gradients within the bar of the oracle and close
+    to serbf_backward's (fixed-point vs float accumulation)."""
+    pb.build_neighbors()
+    pb.forward()
+    pb.backward()
+    torch.cuda.synchronize()
+    psi, err, mask = pb.psi[:pb.n].clone(), pb.err[:pb.n].clone(), pb.mask[:pb.n].clone()
+    g_sep, st_sep = pb.grad.clone(), pb.stats.clone()
+    pb.grad.zero_()
+    pb.forward_backward()
+    torch.cuda.synchronize()
+    assert torch.equal(psi, pb.psi[:pb.n]) and torch.equal(err, pb.err[:pb.n]) and torch.equal(mask, pb.mask[:pb.n])
+    assert torch.equal(st_sep[:6], pb.stats[:6])  # loss terms and both pair counts
+    h, P = _oracle_inputs(pb)
+    m = pb.m()
+    g_o, np_o = orc.backward(h["x"], h["y"], h["z"], err.cpu().numpy().astype(np.float64), P, m)
+    assert pb.stats[5].item() == np_o
+    g = pb.grad[:, :m].cpu().numpy()
+    floor = 1e-7 * np.linalg.norm(g_o)
+    for sl in (slice(0, 3), slice(3, 6), slice(6, 9), slice(9, 10)):
+        e = np.linalg.norm(g[sl] - g_o[sl]) / max(np.linalg.norm(g_o[sl]), floor, 1e-300)
+        assert e <= GRAD_TOL, (sl, e)
+    assert rel_l2(g, g_sep[:, :m].cpu().numpy()) <= 1e-5
+    # a second call gives the same bits (integer accumulation, cleared by the epilogue)
+    g1 = pb.grad.clone()
+    pb.forward_backward()
+    torch.cuda.synchronize()
+    assert torch.equal(g1, pb.grad)
+
+
+def test_fused_forward_backward_c1(torch, orc, c1):
+    _fused_check(torch, orc, c1)
+
+
+def test_fused_forward_backward_c2(torch, orc, c2):
+    _fused_check(torch, orc, c2)
+
+
 # ------------------------------------------------------------------ a6
 def _set_state(pb, **fields):
     from paper_2505_02350_gb300 import _native as N
