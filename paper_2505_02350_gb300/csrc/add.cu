@@ -27,6 +27,8 @@ __global__ void __launch_bounds__(kAddThreads) k_add_select(const float *E, cons
                                                            const double *stats, const serbf_state *st,
                                                            double thresh, double frac, int force,
                                                            unsigned long long *sel, int32_t *info) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ unsigned long long sk[];
     __shared__ uint32_t hist[256];
     __shared__ uint32_t tmp[33];
@@ -126,6 +128,8 @@ __global__ void k_add_localmax(const float *x, const float *y, const float *z, c
                                const uint8_t *mask, const uint32_t *cell_start, serbf_grid g, int sf, int nsx,
                                int nsy, float r2, int reach, const unsigned long long *sel, const int32_t *info,
                                uint32_t *keep) {
+    pdl_wait();
+    pdl_trigger();
     if (!info[0]) return;
     const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (s >= info[1]) return;
@@ -161,6 +165,8 @@ __global__ void __launch_bounds__(kAddThreads) k_add_append(const float *x, cons
                                                            const uint32_t *keep, int32_t *info, float *p,
                                                            float *am, float *av, int32_t *m_dev, int cap,
                                                            serbf_state *st, int32_t *status, long long *needed) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t tmp[33];
     if (!info[0]) return;
     const int ns = info[1];
@@ -233,16 +239,16 @@ extern "C" int serbf_add_kernels(const serbf_points *pts, const float *S_raw, co
             return SERBF_ECUDA;
         attr = true;
     }
-    k_add_select<<<1, kAddThreads, smem, s>>>(err, mask, pts->n, stats, st_dev, cfg->tau_m * 0.5, cfg->topk_frac,
+    launch_pdl(k_add_select, dim3(1), dim3(kAddThreads), smem, s, err, mask, pts->n, stats, st_dev, cfg->tau_m * 0.5, cfg->topk_frac,
                                                force, ws->sel_key, ws->add_info);
     const float r2 = (float)(cfg->add_radius * cfg->add_radius);
     int reach = (int)ceil(cfg->add_radius / ws->grid.h) + 1;
     if (reach > 1 << 20) reach = 1 << 20;
     unsigned lm_blocks = (unsigned)((kSelMax * 32 + 255) / 256);
-    k_add_localmax<<<lm_blocks, 256, 0, s>>>(pts->x, pts->y, pts->z, err, mask, ws->cell_start, ws->grid, ws->sf,
+    launch_pdl(k_add_localmax, dim3(lm_blocks), dim3(256), 0, s, pts->x, pts->y, pts->z, err, mask, ws->cell_start, ws->grid, ws->sf,
                                             ws->ns[0], ws->ns[1], r2, reach, ws->sel_key, ws->add_info,
                                             ws->sel_keep);
-    k_add_append<<<1, kAddThreads, 0, s>>>(pts->x, pts->y, pts->z, err, S_raw, cfg->dbar_min, cfg->eps, ws->sel_key,
+    launch_pdl(k_add_append, dim3(1), dim3(kAddThreads), 0, s, pts->x, pts->y, pts->z, err, S_raw, cfg->dbar_min, cfg->eps, ws->sel_key,
                                            ws->sel_keep, ws->add_info, prm->p, adam_m, adam_v, prm->m, prm->cap,
                                            st_dev, ws->status, ws->needed);
     SERBF_CHECK_LAUNCH();

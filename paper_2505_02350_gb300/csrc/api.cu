@@ -57,10 +57,14 @@ void carve(Carver &c, serbf_workspace *w, const serbf_ws_sizes *s) {
     w->tile_super = c.take<uint32_t>(T);
     w->tile_start = c.take<uint32_t>(T);
     const int64_t I = T / 2 + S + 2;
+    w->max_items = I;
     w->super_item0 = c.take<uint32_t>(S + 1);
     w->item_rec = c.take<uint4>(I);
-    w->item_cost = c.take<uint32_t>(I);
+    w->item_class = c.take<uint8_t>(I);
+    w->class_hist = c.take<uint32_t>((I + kOrderChunk - 1) / kOrderChunk * kCostClasses);
     w->order_rec = c.take<uint4>(I);
+    w->sched = c.take<uint32_t>(4);
+    w->sched_total = c.take<unsigned long long>(2);
     w->tile_lo = c.take<float4>(T);
     w->tile_hi = c.take<float4>(T);
     w->sup_lo = c.take<float4>(S);

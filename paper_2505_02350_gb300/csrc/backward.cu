@@ -35,6 +35,8 @@ __global__ void __launch_bounds__(1024) k_nz_compact(const float *x, const float
                                                      const uint32_t *stile0, const uint32_t *tile_start,
                                                      const uint32_t *cell_start, int cps, const float4 *tlo,
                                                      const float4 *thi, float4 *nz, float4 *rec, uint32_t *ccnt) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t cnt[32];
     const int s = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t t0 = stile0[s], t1 = stile0[s + 1];
@@ -85,6 +87,8 @@ struct BwdArgs {
 
 template <bool KAHAN>
 __global__ void __launch_bounds__(kBwdThreads) k_moments(BwdArgs a) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int NW = kBwdThreads / 32;
     constexpr int RING = 2 * kQueue;  // two points per lane in flight
     __shared__ uint32_t ring[NW][RING];
@@ -200,6 +204,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_moments(BwdArgs a) {
 // gradients; the pair count total is a fixed-order sum by the last block.
 __global__ void k_grad_epilogue(const float *p, const int32_t *m_dev, int cap, const float *mom, int nparts,
                                 float *grad, unsigned long long *pairs, uint32_t *counter, double *stats) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ bool s_last;
     __shared__ unsigned long long red[32];
     const int m = *m_dev;
@@ -252,7 +258,7 @@ extern "C" int serbf_backward(const serbf_points *pts, const serbf_params *prm, 
     const int64_t nt = ws->ntiles;
     const int cps = ws->sf * ws->sf * ws->sf;
     if (nt > 0)
-        k_nz_compact<<<dim3((unsigned)ws->max_chunks, (unsigned)ws->nsuper), 1024, 0, s>>>(
+        launch_pdl(k_nz_compact, dim3((unsigned)ws->max_chunks, (unsigned)ws->nsuper), dim3(1024), 0, s,
             pts->x, pts->y, pts->z, err, ws->super_tile0, ws->tile_start, ws->cell_start, cps, ws->tile_lo,
             ws->tile_hi, ws->nz, ws->nzrec, ws->nzc_cnt);
     BwdArgs a;
@@ -279,10 +285,10 @@ extern "C" int serbf_backward(const serbf_points *pts, const serbf_params *prm, 
     splits = splits < 1 ? 1 : (splits > kBwdSplit ? kBwdSplit : splits);
     const dim3 grid((unsigned)prm->cap, (unsigned)splits);
     if (cfg->kahan)
-        k_moments<true><<<grid, kBwdThreads, 0, s>>>(a);
+        launch_pdl(k_moments<true>, dim3(grid), dim3(kBwdThreads), 0, s, a);
     else
-        k_moments<false><<<grid, kBwdThreads, 0, s>>>(a);
-    k_grad_epilogue<<<(prm->cap + 7) / 8, 256, 0, s>>>(prm->p, prm->m, prm->cap, ws->moments,
+        launch_pdl(k_moments<false>, dim3(grid), dim3(kBwdThreads), 0, s, a);
+    launch_pdl(k_grad_epilogue, dim3((prm->cap + 7) / 8), dim3(256), 0, s, prm->p, prm->m, prm->cap, ws->moments,
                                                         splits * (kBwdThreads / 32), grad,
                                                            ws->bwd_pairs, ws->counters + 1, stats);
     SERBF_CHECK_LAUNCH();

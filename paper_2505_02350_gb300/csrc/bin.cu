@@ -117,11 +117,11 @@ __global__ void k_super_tiles(const uint32_t *cell_start, int nsuper, int cps, u
 }
 
 // Tiles of each super cell, and its work items: the tiles at even offsets
-// (with the following tile, if any, as the item's second tile).  Items start
-// in natural order with zero cost.
+// (with the following tile, if any, as the item's second tile).  The first
+// forward takes them in this order.
 __global__ void k_fill_tiles(const uint32_t *cell_start, const uint32_t *stile0, const uint32_t *sitem0, int nsuper,
                              int cps, uint32_t *tile_super, uint32_t *tile_start, uint4 *item_rec,
-                             uint32_t *item_cost, uint4 *order_rec) {
+                             uint4 *order_rec, uint8_t *item_class) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsuper; s += gridDim.x * blockDim.x) {
         const uint32_t t0 = stile0[s], t1 = stile0[s + 1], i0 = sitem0[s];
         const uint32_t p0 = cell_start[(int64_t)s * cps], pe = cell_start[(int64_t)(s + 1) * cps];
@@ -134,8 +134,8 @@ __global__ void k_fill_tiles(const uint32_t *cell_start, const uint32_t *stile0,
                 const uint32_t np = min(pe - ps, 2u * kTile);
                 const uint4 r = make_uint4(t, (uint32_t)s, ps, np | (it << 7));
                 item_rec[it] = r;
-                item_cost[it] = 0u;
                 order_rec[it] = r;
+                item_class[it] = 3;  // one class for all until a forward has measured them
             }
         }
     }
@@ -276,8 +276,8 @@ extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, 
     rc = launch_exscan_u32(ws->super_item0, nsuper, s);
     if (rc) return rc;
     k_fill_tiles<<<gsz(nsuper, 256), 256, 0, s>>>(ws->cell_start, ws->super_tile0, ws->super_item0, (int)nsuper, cps,
-                                                  ws->tile_super, ws->tile_start, ws->item_rec, ws->item_cost,
-                                                  ws->order_rec);
+                                                  ws->tile_super, ws->tile_start, ws->item_rec, ws->order_rec,
+                                                  ws->item_class);
     SERBF_CHECK_LAUNCH();
     uint32_t nt = 0, mt = 0, ni = 0;
     if (cudaMemcpyAsync(&nt, ws->super_tile0 + nsuper, sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -288,6 +288,11 @@ extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, 
     if (cudaStreamSynchronize(s) != cudaSuccess) return SERBF_ECUDA;
     if ((int64_t)nt > ws->max_tiles || ni >= (1u << 25)) return SERBF_ECAPACITY;  // item ids have 25 bits
     ws->nitems = ni;
+    // scheduling state: no mean cost yet (the first forward files every item
+    // in the same class), no counts
+    if (cudaMemsetAsync(ws->sched, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return SERBF_ECUDA;
+    if (cudaMemsetAsync(ws->sched_total, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) return SERBF_ECUDA;
+
     ws->ntiles = nt;
     ws->max_chunks = (int32_t)((mt + kTile - 1) / kTile);
     if (nt > 0)

@@ -14,9 +14,9 @@ constexpr int kTile = 32;                         // points per forward/backward
 constexpr int kSortTile = 4096;                   // elements per radix-sort block
 constexpr int kQueue = 64;                        // per-warp ring of staged candidates
 constexpr int kFwdGroup = 64;                     // tiles per first-level forward reduction group
-constexpr int kItemBuckets = 129;                 // cost classes of the forward's heavy-first order
-constexpr float kFixScale = 68719476736.f;        // 2^36: fixed-point unit of the fused adjoint's moments
-constexpr double kFixUnit = 1.0 / 68719476736.0;
+constexpr double kFixUnit = 1.0 / 68719476736.0;  // 2^-36: fixed-point unit of the fused adjoint's moments
+constexpr int kCostClasses = 8;                   // cost classes of the forward's heavy-first schedule
+constexpr int kOrderChunk = 1024;                 // items per block of the class sort
 constexpr int kBwdThreads = 64;                   // threads per adjoint block
 constexpr int kBwdSplit = 16;                     // most blocks per kernel in the adjoint
 constexpr int kBwdWarpsPerKernel = kBwdSplit * kBwdThreads / 32;  // == 32, one epilogue lane each
@@ -44,6 +44,7 @@ struct serbf_workspace {
     serbf_ws_sizes sz;
     int64_t max_tiles;
     int64_t max_supers;
+    int64_t max_items;
     int64_t sort_blocks;
     // grid recorded by serbf_bin_points
     serbf_grid grid;
@@ -71,8 +72,15 @@ struct serbf_workspace {
     // Item record: (first tile, super cell, first point, points | item << 7).
     uint32_t *super_item0;  // nsuper + 1: first item of each super cell
     uint4 *item_rec;        // record of each item, in item order
-    uint32_t *item_cost;    // work measured by the last forward (0 after binning)
-    uint4 *order_rec;       // item records by decreasing cost (heavy first)
+    // heavy-first order of the forward: each launch files every item into a
+    // cost class (item_class); a stable sort by class, descending (class
+    // counts per chunk of kOrderChunk items in class_hist), gives the next
+    // launch's order (order_rec).
+    uint8_t *item_class;    // max_items
+    uint32_t *class_hist;   // chunks x kCostClasses
+    uint4 *order_rec;       // max_items
+    uint32_t *sched;        // [0] mean cost of the last launch
+    unsigned long long *sched_total;  // cost sum of the running launch
     float4 *sup_lo, *sup_hi;
     // per-kernel records
     float4 *kfwd;  // 3 per kernel
@@ -111,6 +119,33 @@ struct serbf_workspace {
     } while (0)
 
 namespace serbf {
+
+// ---------------------------------------------------------------- dependent launches
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while its predecessor on the stream is still running (inside a
+// CUDA graph as well); it calls pdl_wait() before it touches anything, which
+// returns once the predecessor has finished and its writes are visible, and
+// pdl_trigger() to let its own successor be scheduled.  This hides the launch
+// gap between the short kernels of one epoch.  In a kernel launched without
+// the attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... Params, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Params>(args)...);
+}
 
 // ---------------------------------------------------------------- device helpers
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -235,94 +270,6 @@ __device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t *tmp, uint
     if (total) *total = tmp[32];
     __syncthreads();
     return r;
-}
-
-// Cost class of a forward work item: 4 classes per octave of the measured cost.
-__device__ __forceinline__ int cost_bucket(uint32_t c) {
-    if (!c) return 0;
-    const int e = 31 - __clz(c);
-    const uint32_t f = e >= 2 ? (c >> (e - 2)) & 3u : (c << (2 - e)) & 3u;
-    return 1 + 4 * e + (int)f;  // 1 .. 128
-}
-
-// Heavy-first order of the forward's work items from the costs the last
-// forward measured: a counting sort by cost class, descending, run by one
-// block of blockDim.x = 32 * kOrderWarps threads.  Any order is correct --
-// each item is evaluated by one group of warps and the loss partials are
-// reduced by tile index -- the order only balances the persistent forward.
-// Each warp counts its share of the items in a private histogram, so the
-// shared-memory atomics only collide within a warp; each warp loads 8 x 32
-// costs and records at a time.
-constexpr int kOrderWarps = 32;
-struct OrderSmem {
-    uint32_t wh[kItemBuckets][kOrderWarps];  // per class, per warp: counts, then cursors
-    uint32_t tot[kItemBuckets];              // per class: count, then first position
-};
-
-__device__ __forceinline__ void order_items(const uint32_t *cost, const uint4 *rec, uint4 *order, int64_t nitems,
-                                            OrderSmem &sm) {
-    constexpr int U = 8;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = threadIdx.x; q < kItemBuckets * kOrderWarps; q += blockDim.x) (&sm.wh[0][0])[q] = 0u;
-    __syncthreads();
-    const int64_t per_round = (int64_t)kOrderWarps * 32 * U;
-    for (int64_t base = (int64_t)warp * 32 * U; base < nitems; base += per_round) {
-        int bk[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t i = base + 32 * u + lane;
-            bk[u] = i < nitems ? cost_bucket(__ldcg(cost + i)) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (bk[u] >= 0) atomicAdd(&sm.wh[bk[u]][warp], 1u);
-    }
-    __syncthreads();
-    // class totals (warp w handles classes w, w + 32, ...; lanes are warps)
-    for (int b = warp; b < kItemBuckets; b += kOrderWarps) {
-        const uint32_t v = sm.wh[b][lane];
-        const uint32_t inc = warp_iscan(v);
-        sm.wh[b][lane] = inc - v;  // exclusive prefix over warps
-        if (lane == 31) sm.tot[b] = inc;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        // first position of each class: classes in descending order; lane l
-        // owns classes kItemBuckets-1-5l ... kItemBuckets-5-5l
-        uint32_t v[5], sum = 0;
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const int b = kItemBuckets - 1 - (5 * lane + q);
-            v[q] = b >= 0 ? sm.tot[b] : 0u;
-            sum += v[q];
-        }
-        uint32_t run = warp_iscan(sum) - sum;
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const int b = kItemBuckets - 1 - (5 * lane + q);
-            if (b >= 0) sm.tot[b] = run;
-            run += v[q];
-        }
-    }
-    __syncthreads();
-    for (int b = warp; b < kItemBuckets; b += kOrderWarps) sm.wh[b][lane] += sm.tot[b];
-    __syncthreads();
-    for (int64_t base = (int64_t)warp * 32 * U; base < nitems; base += per_round) {
-        int bk[U];
-        uint4 r[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t i = base + 32 * u + lane;
-            bk[u] = -1;
-            if (i < nitems) {
-                bk[u] = cost_bucket(__ldcg(cost + i));
-                r[u] = rec[i];
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (bk[u] >= 0) order[atomicAdd(&sm.wh[bk[u]][warp], 1u)] = r[u];
-    }
 }
 
 // ---------------------------------------------------------------- adjoint helpers

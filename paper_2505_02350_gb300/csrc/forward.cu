@@ -31,10 +31,14 @@ struct FwdArgs {
     const uint32_t *slist, *scnt;
     const float4 *kfwd;
     const float4 *kbwd;      // adjoint records (c, r2), rows of R with log2(e) d_k^2
-    const uint4 *order_rec;  // item records, heaviest first
+    const uint4 *item_rec;   // item records
+    const uint4 *order_rec;  // item records, heaviest class first (stable)
+    uint8_t *item_class;     // cost class of each item, for the next order
+    uint32_t *sched;         // mean cost of the last launch
+    unsigned long long *sched_total;
+    int64_t max_items;
     unsigned long long *adj_fix;    // fixed-point moments (fused adjoint)
     unsigned long long *adj_pairs;  // adjoint pair count (fused adjoint)
-    uint32_t *item_cost;
     int64_t ntiles, nitems;
     int scap, cps;
     float tau1, tau2;  // tau1 rounded down, tau2 rounded up to float: exact double decisions
@@ -44,9 +48,13 @@ struct FwdArgs {
     FwdPart *gpart;       // one partial per group of kFwdGroup tiles
     uint32_t *group_done; // tiles finished per group
     uint32_t *counter;    // groups finished
-    uint32_t *item_next;  // next work item to take (zeroed before each launch)
+    uint32_t *item_next;  // next work item to take (zero between launches)
+    uint32_t *exit_count; // blocks that have exited (zero between launches)
     double *stats;
 };
+
+constexpr int kTouch = 128;  // kernels remembered per warp and item for the adjoint (more: re-scan the list)
+constexpr int kNz = 2 * kTile;
 
 // Two float32 lanes in one 64-bit register: the packed f32x2 arithmetic of
 // sm_100+ does two IEEE round-to-nearest operations per instruction, each
@@ -274,9 +282,10 @@ __device__ __forceinline__ ItemInfo item_info(uint4 r, int lane) {
 // box, staged in pairs and evaluated against the lane's two points.
 // Returns the lane's partial sums and pair counts; *cost gets the warp's
 // measured work.
-template <int G>
+template <int G, bool ADJ>
 __device__ __forceinline__ void forward_share(const FwdArgs &a, const ItemInfo &it, int w, float *ringP, float *ringF,
-                                              int lane, f2 (&acc)[2], uint32_t (&n)[2], uint32_t &cost) {
+                                              int lane, f2 (&acc)[2], uint32_t (&n)[2], uint32_t &cost,
+                                              uint32_t *touch, int &ntouch) {
     const unsigned lt = (1u << lane) - 1u;
     // invalid lanes carry NaN so the support test fails for them
     const float qnan = __int_as_float(0x7fc00000);
@@ -319,14 +328,17 @@ __device__ __forceinline__ void forward_share(const FwdArgs &a, const ItemInfo &
     }
     uint32_t jn = b0 + kStride + lane < L ? lst[b0 + kStride + lane] : 0u;
     int nchunks = 0;
+    ntouch = 0;
     for (int b = b0; b < L; b += kStride) {
         const float4 k0 = c0, k1 = c1, k2 = c2;
+        const uint32_t j = jc;
         const bool live = b + lane < L;
         if (b + kStride + lane < L) {
             c0 = a.kfwd[3 * jn];
             c1 = a.kfwd[3 * jn + 1];
             c2 = a.kfwd[3 * jn + 2];
         }
+        jc = jn;
         if (b + 2 * kStride + lane < L) jn = lst[b + 2 * kStride + lane];
         ++nchunks;
         bool part = false, full = false;
@@ -337,6 +349,13 @@ __device__ __forceinline__ void forward_share(const FwdArgs &a, const ItemInfo &
         const unsigned bp = __ballot_sync(0xffffffffu, part), bf = __ballot_sync(0xffffffffu, full);
         if (part) stage(ringP, (hp + qp + __popc(bp & lt)) & (kQueue - 1), k0, k1, k2);
         if (full) stage(ringF, (hf + qf + __popc(bf & lt)) & (kQueue - 1), k0, k1, k2);
+        if (ADJ) {
+            // the kernels that reach the item box, for the adjoint pass
+            const unsigned ba = bp | bf;
+            const int pos = ntouch + __popc(ba & lt);
+            if ((part || full) && pos < kTouch) touch[pos] = j;
+            ntouch += __popc(ba);
+        }
         qp += __popc(bp);
         qf += __popc(bf);
         npart += __popc(bp);
@@ -376,50 +395,123 @@ __device__ __forceinline__ void forward_share(const FwdArgs &a, const ItemInfo &
 
 // ---------------------------------------------------------------- fused adjoint
 // After an item's residuals are known, its points with E != 0 (at most 64,
-// in shared memory as (x, y, z, E)) are taken against the kernels of the
-// same candidate chunks whose support reaches their box: lanes are kernels,
-// each lane loops over the points and accumulates the ten App. A moments of
-// its kernel (the pair arithmetic of the kernel-major adjoint).  The item's
-// float partial moments go to per-kernel 64-bit fixed-point accumulators
-// (unit 2^-36) by integer atomics: integer addition is associative, so the
-// totals do not depend on the order in which items finish.
+// in shared memory as x, y, z, E arrays: tile 0 from 0, tile 1 from 32, each
+// padded to an even count) are taken against the kernels that reached the
+// item box in the forward filter, kept if their support reaches the box of
+// those points: lanes are kernels, each lane loops over the points two at a
+// time (packed f32x2) and accumulates the ten App. A moments of its kernel.
+// The item's float partial moments go to per-kernel 64-bit fixed-point
+// accumulators (unit 2^-36) by integer atomics: integer addition is
+// associative, so the totals do not depend on the order in which items
+// finish.
+
+struct NzPoints {
+    float x[kNz], y[kNz], z[kNz], e[kNz];
+};
+
+__device__ __forceinline__ f2 f2_dup(float v) { return f2_pack(v, v); }
+
+// v * 2^36 rounded to the nearest integer (halves away from zero), with
+// integer operations only (a float to 64-bit integer conversion would use
+// the slow double-precision unit).  |v| >= 2^26 saturates at 2^62.
+__device__ __forceinline__ long long to_fix36(float v) {
+    const uint32_t b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xffu);  // biased exponent; 0: zero or below 2^-126
+    if (e == 0) return 0;
+    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);  // v = m 2^(e - 150)
+    const int sh = e - 150 + 36;
+    long long r;
+    if (sh >= 0)
+        r = sh >= 39 ? (1ll << 62) : (m << sh);
+    else if (sh > -25)
+        r = (m + (1ll << (-sh - 1))) >> (-sh);
+    else
+        r = 0;
+    return (b >> 31) ? -r : r;
+}
 
 // Lane = kernel q[(head + lane) % 64] for lane < cnt; all nz points.
 __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *q, int head, int cnt,
-                                              const float4 *nzl, int nc0, int nc1, int lane, uint32_t &pairs) {
+                                              const NzPoints &nz, int nc0, int nc1, int lane, uint32_t &pairs) {
     if (lane >= cnt) return;
     const uint32_t j = q[(head + lane) & (kQueue - 1)];
     const float4 k0 = a.kbwd[4 * j], k1 = a.kbwd[4 * j + 1], k2 = a.kbwd[4 * j + 2], k3 = a.kbwd[4 * j + 3];
-    float acc[10], cmp[10];
+    const f2 cx = f2_dup(k0.x), cy = f2_dup(k0.y), cz = f2_dup(k0.z);
+    const f2 r11 = f2_dup(k1.x), r12 = f2_dup(k1.y), r13 = f2_dup(k1.z), e1 = f2_dup(k1.w);
+    const f2 r21 = f2_dup(k2.x), r22 = f2_dup(k2.y), r23 = f2_dup(k2.z), e2 = f2_dup(k2.w);
+    const f2 r31 = f2_dup(k3.x), r32 = f2_dup(k3.y), r33 = f2_dup(k3.z), e3 = f2_dup(k3.w);
+    f2 acc[10];
 #pragma unroll
-    for (int r = 0; r < 10; ++r) acc[r] = cmp[r] = 0.f;
+    for (int r = 0; r < 10; ++r) acc[r] = 0ull;
     uint32_t np = 0;
-    for (int p = 0; p < nc0; ++p) accumulate<false>(nzl[p], k0, k1, k2, k3, acc, cmp, np);
-    for (int p = 0; p < nc1; ++p) accumulate<false>(nzl[kTile + p], k0, k1, k2, k3, acc, cmp, np);
+#pragma unroll 1
+    for (int seg = 0; seg < 2; ++seg) {
+        const int base = seg ? kTile : 0, cntp = ((seg ? nc1 : nc0) + 1) >> 1;
+#pragma unroll 2
+        for (int pp = 0; pp < cntp; ++pp) {
+            const int i = base + 2 * pp;
+            const f2 px = *reinterpret_cast<const f2 *>(&nz.x[i]), py = *reinterpret_cast<const f2 *>(&nz.y[i]);
+            const f2 pz = *reinterpret_cast<const f2 *>(&nz.z[i]), pe = *reinterpret_cast<const f2 *>(&nz.e[i]);
+            const f2 dx = f2_sub(px, cx), dy = f2_sub(py, cy), dz = f2_sub(pz, cz);
+            // Eq. 3-15-1, same float operations as the scalar test
+            const f2 d2 = f2_add(f2_add(f2_mul(dx, dx), f2_mul(dy, dy)), f2_mul(dz, dz));
+            float d0, d1;
+            f2_unpack(d2, d0, d1);
+            const bool i0 = d0 < k0.w, i1 = d1 < k0.w;
+            const f2 u1 = f2_fma(r13, dz, f2_fma(r12, dy, f2_mul(r11, dx)));
+            const f2 u2 = f2_fma(r23, dz, f2_fma(r22, dy, f2_mul(r21, dx)));
+            const f2 u3 = f2_fma(r33, dz, f2_fma(r32, dy, f2_mul(r31, dx)));
+            const f2 qv = f2_fma(f2_mul(e3, u3), u3, f2_fma(f2_mul(e2, u2), u2, f2_mul(f2_mul(e1, u1), u1)));
+            float q0, q1, pe0, pe1;
+            f2_unpack(qv, q0, q1);
+            f2_unpack(pe, pe0, pe1);
+            const float s0 = i0 ? ex2_approx(-q0) * pe0 : 0.f;
+            const float s1 = i1 ? ex2_approx(-q1) * pe1 : 0.f;
+            np += (uint32_t)(i0 && pe0 != 0.f) + (uint32_t)(i1 && pe1 != 0.f);  // pads have E = 0
+            const f2 sv = f2_pack(s0, s1);
+            const f2 su1 = f2_mul(sv, u1), su2 = f2_mul(sv, u2), su3 = f2_mul(sv, u3);
+            acc[0] = f2_add(acc[0], sv);
+            acc[1] = f2_add(acc[1], su1);
+            acc[2] = f2_add(acc[2], su2);
+            acc[3] = f2_add(acc[3], su3);
+            acc[4] = f2_fma(su1, u1, acc[4]);
+            acc[5] = f2_fma(su1, u2, acc[5]);
+            acc[6] = f2_fma(su1, u3, acc[6]);
+            acc[7] = f2_fma(su2, u2, acc[7]);
+            acc[8] = f2_fma(su2, u3, acc[8]);
+            acc[9] = f2_fma(su3, u3, acc[9]);
+        }
+    }
     if (np) {
         unsigned long long *o = a.adj_fix + 10 * (size_t)j;
 #pragma unroll
-        for (int r = 0; r < 10; ++r)
-            if (acc[r] != 0.f) atomicAdd(o + r, (unsigned long long)__float2ll_rn(acc[r] * kFixScale));
+        for (int r = 0; r < 10; ++r) {
+            float lo, hi;
+            f2_unpack(acc[r], lo, hi);
+            const float v = lo + hi;
+            if (v != 0.f) atomicAdd(o + r, (unsigned long long)to_fix36(v));
+        }
         pairs += np;
     }
 }
 
-// One warp's share of an item's adjoint: candidate chunks w, w + G, ... of
-// the super cell's list, filtered against the box of the nz points.
+// One warp's share of an item's adjoint: the kernels this warp found
+// reaching the item box (or, if it found more than kTouch, its candidate
+// chunks of the super cell's list again), filtered against the nz box.
 template <int G>
-__device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &it, int w, const float4 *nzl, int nc0,
-                                              int nc1, float4 lo, float4 hi, uint32_t *q, int lane,
-                                              uint32_t &cost) {
+__device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &it, int w, const NzPoints &nz,
+                                              int nc0, int nc1, float4 lo, float4 hi, const uint32_t *touch,
+                                              int ntouch, uint32_t *q, int lane, uint32_t &cost) {
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t *lst = a.slist + (size_t)it.sup * a.scap;
-    const int L = min((int)a.scnt[it.sup], a.scap);
-    constexpr int kStride = 32 * G;
+    const bool listed = ntouch <= kTouch;
+    const int L = listed ? ntouch : min((int)a.scnt[it.sup], a.scap);
+    const int b0 = listed ? 0 : 32 * w, stride = listed ? 32 : 32 * G;
     int head = 0, qn = 0, nk = 0;
     uint32_t pairs = 0;
-    for (int b = 32 * w; b < L; b += kStride) {
+    for (int b = b0; b < L; b += stride) {
         const bool live = b + lane < L;
-        const uint32_t j = live ? lst[b + lane] : 0u;
+        const uint32_t j = live ? (listed ? touch[b + lane] : lst[b + lane]) : 0u;
         bool hit = false;
         if (live) {
             const float4 k0 = a.kbwd[4 * j];
@@ -431,25 +523,42 @@ __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &
         nk += __popc(bal);
         __syncwarp();
         if (qn >= 32) {
-            adjoint_batch(a, q, head, 32, nzl, nc0, nc1, lane, pairs);
+            adjoint_batch(a, q, head, 32, nz, nc0, nc1, lane, pairs);
             head = (head + 32) & (kQueue - 1);
             qn -= 32;
             __syncwarp();
         }
     }
-    if (qn > 0) adjoint_batch(a, q, head, qn, nzl, nc0, nc1, lane, pairs);
+    if (qn > 0) adjoint_batch(a, q, head, qn, nz, nc0, nc1, lane, pairs);
     __syncwarp();
     const uint32_t tot = warp_sum(pairs);
     if (lane == 0 && tot) atomicAdd(a.adj_pairs, (unsigned long long)tot);
     cost += (uint32_t)(nk * (nc0 + nc1)) / 4u + 32u;
 }
 
-// The nz points of one 32-point tile (lanes = points): compacted to nzl in
-// lane order; returns their count and box (empty: +inf / -inf).
-__device__ __forceinline__ int nz_tile(float4 *nzl, bool nz, float x, float y, float z, float e, int lane,
+// The nz points of one 32-point tile (lanes = points): compacted in lane
+// order from `base`, padded to an even count with a copy of the last point
+// with E = 0 (it adds zero and is not counted); returns their count and box
+// (empty: +inf / -inf).
+__device__ __forceinline__ int nz_tile(NzPoints &nzp, int base, bool nz, float x, float y, float z, float e, int lane,
                                        float4 &lo, float4 &hi) {
     const unsigned bal = __ballot_sync(0xffffffffu, nz);
-    if (nz) nzl[__popc(bal & ((1u << lane) - 1u))] = make_float4(x, y, z, e);
+    const int cnt = __popc(bal);
+    if (nz) {
+        const int i = base + __popc(bal & ((1u << lane) - 1u));
+        nzp.x[i] = x;
+        nzp.y[i] = y;
+        nzp.z[i] = z;
+        nzp.e[i] = e;
+    }
+    __syncwarp();
+    if ((cnt & 1) && lane == 0) {
+        // pad: a copy of the last point with E = 0 (finite, adds nothing)
+        nzp.x[base + cnt] = nzp.x[base + cnt - 1];
+        nzp.y[base + cnt] = nzp.y[base + cnt - 1];
+        nzp.z[base + cnt] = nzp.z[base + cnt - 1];
+        nzp.e[base + cnt] = 0.f;
+    }
     float mnx = nz ? x : INFINITY, mny = nz ? y : INFINITY, mnz = nz ? z : INFINITY;
     float mxx = nz ? x : -INFINITY, mxy = nz ? y : -INFINITY, mxz = nz ? z : -INFINITY;
     if (bal) {
@@ -465,7 +574,7 @@ __device__ __forceinline__ int nz_tile(float4 *nzl, bool nz, float x, float y, f
     }
     lo = make_float4(mnx, mny, mnz, 0.f);
     hi = make_float4(mxx, mxy, mxz, 0.f);
-    return __popc(bal);
+    return cnt;
 }
 
 __device__ __forceinline__ float4 box_min(float4 a, float4 b) {
@@ -475,13 +584,63 @@ __device__ __forceinline__ float4 box_max(float4 a, float4 b) {
     return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), 0.f);
 }
 
+// ---------------------------------------------------------------- scheduling
+// Heavy-first order: blocks claim positions of order_rec, which lists the
+// items by the cost class the previous launch measured, heaviest first and
+// in natural (spatially coherent) order within a class.  Every launch files
+// each item's class for the next order.  Each item is evaluated exactly once
+// whatever the order, and the loss partials are reduced by tile index, so
+// the order never changes a result.
+__device__ __forceinline__ uint4 resolve(const FwdArgs &a, uint32_t k) {
+    return (int64_t)k < a.nitems ? a.order_rec[k] : make_uint4(0u, 0u, 0u, 0u);  // w = 0: none left
+}
+
+// Class of a measured cost: 0 below mean / 4, then about one class per half
+// octave up to 7 at 4 x mean and above (all in class 3 before a mean exists).
+__device__ __forceinline__ int cost_class(uint32_t c, uint32_t mean) {
+    if (mean == 0) return 3;
+    const uint64_t c4 = 4ull * c;
+    int k = 0;
+    k += c4 >= mean;         // >= mean / 4
+    k += c4 >= 2ull * mean;  // >= mean / 2
+    k += c4 >= 3ull * mean;  // >= 0.75 mean
+    k += c4 >= 4ull * mean;  // >= mean
+    k += c4 >= 6ull * mean;  // >= 1.5 mean
+    k += c4 >= 8ull * mean;  // >= 2 mean
+    k += c4 >= 16ull * mean; // >= 4 mean
+    return k;
+}
+
+// Files an item's class by its measured cost.
+__device__ __forceinline__ void note_cost(const FwdArgs &a, uint32_t mean, uint4 rec, uint32_t c) {
+    const uint32_t item = rec.w >> 7;
+    const int cls = cost_class(c, mean);
+    a.item_class[item] = (uint8_t)cls;
+    atomicAdd(a.sched_total, (unsigned long long)c);
+}
+
+// Last block out: records the mean cost and resets the claim counters.
+__device__ __forceinline__ void sched_finish(const FwdArgs &a) {
+    __threadfence();
+    if (atomicAdd(a.exit_count, 1u) != gridDim.x - 1) return;
+    __threadfence();
+    const unsigned long long tot = __ldcg(a.sched_total);
+    const unsigned long long mean = a.nitems > 0 ? tot / (unsigned long long)a.nitems : 0ull;
+    a.sched[0] = (uint32_t)min(mean, 0xffffffffull);
+    *a.sched_total = 0ull;
+    *a.item_next = 0u;
+    *a.exit_count = 0u;
+}
+
 // Persistent blocks take work items, heaviest first, from a global counter.
 // The G warps of a block share an item (its candidate list split by 32-entry
 // chunks); their partial sums are combined in warp order, so Psi does not
 // depend on timing.  G = 1 when there are enough items to balance the warps,
 // 2 or 4 for small problems.
 template <int G, bool ADJ>
-__global__ void __launch_bounds__(G * 32, 24 / G) k_forward(FwdArgs a) {
+__global__ void __launch_bounds__(G * 32, (ADJ ? 20 : 24) / G) k_forward(FwdArgs a) {
+    pdl_wait();
+    pdl_trigger();
     // two rings per warp (kernels partly / fully covering the item box); a
     // ring holds 64 staged kernels (32 pairs), consumed 32 at a time from
     // slot 0 or 32
@@ -490,25 +649,29 @@ __global__ void __launch_bounds__(G * 32, 24 / G) k_forward(FwdArgs a) {
     __shared__ float2 red_psi[G][32];
     __shared__ uint2 red_n[G][32];
     __shared__ uint32_t red_cost[G];
-    __shared__ uint32_t s_k;
+    __shared__ uint4 s_rec;
     // fused adjoint: the item's nz points (tile 0 at 0, tile 1 at 32), their
     // counts and boxes, and a per-warp queue of kernel indices
-    __shared__ float4 nzl[ADJ ? 2 * kTile : 1];
+    __shared__ __align__(16) NzPoints nzl[1];
     __shared__ int s_nc[2];
     __shared__ float4 s_box[2][2];
     __shared__ uint32_t adjq[ADJ ? G : 1][ADJ ? kQueue : 1];
+    __shared__ uint32_t touch[ADJ ? G : 1][ADJ ? kTouch : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) s_k = atomicAdd(a.item_next, 1u);
+    const uint32_t mean = a.sched[0];
+    if (threadIdx.x == 0) s_rec = resolve(a, atomicAdd(a.item_next, 1u));
     __syncthreads();
-    uint32_t k = s_k;
-    while ((int64_t)k < a.nitems) {
-        const ItemInfo it = item_info(a.order_rec[k], lane);
-        // the next item is claimed now; its index is only needed at the end
+    uint4 rec = s_rec;  // the item's record; no points (w = 0) when done
+    while (rec.w != 0u) {
+        const ItemInfo it = item_info(rec, lane);
+        // the next claim is made now; it is only resolved at the end
         uint32_t knext = 0;
         if (threadIdx.x == 0) knext = atomicAdd(a.item_next, 1u);
         f2 acc[2];
         uint32_t n[2], cost;
-        forward_share<G>(a, it, warp, ringP[warp], ringF[warp], lane, acc, n, cost);
+        int ntouch = 0;
+        forward_share<G, ADJ>(a, it, warp, ringP[warp], ringF[warp], lane, acc, n, cost, touch[ADJ ? warp : 0],
+                              ntouch);
         if (G == 1) {
             // one warp: finish both tiles directly
             float l0, h0, l1, h1;
@@ -525,18 +688,25 @@ __global__ void __launch_bounds__(G * 32, 24 / G) k_forward(FwdArgs a) {
             }
             if (ADJ) {
                 float4 lo0, hi0, lo1, hi1;
-                const int nc0 = nz_tile(nzl, e0 != 0.f, a.x[it.v0 ? it.i0 : 0], a.y[it.v0 ? it.i0 : 0],
+                const int nc0 = nz_tile(nzl[0], 0, e0 != 0.f, a.x[it.v0 ? it.i0 : 0], a.y[it.v0 ? it.i0 : 0],
                                         a.z[it.v0 ? it.i0 : 0], e0, lane, lo0, hi0);
-                const int nc1 = nz_tile(nzl + kTile, e1 != 0.f, a.x[it.v1 ? it.i1 : 0], a.y[it.v1 ? it.i1 : 0],
+                const int nc1 = nz_tile(nzl[0], kTile, e1 != 0.f, a.x[it.v1 ? it.i1 : 0], a.y[it.v1 ? it.i1 : 0],
                                         a.z[it.v1 ? it.i1 : 0], e1, lane, lo1, hi1);
                 __syncwarp();
                 if (nc0 + nc1 > 0)
-                    adjoint_share<1>(a, it, 0, nzl, nc0, nc1, box_min(lo0, lo1), box_max(hi0, hi1), adjq[0], lane,
-                                     cost);
+                    adjoint_share<1>(a, it, 0, nzl[0], nc0, nc1, box_min(lo0, lo1), box_max(hi0, hi1), touch[0],
+                                     ntouch, adjq[0], lane, cost);
                 __syncwarp();
             }
-            if (lane == 0) a.item_cost[it.item] = cost;
-            k = __shfl_sync(0xffffffffu, knext, 0);
+            uint4 rn = make_uint4(0u, 0u, 0u, 0u);
+            if (lane == 0) {
+                note_cost(a, mean, rec, cost);
+                rn = resolve(a, knext);
+            }
+            rec.x = __shfl_sync(0xffffffffu, rn.x, 0);
+            rec.y = __shfl_sync(0xffffffffu, rn.y, 0);
+            rec.z = __shfl_sync(0xffffffffu, rn.z, 0);
+            rec.w = __shfl_sync(0xffffffffu, rn.w, 0);
             continue;
         }
         {
@@ -567,8 +737,8 @@ __global__ void __launch_bounds__(G * 32, 24 / G) k_forward(FwdArgs a) {
             finish_tile(a, it.t0 + warp, l2, mx, cnt, pr, lane);
             if (ADJ) {
                 float4 lo, hi;
-                const int nc = nz_tile(nzl + kTile * warp, e != 0.f, a.x[v ? i : 0], a.y[v ? i : 0], a.z[v ? i : 0],
-                                       e, lane, lo, hi);
+                const int nc = nz_tile(nzl[0], kTile * warp, e != 0.f, a.x[v ? i : 0], a.y[v ? i : 0],
+                                       a.z[v ? i : 0], e, lane, lo, hi);
                 if (lane == 0) {
                     s_nc[warp] = nc;
                     s_box[warp][0] = lo;
@@ -581,9 +751,9 @@ __global__ void __launch_bounds__(G * 32, 24 / G) k_forward(FwdArgs a) {
                     uint32_t c = 0;
 #pragma unroll
                     for (int q = 0; q < G; ++q) c += red_cost[q];
-                    a.item_cost[it.item] = c;
+                    note_cost(a, mean, rec, c);
                 }
-                s_k = knext;
+                s_rec = resolve(a, knext);
             }
         }
         if (ADJ) {
@@ -593,7 +763,7 @@ __global__ void __launch_bounds__(G * 32, 24 / G) k_forward(FwdArgs a) {
                 const float4 lo = nc1 ? (nc0 ? box_min(s_box[0][0], s_box[1][0]) : s_box[1][0]) : s_box[0][0];
                 const float4 hi = nc1 ? (nc0 ? box_max(s_box[0][1], s_box[1][1]) : s_box[1][1]) : s_box[0][1];
                 uint32_t c = 0;
-                adjoint_share<G>(a, it, warp, nzl, nc0, nc1, lo, hi, adjq[warp], lane, c);
+                adjoint_share<G>(a, it, warp, nzl[0], nc0, nc1, lo, hi, touch[warp], ntouch, adjq[warp], lane, c);
                 if (lane == 0) red_cost[warp] += c;
             }
             __syncthreads();
@@ -601,12 +771,15 @@ __global__ void __launch_bounds__(G * 32, 24 / G) k_forward(FwdArgs a) {
                 uint32_t c = 0;
 #pragma unroll
                 for (int q = 0; q < G; ++q) c += red_cost[q];
-                a.item_cost[it.item] = c;
+                note_cost(a, mean, rec, c);
             }
         }
         __syncthreads();
-        k = s_k;
+        rec = s_rec;
     }
+    // the last block out prepares the next launch: every block has made its
+    // last claim and recorded its costs before it counts itself out
+    if (threadIdx.x == 0) sched_finish(a);
 }
 
 template <int G, bool ADJ>
@@ -622,10 +795,7 @@ int launch_forward(const FwdArgs &a, int64_t nitems, int sm_count, cudaStream_t 
     int64_t blocks = nitems;
     const int64_t resident = (int64_t)sm_count * per_sm;
     if (blocks > resident) blocks = resident;
-    // the item counter is reset before every launch (blocks still looking for
-    // work may touch it after the last item is done, so the kernel cannot)
-    cudaMemsetAsync(a.item_next, 0, sizeof(uint32_t), s);
-    k_forward<G, ADJ><<<(unsigned)blocks, G * 32, 0, s>>>(a);
+    launch_pdl(k_forward<G, ADJ>, dim3((unsigned)blocks), dim3(G * 32), 0, s, a);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;
 }
@@ -648,6 +818,8 @@ int64_t forward_groups(int sm_count) {
 // publishes the adjoint pair count.
 __global__ void k_adj_epilogue(const float *p, const int32_t *m_dev, int cap, unsigned long long *fix,
                                unsigned long long *pairs, uint32_t *counter, float *grad, double *stats) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ bool s_last;
     const int m = *m_dev;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -690,8 +862,12 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
     a.t = pts->t;
     a.tile_super = ws->tile_super;
     a.stile0 = ws->super_tile0;
+    a.item_rec = ws->item_rec;
     a.order_rec = ws->order_rec;
-    a.item_cost = ws->item_cost;
+    a.item_class = ws->item_class;
+    a.sched = ws->sched;
+    a.sched_total = ws->sched_total;
+    a.max_items = ws->max_items;
     a.nitems = ws->nitems;
     a.tile_start = ws->tile_start;
     a.cell_start = ws->cell_start;
@@ -720,6 +896,7 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
     a.group_done = ws->fwd_group_done;
     a.counter = ws->counters + 0;
     a.item_next = ws->counters + 4;
+    a.exit_count = ws->counters + 6;
     a.stats = stats;
     int rc = SERBF_OK;
     if (ws->ntiles == 0) {
@@ -741,7 +918,7 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
                                   : launch_forward<4, false>(a, ni, ws->sm_count, s));
     }
     if (rc || !adj) return rc;
-    k_adj_epilogue<<<(prm->cap + 255) / 256, 256, 0, s>>>(prm->p, prm->m, prm->cap, ws->adj_fix, ws->adj_pairs,
+    launch_pdl(k_adj_epilogue, dim3((prm->cap + 255) / 256), dim3(256), 0, s, prm->p, prm->m, prm->cap, ws->adj_fix, ws->adj_pairs,
                                                           ws->counters + 5, grad, stats);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;

@@ -17,6 +17,8 @@ namespace {
 // kbwd: (c, r2) and the rows of R with e_k = log2(e) d_k^2 in .w.
 // R is the App. A matrix (entries r1..r9).
 __global__ void k_prep(const float *p, int cap, const int32_t *m_dev, float nle, float4 *kfwd, float4 *kbwd) {
+    pdl_wait();
+    pdl_trigger();
     int m = *m_dev;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
         float cx = p[PCX * cap + j], cy = p[PCY * cap + j], cz = p[PCZ * cap + j];
@@ -53,19 +55,88 @@ __global__ void k_prep(const float *p, int cap, const int32_t *m_dev, float nle,
     }
 }
 
-// The forward's heavy-first item order for its next launch, from the costs
-// the last forward measured.  Runs on the workspace's side stream, next to
-// the (small) neighbour-rebuild kernels.
-__global__ void __launch_bounds__(kOrderWarps * 32) k_order_items(const uint32_t *item_cost, const uint4 *item_rec,
-                                                                  uint4 *order_rec, int64_t nitems) {
-    __shared__ OrderSmem sm;
-    order_items(item_cost, item_rec, order_rec, nitems, sm);
+// The forward's heavy-first order for its next launch: a stable sort of the
+// items by the cost class the last forward filed, descending, in two
+// launches on the workspace's side stream (next to the neighbour rebuild).
+// k_class_count: block b counts the classes of items [b kOrderChunk,
+// (b + 1) kOrderChunk).  k_order_items: block b places the same items; a
+// class starts after all heavier classes and after this class in earlier
+// chunks, and the rank inside the chunk comes from ballots in item order.
+__global__ void __launch_bounds__(kOrderChunk) k_class_count(const uint8_t *item_class, int64_t nitems,
+                                                             uint32_t *hist) {
+    constexpr int NW = kOrderChunk / 32;
+    __shared__ uint32_t s_wcnt[NW][kCostClasses];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * kOrderChunk + threadIdx.x;
+    const int cls = i < nitems ? (int)item_class[i] : -1;
+#pragma unroll
+    for (int c = 0; c < kCostClasses; ++c) {
+        const unsigned bal = __ballot_sync(0xffffffffu, cls == c);
+        if (lane == 0) s_wcnt[warp][c] = __popc(bal);
+    }
+    __syncthreads();
+    if (threadIdx.x < kCostClasses) {
+        uint32_t t = 0;
+        for (int w = 0; w < NW; ++w) t += s_wcnt[w][threadIdx.x];
+        hist[(size_t)blockIdx.x * kCostClasses + threadIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kOrderChunk) k_order_items(const uint8_t *item_class, const uint32_t *hist,
+                                                             const uint4 *item_rec, uint4 *order_rec, int64_t nitems) {
+    constexpr int NW = kOrderChunk / 32;
+    __shared__ uint32_t s_base[kCostClasses];      // first position of each class for this chunk
+    __shared__ uint32_t s_tot[kCostClasses];
+    __shared__ uint32_t s_wcnt[NW][kCostClasses];  // per warp: class counts, then offsets
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nchunks = (int)((nitems + kOrderChunk - 1) / kOrderChunk), b = blockIdx.x;
+    // class totals and this class's count in earlier chunks: warp c handles class c
+    if (warp < kCostClasses) {
+        uint32_t tot = 0, before = 0;
+        for (int q = lane; q < nchunks; q += 32) {
+            const uint32_t v = hist[(size_t)q * kCostClasses + warp];
+            tot += v;
+            before += q < b ? v : 0u;
+        }
+        tot = warp_sum(tot);
+        before = warp_sum(before);
+        if (lane == 0) {
+            s_tot[warp] = tot;
+            s_base[warp] = before;
+        }
+    }
+    const int64_t i = (int64_t)b * kOrderChunk + threadIdx.x;
+    const int cls = i < nitems ? (int)item_class[i] : -1;
+    const uint4 r = i < nitems ? item_rec[i] : make_uint4(0u, 0u, 0u, 0u);
+    uint32_t rank = 0;
+#pragma unroll
+    for (int c = 0; c < kCostClasses; ++c) {
+        const unsigned bal = __ballot_sync(0xffffffffu, cls == c);
+        if (cls == c) rank = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) s_wcnt[warp][c] = __popc(bal);
+    }
+    __syncthreads();
+    if (threadIdx.x < kCostClasses) {
+        const int c = threadIdx.x;
+        uint32_t heavier = 0;  // classes are placed in descending order
+        for (int q = c + 1; q < kCostClasses; ++q) heavier += s_tot[q];
+        uint32_t run = heavier + s_base[c];
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t v = s_wcnt[w][c];
+            s_wcnt[w][c] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    if (cls >= 0) order_rec[s_wcnt[warp][cls] + rank] = r;
 }
 
 // One block per super cell: every kernel whose support may reach the box.
 __global__ void __launch_bounds__(256) k_super_lists(const float4 *kfwd, const int32_t *m_dev, const float4 *slo,
                                                      const float4 *shi, uint32_t *list, uint32_t *cnt, int cap,
                                                      int32_t *status, long long *needed) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t tmp[33];
     int s = blockIdx.x;
     float4 lo = slo[s], hi = shi[s];
@@ -177,7 +248,7 @@ namespace serbf {
 int launch_prep(const serbf_params *prm, const serbf_config *cfg, serbf_workspace *ws, cudaStream_t s) {
     float nle = (float)(-log(cfg->eps));
     int blocks = (prm->cap + 127) / 128;
-    k_prep<<<blocks, 128, 0, s>>>(prm->p, prm->cap, prm->m, nle, ws->kfwd, ws->kbwd);
+    launch_pdl(k_prep, dim3(blocks), dim3(128), 0, s, prm->p, prm->cap, prm->m, nle, ws->kfwd, ws->kbwd);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;
 }
@@ -198,13 +269,16 @@ extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params
     if (fork) {
         if (cudaEventRecord(ws->ev_fork, s) != cudaSuccess) return SERBF_ECUDA;
         if (cudaStreamWaitEvent(ws->aux, ws->ev_fork, 0) != cudaSuccess) return SERBF_ECUDA;
-        k_order_items<<<1, kOrderWarps * 32, 0, ws->aux>>>(ws->item_cost, ws->item_rec, ws->order_rec, ws->nitems);
+        const unsigned nchunks = (unsigned)((ws->nitems + kOrderChunk - 1) / kOrderChunk);
+        k_class_count<<<nchunks, kOrderChunk, 0, ws->aux>>>(ws->item_class, ws->nitems, ws->class_hist);
+        k_order_items<<<nchunks, kOrderChunk, 0, ws->aux>>>(ws->item_class, ws->class_hist, ws->item_rec,
+                                                            ws->order_rec, ws->nitems);
         SERBF_CHECK_LAUNCH();
         if (cudaEventRecord(ws->ev_join, ws->aux) != cudaSuccess) return SERBF_ECUDA;
     }
     int rc = launch_prep(prm, cfg, ws, s);
     if (rc) return rc;
-    k_super_lists<<<ws->nsuper, 256, 0, s>>>(ws->kfwd, prm->m, ws->sup_lo, ws->sup_hi, ws->sup_list, ws->sup_cnt,
+    launch_pdl(k_super_lists, dim3(ws->nsuper), dim3(256), 0, s, ws->kfwd, prm->m, ws->sup_lo, ws->sup_hi, ws->sup_list, ws->sup_cnt,
                                               ws->sz.super_cap, ws->status, ws->needed);
     SERBF_CHECK_LAUNCH();
     // join the side stream

@@ -84,6 +84,8 @@ static_assert(sizeof(serbf_state) % 8 == 0, "state is copied as 32-bit words");
 // (Eq. 3-14_2) and the two Eq. 3-21 dot products; the last block turns them
 // into alpha and beta and the Adam bias corrections.
 __global__ void __launch_bounds__(kStepThreads) k_step_alpha(StepArgs a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ ff sh3[33][3];
     __shared__ bool s_last;
     const int m = *a.m, cap = a.cap;
@@ -140,6 +142,8 @@ __global__ void __launch_bounds__(kStepThreads) k_step_alpha(StepArgs a) {
 // Eq. grad (App. A) and the Adam update; then the last block runs the epoch
 // tail of Algorithm 3 on a shared-memory copy of the state.
 __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ ff sh1[33][1];
     __shared__ bool s_last;
     __shared__ __align__(8) uint32_t s_words[kStateWords];
@@ -277,6 +281,8 @@ __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
 // Eq. 3-27: stable compaction of the kernels with |w| >= tau_d.
 __global__ void __launch_bounds__(kStepThreads) k_prune(float *p, float *am, float *av, int32_t *m_dev, int cap,
                                                         serbf_state *st, double tau_d, int force) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ uint32_t tmp[33];
     __shared__ int s_go;
     if (threadIdx.x == 0) s_go = force || st->do_prune;
@@ -336,8 +342,8 @@ extern "C" int serbf_step(serbf_params *prm, const float *grad, float *adam_m, f
                ws->step_part, ws->step_scal, ws->counters + 2};
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned nb = (unsigned)((prm->cap + kStepThreads - 1) / kStepThreads);
-    k_step_alpha<<<nb, kStepThreads, 0, s>>>(a);
-    k_step_adam<<<dim3(nb, SERBF_NPARAM), kStepThreads, 0, s>>>(a);
+    launch_pdl(k_step_alpha, dim3(nb), dim3(kStepThreads), 0, s, a);
+    launch_pdl(k_step_adam, dim3(nb, SERBF_NPARAM), dim3(kStepThreads), 0, s, a);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;
 }
@@ -345,7 +351,7 @@ extern "C" int serbf_step(serbf_params *prm, const float *grad, float *adam_m, f
 extern "C" int serbf_prune(serbf_params *prm, float *adam_m, float *adam_v, serbf_state *st_dev,
                            const serbf_config *cfg, void *stream) {
     if (!prm || !prm->p || !prm->m || prm->cap < 1 || !adam_m || !adam_v || !st_dev || !cfg) return SERBF_EINVAL;
-    k_prune<<<1, kStepThreads, 0, (cudaStream_t)stream>>>(prm->p, adam_m, adam_v, prm->m, prm->cap, st_dev,
+    launch_pdl(k_prune, dim3(1), dim3(kStepThreads), 0, (cudaStream_t)stream, prm->p, adam_m, adam_v, prm->m, prm->cap, st_dev,
                                                            cfg->tau_d, 0);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;
