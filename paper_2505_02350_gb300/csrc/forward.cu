@@ -816,6 +816,8 @@ int64_t forward_groups(int sm_count) {
 // Fused adjoint epilogue: one thread per kernel turns its fixed-point moments
 // into the ten App. A gradients and clears the accumulators; the last block
 // publishes the adjoint pair count.
+constexpr float kFixUnitF = 1.4551915228366852e-11f;  // 2^-36
+
 __global__ void k_adj_epilogue(const float *p, const int32_t *m_dev, int cap, unsigned long long *fix,
                                unsigned long long *pairs, uint32_t *counter, float *grad, double *stats) {
     pdl_wait();
@@ -828,7 +830,11 @@ __global__ void k_adj_epilogue(const float *p, const int32_t *m_dev, int cap, un
         float M[10];
 #pragma unroll
         for (int r = 0; r < 10; ++r) {
-            M[r] = (float)((double)(long long)o[r] * kFixUnit);
+            // int64 -> float through two 32-bit conversions (the 64-bit one runs
+        // on the slow double-precision unit); relative error ~1e-7
+        const long long v = (long long)o[r];
+        const float hi = (float)(int)(v >> 32), lo = (float)(uint32_t)(v & 0xffffffffll);
+        M[r] = fmaf(hi, 4294967296.f, lo) * kFixUnitF;
             o[r] = 0ull;
         }
         grad_from_moments(p, cap, j, M, grad);

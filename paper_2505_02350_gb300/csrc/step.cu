@@ -1,9 +1,9 @@
 // Algorithm 3 update for one full-batch epoch: Eq. 3-21 dynamic weighting,
 // Adam, and the epoch-tail gates (Eq. 3-27 deletion due, Eq. l1_activate,
-// Eq. add_activate, L2-only phase with a cosine learning rate from T^e).  Two
-// grid-wide launches whose last blocks finish the reductions: the state
-// machine lives on the device so that a step needs no host round trip.  Also
-// the Eq. 3-27 compaction.
+// Eq. add_activate, L2-only phase with a cosine learning rate from T^e).  The
+// state machine lives on the device so that a step needs no host round trip.
+// Two grid-wide launches whose last blocks finish the reductions.  Also the
+// Eq. 3-27 compaction.
 #include <math.h>
 
 #include "common.cuh"
@@ -80,27 +80,162 @@ struct StepArgs {
 constexpr int kStateWords = (int)(sizeof(serbf_state) / 4);
 static_assert(sizeof(serbf_state) % 8 == 0, "state is copied as 32-bit words");
 
-// Stage 1 of the update (one thread per kernel, many blocks): L1 = sum |w|
-// (Eq. 3-14_2) and the two Eq. 3-21 dot products; the last block turns them
-// into alpha and beta and the Adam bias corrections.
+// ---------------------------------------------------------------- pieces
+// The three sums of Eq. 3-21 and Eq. 3-14_2 for kernel j: |w|, and with the
+// L1 term on, (g1 - g2) g1 and |g2 - g1|^2 on the weight gradients.
+__device__ __forceinline__ void alpha_terms(const StepArgs &a, int j, bool use_l1, float (&part)[3]) {
+    const float w = a.p[PW * a.cap + j], g2 = a.grad[PW * a.cap + j];
+    part[0] += fabsf(w);
+    if (use_l1) {
+        const float g1 = sgnf(w);
+        part[1] += (g1 - g2) * g1;
+        part[2] += (g2 - g1) * (g2 - g1);
+    }
+}
+
+// alpha (clamped to [0, 1]; 1 when the L1 term is off or the two gradients
+// coincide), beta = 1 - alpha, the Adam bias corrections; writes the stats.
+// sc = {alpha, beta, 1 - beta1^t, 1 - beta2^t}.
+__device__ __forceinline__ void alpha_finish(const StepArgs &a, bool use_l1, const ff (&fin)[3], float (&sc)[4]) {
+    // float arithmetic (FP64 is slow on this part): alpha to ~1e-7
+    const float num = fin[1].hi + fin[1].lo, den = fin[2].hi + fin[2].lo;
+    float al = 1.f;
+    if (use_l1 && den > 0.f) al = fminf(1.f, fmaxf(0.f, num / den));
+    const float t = (float)(a.st->adam_t + 1);
+    sc[0] = al;
+    sc[1] = 1.f - al;
+    sc[2] = 1.f - powf((float)a.c.beta1, t);
+    sc[3] = 1.f - powf((float)a.c.beta2, t);
+    a.stats[SERBF_STAT_L1] = (double)fin[0].hi + (double)fin[0].lo;
+    a.stats[SERBF_STAT_ALPHA] = al;
+    a.stats[SERBF_STAT_BETA] = 1.f - al;
+}
+
+// tau_d rounded up to float: |w| >= taud decides as in double.
+__device__ __forceinline__ float tau_d_float(double tau_d) {
+    float t = (float)tau_d;
+    if ((double)t < tau_d) t = nextafterf(t, INFINITY);
+    return t;
+}
+
+// Combined gradient of Eq. grad (App. A) and the Adam update of parameter
+// (r, j); returns 1 when it is a weight that stays at or above tau_d (b_f).
+__device__ __forceinline__ float adam_param(const StepArgs &a, int r, int j, const float (&sc)[4], float lr,
+                                            float taud) {
+    const float b1 = (float)a.c.beta1, b2 = (float)a.c.beta2, eps = (float)a.c.adam_eps;
+    const int64_t q = (int64_t)r * a.cap + j;
+    const float pv = a.p[q];
+    float g = sc[0] * a.grad[q];
+    if (r == PW) g = fmaf(sc[1], sgnf(pv), g);
+    const float mo = fmaf(b1, a.am[q], (1.f - b1) * g);
+    const float vo = fmaf(b2, a.av[q], (1.f - b2) * g * g);
+    const float pn = pv - lr * (mo / sc[2]) / (sqrtf(vo / sc[3]) + eps);
+    a.am[q] = mo;
+    a.av[q] = vo;
+    a.p[q] = pn;
+    return (r == PW && fabsf(pn) >= taud) ? 1.f : 0.f;
+}
+
+// The epoch tail of Algorithm 3 on a shared-memory copy of the state, run by
+// one warp: histories, deletion due (every k^l2 epochs while l1_optim and
+// e < T^e), Eq. l1_activate (population std of the last k^l2 L2 values <
+// tau^l2), Eq. add_activate (range of the last k^l1 values of b_f < tau^l1),
+// the L2-only phase with a cosine learning rate from T^e.
+__device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float alpha, float beta, int lane) {
+    const double l2 = a.stats[SERBF_STAT_L2];
+    const int e = st.epoch + 1;
+    const int kl2 = a.c.k_l2, kl1 = a.c.k_l1;
+    int l1n = st.l1_optim;
+    const int phase2 = st.phase2;
+    if (lane == 0) {
+        st.l2_hist[(e - 1) % kl2] = l2;
+        st.bf_hist[(e - 1) % kl1] = (int32_t)bf;
+        st.n_l2 = min(st.n_l2 + 1, kl2);
+        st.n_bf = min(st.n_bf + 1, kl1);
+    }
+    __syncwarp();
+    const int n_l2 = st.n_l2, n_bf = st.n_bf;
+    const int do_prune = (e % kl2 == 0) && l1n && (e < a.c.T_e);
+    if (!l1n && !phase2 && e >= kl2 && n_l2 == kl2) {
+        // population std of the last k_l2 values; each double is split into
+        // a float-float pair so the mean and deviations keep ~48 bits
+        ff v{0.f, 0.f};
+        for (int k = lane; k < kl2; k += 32) {
+            const double x = st.l2_hist[k];
+            const float xh = (float)x;
+            v = ff_add(v, ff{xh, (float)(x - (double)xh)});
+        }
+        v = warp_sum_ff(v);
+        const float inv = 1.f / (float)kl2;
+        const ff mean{v.hi * inv, v.lo * inv};
+        float var = 0.f;
+        for (int k = lane; k < kl2; k += 32) {
+            const double x = st.l2_hist[k];
+            const float xh = (float)x;
+            const ff d = ff_add(ff{xh, (float)(x - (double)xh)}, ff{-mean.hi, -mean.lo});
+            const float dd = d.hi + d.lo;
+            var = fmaf(dd, dd, var);
+        }
+        var = warp_sum(var) * inv;
+        if (sqrtf(var) < (float)a.c.tau_l2) l1n = 1;
+    }
+    int do_add = 0;
+    if (l1n && !phase2 && n_bf == kl1) {
+        int lo = 0x7fffffff, hi = -0x7fffffff;
+        for (int k = lane; k < kl1; k += 32) {
+            lo = min(lo, st.bf_hist[k]);
+            hi = max(hi, st.bf_hist[k]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if ((float)(hi - lo) < (float)a.c.tau_l1) {
+            do_add = 1;
+            l1n = 0;
+        }
+    }
+    if (lane == 0) {
+        int ph = phase2;
+        if (e == a.c.T_e) {
+            ph = 1;
+            l1n = 0;
+        }
+        float lr_next = (float)a.c.lr;
+        if (ph) {
+            const float span = (float)(a.c.M_e - a.c.T_e);
+            float pr = span > 0.f ? (float)(e - a.c.T_e) / span : 1.f;
+            if (pr > 1.f) pr = 1.f;
+            lr_next = (float)a.c.lr_min + (float)(a.c.lr_p2 - a.c.lr_min) * 0.5f * (1.f + cospif(pr));
+        }
+        st.alpha = alpha;
+        st.beta = beta;
+        st.adam_t = st.adam_t + 1;
+        st.do_prune = do_prune;
+        st.do_add = do_add;
+        st.l1_optim = l1n;
+        st.phase2 = ph;
+        st.lr = lr_next;
+        st.epoch = e;
+        a.stats[SERBF_STAT_BF] = bf;
+        a.stats[SERBF_STAT_LOSS] = (float)alpha * (float)l2 + (float)beta * (float)a.stats[SERBF_STAT_L1];
+    }
+}
+
+// ---------------------------------------------------------------- grid path
+// Stage 1 (one thread per kernel, many blocks): the sums of alpha_terms; the
+// last block turns them into alpha, beta and the Adam bias corrections.
 __global__ void __launch_bounds__(kStepThreads) k_step_alpha(StepArgs a) {
     pdl_wait();
     pdl_trigger();
     __shared__ ff sh3[33][3];
     __shared__ bool s_last;
-    const int m = *a.m, cap = a.cap;
+    const int m = *a.m;
     const bool use_l1 = a.st->l1_optim && (a.stats[SERBF_STAT_MAXE] < a.c.tau_m);
     float part[3] = {0.f, 0.f, 0.f};
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < m) {
-        const float w = a.p[PW * cap + j], g2 = a.grad[PW * cap + j];
-        part[0] = fabsf(w);
-        if (use_l1) {
-            const float g1 = sgnf(w);
-            part[1] = (g1 - g2) * g1;
-            part[2] = (g2 - g1) * (g2 - g1);
-        }
-    }
+    if (j < m) alpha_terms(a, j, use_l1, part);
     ff tot[3];
     block_sums_ff<3>(part, sh3, tot);
     if (threadIdx.x == 0) {
@@ -122,54 +257,27 @@ __global__ void __launch_bounds__(kStepThreads) k_step_alpha(StepArgs a) {
     ff fin[3];
     block_sums_ff3(acc, sh3, fin);
     if (threadIdx.x == 0) {
-        // float arithmetic from here (FP64 is slow on this part): alpha to ~1e-7
-        const float num = fin[1].hi + fin[1].lo, den = fin[2].hi + fin[2].lo;
-        float al = 1.f;
-        if (use_l1 && den > 0.f) al = fminf(1.f, fmaxf(0.f, num / den));
-        const float t = (float)(a.st->adam_t + 1);
-        a.scal[0] = al;
-        a.scal[1] = 1.f - al;
-        a.scal[2] = 1.f - powf((float)a.c.beta1, t);
-        a.scal[3] = 1.f - powf((float)a.c.beta2, t);
-        a.stats[SERBF_STAT_L1] = (double)fin[0].hi + (double)fin[0].lo;
-        a.stats[SERBF_STAT_ALPHA] = al;
-        a.stats[SERBF_STAT_BETA] = 1.f - al;
+        float sc[4];
+        alpha_finish(a, use_l1, fin, sc);
+        for (int k = 0; k < 4; ++k) a.scal[k] = sc[k];
         *a.counter = 0u;
     }
 }
 
-// Stage 2 (one thread per parameter, many blocks): the combined gradient of
-// Eq. grad (App. A) and the Adam update; then the last block runs the epoch
-// tail of Algorithm 3 on a shared-memory copy of the state.
+// Stage 2 (one thread per parameter, many blocks): adam_param; then the last
+// block runs the epoch tail.
 __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
     pdl_wait();
     pdl_trigger();
     __shared__ ff sh1[33][1];
     __shared__ bool s_last;
     __shared__ __align__(8) uint32_t s_words[kStateWords];
-    const int m = *a.m, cap = a.cap;
+    const int m = *a.m;
     const int r = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
-    const float alpha = (float)a.scal[0], beta = (float)a.scal[1];
-    const float bc1 = (float)a.scal[2], bc2 = (float)a.scal[3];
-    const float lr = (float)a.st->lr;
-    const float b1 = (float)a.c.beta1, b2 = (float)a.c.beta2, eps = (float)a.c.adam_eps;
-    // b_f: |w| >= tau_d decided in float with tau_d rounded up (same decision as in double)
-    float taud = (float)a.c.tau_d;
-    if ((double)taud < a.c.tau_d) taud = nextafterf(taud, INFINITY);
+    const float sc[4] = {(float)a.scal[0], (float)a.scal[1], (float)a.scal[2], (float)a.scal[3]};
+    const float lr = (float)a.st->lr, taud = tau_d_float(a.c.tau_d);
     float bfc[1] = {0.f};
-    if (j < m) {
-        const int64_t q = (int64_t)r * cap + j;
-        const float pv = a.p[q];
-        float g = alpha * a.grad[q];
-        if (r == PW) g = fmaf(beta, sgnf(pv), g);
-        const float mo = fmaf(b1, a.am[q], (1.f - b1) * g);
-        const float vo = fmaf(b2, a.av[q], (1.f - b2) * g * g);
-        const float pn = pv - lr * (mo / bc1) / (sqrtf(vo / bc2) + eps);
-        a.am[q] = mo;
-        a.av[q] = vo;
-        a.p[q] = pn;
-        if (r == PW) bfc[0] = fabsf(pn) >= taud ? 1.f : 0.f;
-    }
+    if (j < m) bfc[0] = adam_param(a, r, j, sc, lr, taud);
     ff tot[1];
     block_sums_ff<1>(bfc, sh1, tot);
     const unsigned nblocks = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
@@ -190,88 +298,9 @@ __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
     block_sums_ff<1>(cc, sh1, tot);
     const double bf = (double)tot[0].hi + tot[0].lo;
     serbf_state &st = *reinterpret_cast<serbf_state *>(s_words);
-    const double l2 = a.stats[SERBF_STAT_L2];
     if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        const int e = st.epoch + 1;
-        const int kl2 = a.c.k_l2, kl1 = a.c.k_l1;
-        int l1n = st.l1_optim;
-        const int phase2 = st.phase2;
-        if (lane == 0) {
-            st.l2_hist[(e - 1) % kl2] = l2;
-            st.bf_hist[(e - 1) % kl1] = (int32_t)bf;
-            st.n_l2 = min(st.n_l2 + 1, kl2);
-            st.n_bf = min(st.n_bf + 1, kl1);
-        }
-        __syncwarp();
-        const int n_l2 = st.n_l2, n_bf = st.n_bf;
-        const int do_prune = (e % kl2 == 0) && l1n && (e < a.c.T_e);
-        if (!l1n && !phase2 && e >= kl2 && n_l2 == kl2) {
-            // population std of the last k_l2 values; each double is split into
-            // a float-float pair so the mean and deviations keep ~48 bits
-            ff v{0.f, 0.f};
-            for (int k = lane; k < kl2; k += 32) {
-                const double x = st.l2_hist[k];
-                const float xh = (float)x;
-                v = ff_add(v, ff{xh, (float)(x - (double)xh)});
-            }
-            v = warp_sum_ff(v);
-            const float inv = 1.f / (float)kl2;
-            const ff mean{v.hi * inv, v.lo * inv};
-            float var = 0.f;
-            for (int k = lane; k < kl2; k += 32) {
-                const double x = st.l2_hist[k];
-                const float xh = (float)x;
-                const ff d = ff_add(ff{xh, (float)(x - (double)xh)}, ff{-mean.hi, -mean.lo});
-                const float dd = d.hi + d.lo;
-                var = fmaf(dd, dd, var);
-            }
-            var = warp_sum(var) * inv;
-            if (sqrtf(var) < (float)a.c.tau_l2) l1n = 1;
-        }
-        int do_add = 0;
-        if (l1n && !phase2 && n_bf == kl1) {
-            int lo = 0x7fffffff, hi = -0x7fffffff;
-            for (int k = lane; k < kl1; k += 32) {
-                lo = min(lo, st.bf_hist[k]);
-                hi = max(hi, st.bf_hist[k]);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-            }
-            if ((float)(hi - lo) < (float)a.c.tau_l1) {
-                do_add = 1;
-                l1n = 0;
-            }
-        }
-        if (lane == 0) {
-            int ph = phase2;
-            if (e == a.c.T_e) {
-                ph = 1;
-                l1n = 0;
-            }
-            float lr_next = (float)a.c.lr;
-            if (ph) {
-                const float span = (float)(a.c.M_e - a.c.T_e);
-                float pr = span > 0.f ? (float)(e - a.c.T_e) / span : 1.f;
-                if (pr > 1.f) pr = 1.f;
-                lr_next = (float)a.c.lr_min + (float)(a.c.lr_p2 - a.c.lr_min) * 0.5f * (1.f + cospif(pr));
-            }
-            st.alpha = alpha;
-            st.beta = beta;
-            st.adam_t = st.adam_t + 1;
-            st.do_prune = do_prune;
-            st.do_add = do_add;
-            st.l1_optim = l1n;
-            st.phase2 = ph;
-            st.lr = lr_next;
-            st.epoch = e;
-            a.stats[SERBF_STAT_BF] = bf;
-            a.stats[SERBF_STAT_LOSS] = (float)alpha * (float)l2 + (float)beta * (float)a.stats[SERBF_STAT_L1];
-            a.counter[1] = 0u;
-        }
+        epoch_tail(a, st, bf, sc[0], sc[1], threadIdx.x);
+        if (threadIdx.x == 0) a.counter[1] = 0u;
     }
     __syncthreads();
     uint32_t *gwo = reinterpret_cast<uint32_t *>(a.st);

@@ -265,9 +265,10 @@ def _set_state(pb, **fields):
     pb.state.copy_(pb.state.new_tensor(raw))
 
 
+@pytest.mark.parametrize("cap", [None, 9000])  # a few blocks, many blocks
 @pytest.mark.parametrize("l1", [False, True])
-def test_step_parity(torch, orc, l1):
-    pb = problem("c1")
+def test_step_parity(torch, orc, l1, cap):
+    pb = problem("c1", cap=cap)
     pb.build_neighbors()
     pb.forward()
     pb.backward()
@@ -300,10 +301,11 @@ def test_step_parity(torch, orc, l1):
     assert pb.stats[8].item() == np.sum(np.abs(P1[9, :m]) >= 0.01)
 
 
-def test_gate_sequence_matches_oracle(torch, orc):
+@pytest.mark.parametrize("cap", [None, 9000])
+def test_gate_sequence_matches_oracle(torch, orc, cap):
     """Run the device state machine for many epochs on fixed gradients and a
     scripted L2 sequence; every flag must follow the oracle's Algorithm 3."""
-    pb = problem("c1")
+    pb = problem("c1", cap=cap)
     m, cap = pb.m(), pb.cap
     pb.cfg.T_e = 70
     pb.cfg.M_e = 90
