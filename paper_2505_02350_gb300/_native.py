@@ -35,7 +35,8 @@ class Config(C.Structure):
                 ("lr_p2", C.c_double), ("lr_min", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double),
                 ("adam_eps", C.c_double), ("topk_frac", C.c_double), ("add_radius", C.c_double),
                 ("dbar_min", C.c_double), ("k_l1", C.c_int32), ("k_l2", C.c_int32), ("T_e", C.c_int32),
-                ("M_e", C.c_int32), ("kahan", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("M_e", C.c_int32), ("kahan", C.c_int32), ("fwd_warps", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class State(C.Structure):

@@ -859,6 +859,7 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
     if (pts->n > 0 && (!pts->x || !pts->y || !pts->z || !pts->t || !psi || !err || !mask)) return SERBF_EINVAL;
     if (!stats) return SERBF_EINVAL;
     const bool adj = grad != nullptr;
+    if (cfg->fwd_warps != 0 && cfg->fwd_warps != 1 && cfg->fwd_warps != 2 && cfg->fwd_warps != 4) return SERBF_EINVAL;
     if (adj && (prm->cap < 1 || prm->cap > ws->sz.max_kernels)) return SERBF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     FwdArgs a;
@@ -913,7 +914,8 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
         // warps per item: the fewest that still leave about four items per
         // group of warps for the heavy-first balancing
         const int64_t ni = ws->nitems;
-        const int G = ni >= 4 * forward_groups<1>(ws->sm_count) ? 1 : (ni >= 4 * forward_groups<2>(ws->sm_count) ? 2 : 4);
+        int G = ni >= 4 * forward_groups<1>(ws->sm_count) ? 1 : (ni >= 4 * forward_groups<2>(ws->sm_count) ? 2 : 4);
+        if (cfg->fwd_warps == 1 || cfg->fwd_warps == 2 || cfg->fwd_warps == 4) G = cfg->fwd_warps;
         if (adj)
             rc = G == 1 ? launch_forward<1, true>(a, ni, ws->sm_count, s)
                         : (G == 2 ? launch_forward<2, true>(a, ni, ws->sm_count, s)

@@ -168,6 +168,28 @@ class Problem:
         N.serbf_add_kernels(self.pts, self.sb[:n], self.err[:n], self.mask[:n], self.prm, self.adam_m,
                             self.adam_v, self.state, self.stats, self.cfg, self.ws, force=force)
 
+    def autotune(self, reps=5):
+        """Times the forward (+ adjoint when fused) with 1, 2 and 4 warps per
+        work item on the current parameters and keeps the fastest in
+        cfg.fwd_warps.  Returns {warps: ms per call}.  Parameters are not
+        changed; the outputs of the last call are left in psi/err/grad."""
+        fn = self.forward_backward if self.fused else self.forward
+        self.build_neighbors()
+        times = {}
+        for g in (1, 2, 4):
+            self.cfg.fwd_warps = g
+            fn()  # files the work costs for this configuration's order
+            torch.cuda.synchronize(self.dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize(self.dev)
+            times[g] = e0.elapsed_time(e1) / reps
+        self.cfg.fwd_warps = min(times, key=times.get)
+        return times
+
     def epoch(self):
         """One Algorithm 3 epoch with the full batch: no host synchronisation."""
         self.build_neighbors()
@@ -180,13 +202,16 @@ class Problem:
         self.prune()
         self.add()
 
-    def capture(self):
-        """Capture one epoch as three CUDA graphs (neighbour rebuild | forward
-        and adjoint | step, deletion, addition) so that a step is three graph
-        launches.  Re-capture after binning changes (refinement)."""
+    def capture(self, split=True):
+        """Capture one epoch as CUDA graphs: three (neighbour rebuild | forward
+        and adjoint | step, deletion, addition) with split=True, else one, so
+        that a step is one to three graph launches.  Re-capture after binning
+        changes (refinement)."""
         self.epoch()  # warm up: lazy attribute setup happens outside capture
         torch.cuda.synchronize()
-        if self.fused:
+        if not split:
+            parts = [self.epoch]
+        elif self.fused:
             parts = [self.build_neighbors, self.forward_backward, lambda: (self.step(), self.prune(), self.add())]
         else:
             parts = [self.build_neighbors, self.forward,
@@ -199,6 +224,21 @@ class Problem:
             self.graphs.append(g)
         torch.cuda.synchronize()
         return self.graphs
+
+    # ------------------------------------------------------------ snapshots
+    def snapshot(self):
+        """Device copies of everything an epoch changes (parameters, Adam
+        moments, optimiser state, kernel count)."""
+        return [t.clone() for t in (self.p, self.adam_m, self.adam_v, self.state, self.m_dev)]
+
+    def restore(self, snap):
+        for dst, src in zip((self.p, self.adam_m, self.adam_v, self.state, self.m_dev), snap):
+            dst.copy_(src)
+
+    def rmse(self):
+        """Root mean square of E over id_all after the last forward."""
+        s = self.stats.cpu().numpy()
+        return float(np.sqrt(s[N.STAT_L2] / max(float(s[N.STAT_COUNT]), 1.0)))
 
     def epoch_graph(self):
         for g in self.graphs:

@@ -159,3 +159,47 @@ def workload(name, cap=None, layers=None):
     P = init_kernels(cfg["seed"], cfg["m"], cap=cap, length=cfg["length"] or 0.15,
                      length_range=cfg["length_range"], rotate=cfg["rotate"])
     return cfg, lay, P
+
+
+def sdf_primitives_torch(prims, x, y, z, device):
+    """sdf_primitives evaluated with torch (float64) on `device`; same formulas."""
+    import torch
+    p = torch.stack([torch.as_tensor(np.asarray(v, np.float64), device=device) for v in (x, y, z)], dim=1)
+    out = torch.full((p.shape[0],), float("inf"), dtype=torch.float64, device=device)
+    for pr in prims:
+        c = torch.as_tensor(pr["c"], device=device)
+        R = torch.as_tensor(pr["R"], device=device)
+        s = torch.as_tensor(pr["s"], device=device)
+        lp = (p - c) @ R
+        if pr["kind"] == "ellipsoid":
+            d = (torch.linalg.norm(lp / s, dim=1) - 1.0) * s.min()
+        elif pr["kind"] == "box":
+            q = lp.abs() - s
+            d = torch.linalg.norm(q.clamp(min=0.0), dim=1) + q.max(dim=1).values.clamp(max=0.0)
+        else:
+            zc = lp[:, 2].clamp(-s[2], s[2])
+            d = torch.sqrt(lp[:, 0] ** 2 + lp[:, 1] ** 2 + (lp[:, 2] - zc) ** 2) - s[0]
+        out = torch.minimum(out, d)
+    return out.to(torch.float32).cpu().numpy()
+
+
+def batch_workload(count=64, seed=500, device=None):
+    """Independent random-primitive shapes with uneven grids and kernel counts:
+    per shape 5..40 primitives, a vertex grid of 32, 48, 64, 96 or 128 points
+    per axis, 64..2048 kernels (log-uniform) with lengths
+    U(0.05, 0.2) (512 / M)^(1/3) and random rotations.  Returns a list of
+    dicts (x, y, z, S, P, m, spacing, n, prims).  With a torch device the
+    distances are evaluated there (same formulas)."""
+    out = []
+    for k in range(count):
+        g = rng(seed + k)
+        nprim = int(g.integers(5, 41))
+        n = int(g.choice([32, 48, 64, 96, 128]))
+        m = int(round(math.exp(g.uniform(math.log(64), math.log(2048)))))
+        x, y, z = grid(n)
+        prims = random_primitives(seed + 1000 + k, nprim)
+        S = sdf_primitives(prims, x, y, z) if device is None else sdf_primitives_torch(prims, x, y, z, device)
+        scale = (512.0 / m) ** (1.0 / 3.0)
+        P = init_kernels(seed + 2000 + k, m, length_range=(0.05 * scale, 0.2 * scale), rotate=True)
+        out.append(dict(x=x, y=y, z=z, S=S, P=P, m=m, spacing=spacing(n), n=n, prims=nprim))
+    return out

@@ -254,6 +254,24 @@ def test_fused_forward_backward_c2(torch, orc, c2):
     _fused_check(torch, orc, c2)
 
 
+@pytest.mark.parametrize("warps", [1, 2, 4])
+def test_forward_backward_every_warp_split(torch, orc, warps):
+    """Each work-item split (1, 2 or 4 warps per item) meets the bars."""
+    pb = problem("c2", layers=[32])
+    pb.cfg.fwd_warps = warps
+    _fused_check(torch, orc, pb)
+    h, P = _oracle_inputs(pb)
+    psi_o = orc.forward(h["x"], h["y"], h["z"], h["t"], P, pb.m())[0]
+    assert np.abs(pb.psi[:pb.n].cpu().numpy() - psi_o).max() <= FWD_TOL * float(np.abs(h["t"]).max())
+
+
+def test_autotune_picks_a_split(torch):
+    pb = problem("c1")
+    times = pb.autotune(reps=2)
+    assert set(times) == {1, 2, 4} and all(t > 0 for t in times.values())
+    assert pb.cfg.fwd_warps == min(times, key=times.get)
+
+
 # ------------------------------------------------------------------ a6
 def _set_state(pb, **fields):
     from paper_2505_02350_gb300 import _native as N
