@@ -90,7 +90,10 @@ typedef struct {
     int32_t kahan;     /* 1: compensated per-kernel sums in the adjoint */
     int32_t fwd_warps; /* warps sharing one forward work item: 1, 2 or 4;
                           0 = chosen from the problem size (default) */
-    int32_t reserved[2];
+    int32_t epoch_steps; /* optimiser steps per epoch: 1 = full batch (default);
+                            n > 1: mini-batches, the epoch tail runs every n-th step
+                            on the sum of the n batch L2 values */
+    int32_t reserved[1];
 } serbf_config;
 
 /* Optimiser state of Algorithm 3; lives in DEVICE memory (sizeof bytes). */
@@ -103,9 +106,11 @@ typedef struct {
     int32_t do_add;   /* Eq. 3-24 due (consumed by serbf_add_kernels) */
     int32_t n_l2, n_bf;
     int32_t m_added, m_pruned;
-    int32_t reserved[2];
+    int32_t step;     /* steps done in the current epoch (mini-batches) */
+    int32_t reserved;
     double lr;        /* learning rate of the next epoch */
     double alpha, beta;
+    double l2_epoch;  /* sum of the batch L2 values of the current epoch */
     double l2_hist[64];  /* L2 of epoch e at index (e - 1) mod k_l2 */
     int32_t bf_hist[256]; /* b_f of epoch e at index (e - 1) mod k_l1 */
 } serbf_state;
@@ -242,6 +247,23 @@ int serbf_gather(const float *src, const uint32_t *perm, float *dst, int64_t n, 
 int serbf_build_neighbors(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg,
                           serbf_csr *kmajor, serbf_csr *pmajor, int64_t *npairs, serbf_workspace *ws,
                           void *stream);
+
+/* ------------------------------------------------------------------ initialisation */
+/* Algorithm 1 and Eq. 3-12: initial kernels from the interior training points
+ * (1 < t < 2).  Greedy largest inscribed spheres: repeatedly the interior point
+ * with the largest |S_raw| (the exact SDF value, i.e. the distance to the
+ * surface; the first in binned order among equal values) becomes a centre with
+ * weight t, and every interior point whose squared distance to it is not above
+ * fl(|S|^2) is removed (float distances in the support predicate's operation
+ * order).  Then d_1 = d_2 = d_3 = 2 sqrt(-ln(gamma / w^2)) / dhat with dhat the
+ * distance to the nearest other centre (one centre alone: twice its |S|),
+ * angles 0.  Writes the first min(M, cap) kernels in selection order and sets
+ * the device count; *m_out (host, may be NULL) receives M.  Uses the binning
+ * of pts (serbf_bin_points) and its scratch.  SYNCHRONISES the stream.
+ * ECAPACITY when M > cap (the first cap kernels are written), EINVAL on bad
+ * arguments or gamma outside (0, 1). */
+int serbf_init_kernels(const serbf_points *pts, const float *S_raw, double gamma, serbf_params *prm, int32_t *m_out,
+                       serbf_workspace *ws, void *stream);
 
 /* ------------------------------------------------------------------ a4 */
 /* Eq. 3-26 forward over the pairs of Eq. 3-15-1, Eq. 3-18 filter and the

@@ -25,8 +25,9 @@ u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
 class State(C.Structure):
     _fields_ = [("epoch", C.c_int32), ("l1_optim", C.c_int32), ("phase2", C.c_int32),
                 ("adam_t", C.c_int32), ("do_prune", C.c_int32), ("do_add", C.c_int32),
-                ("n_l2", C.c_int32), ("n_bf", C.c_int32), ("lr", C.c_double), ("alpha", C.c_double),
-                ("beta", C.c_double), ("l2_hist", C.c_double * 64), ("bf_hist", C.c_int32 * 256)]
+                ("n_l2", C.c_int32), ("n_bf", C.c_int32), ("step", C.c_int32), ("pad", C.c_int32),
+                ("lr", C.c_double), ("alpha", C.c_double), ("beta", C.c_double), ("l2_epoch", C.c_double),
+                ("l2_hist", C.c_double * 64), ("bf_hist", C.c_int32 * 256)]
 
 
 class Cfg(C.Structure):
@@ -34,7 +35,7 @@ class Cfg(C.Structure):
                 ("beta1", C.c_double), ("beta2", C.c_double), ("adam_eps", C.c_double),
                 ("tau_m", C.c_double), ("tau_d", C.c_double), ("tau_l1", C.c_double),
                 ("tau_l2", C.c_double), ("k_l1", C.c_int32), ("k_l2", C.c_int32), ("T_e", C.c_int32),
-                ("M_e", C.c_int32)]
+                ("M_e", C.c_int32), ("epoch_steps", C.c_int32), ("pad", C.c_int32)]
 
 
 def lib():
@@ -79,6 +80,9 @@ def lib():
                                        C.c_float, i32p]
         L.oracle_new_kernel.argtypes = [C.c_float, C.c_float, C.c_float, C.c_float, C.c_double,
                                         C.c_double, f64p]
+        L.oracle_inscribed.restype = C.c_int32
+        L.oracle_inscribed.argtypes = [f32p, f32p, f32p, f32p, f32p, C.c_int64, i32p, C.c_int32]
+        L.oracle_init_shape.argtypes = [f64p, f64p, f64p, f64p, f64p, C.c_int32, C.c_double, f64p]
         _lib = L
     return _lib
 
@@ -201,10 +205,11 @@ def adam(p, g, mo, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
     return p, mo, v
 
 
-def default_cfg(T_e=1600, M_e=2000, lr0=0.01):
+def default_cfg(T_e=1600, M_e=2000, lr0=0.01, epoch_steps=1):
     """Algorithm 3 input line and Sec. 4.1 settings; Adam moments at the usual defaults."""
     return Cfg(lr0=lr0, lr_p2=1e-3, lr_min=1e-5, beta1=0.9, beta2=0.999, adam_eps=1e-8,
-               tau_m=0.02, tau_d=0.01, tau_l1=5.0, tau_l2=0.5, k_l1=50, k_l2=10, T_e=T_e, M_e=M_e)
+               tau_m=0.02, tau_d=0.01, tau_l1=5.0, tau_l2=0.5, k_l1=50, k_l2=10, T_e=T_e, M_e=M_e,
+               epoch_steps=epoch_steps)
 
 
 def state_init(cfg):
@@ -214,7 +219,8 @@ def state_init(cfg):
 
 
 def step(P, m, grad, mo, v, l2, max_abs_e, cfg, st):
-    """One Algorithm 3 epoch update in place on float64 arrays P, mo, v (10 x cap)."""
+    """One Algorithm 3 update in place on float64 arrays P, mo, v (10 x cap); the
+    epoch tail runs after every cfg.epoch_steps-th call."""
     cap = P.shape[1]
     lib().oracle_step(P.reshape(-1), cap, m, np.ascontiguousarray(grad, np.float64).reshape(-1),
                       mo.reshape(-1), v.reshape(-1), l2, max_abs_e, C.byref(cfg), C.byref(st))
@@ -248,3 +254,21 @@ def new_kernel(p, e, dbar, eps=1e-7):
     out = np.zeros(10, np.float64)
     lib().oracle_new_kernel(float(p[0]), float(p[1]), float(p[2]), float(e), dbar, eps, out)
     return out
+
+
+def inscribed(x, y, z, t, S, max_out=1 << 20):
+    """Algorithm 1: indices of the selected centres, in order."""
+    x, y, z, t, S = _f32(x), _f32(y), _f32(z), _f32(t), _f32(S)
+    out = np.zeros(max(max_out, 1), np.int32)
+    n = lib().oracle_inscribed(x, y, z, t, S, x.shape[0], out, max_out)
+    return out[:min(n, max_out)].copy(), n
+
+
+def init_shape(c, w, r, gamma=1e-3):
+    """Eq. 3-12 for centres c (M x 3), weights w, radii r: the axis parameter d."""
+    c = np.ascontiguousarray(c, np.float64)
+    w, r = np.ascontiguousarray(w, np.float64), np.ascontiguousarray(r, np.float64)
+    d = np.zeros(max(len(w), 1))
+    lib().oracle_init_shape(np.ascontiguousarray(c[:, 0]), np.ascontiguousarray(c[:, 1]),
+                            np.ascontiguousarray(c[:, 2]), w, r, len(w), gamma, d)
+    return d[:len(w)]

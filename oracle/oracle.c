@@ -454,6 +454,18 @@ void oracle_step(double *P, int32_t cap, int32_t m, const double *grad, double *
     free(mk);
     free(vk);
 
+    /* Algorithm 3 runs the gates once per epoch, after its last batch: with
+     * epoch_steps > 1 mini-batches the L2 of the epoch is the sum of its
+     * batch values (reading of the per-epoch L2 for mini-batches) */
+    l2 += st->l2_epoch;
+    if (st->step + 1 < (cfg->epoch_steps > 1 ? cfg->epoch_steps : 1)) {
+        st->step += 1;
+        st->l2_epoch = l2;
+        return;
+    }
+    st->step = 0;
+    st->l2_epoch = 0.0;
+
     /* epoch tail */
     st->do_prune = (e % cfg->k_l2 == 0) && st->l1_optim && (e < cfg->T_e);
     int32_t bf = 0;
@@ -592,4 +604,72 @@ void oracle_new_kernel(float px, float py, float pz, float e, double dbar, doubl
     out[TY] = 0.0;
     out[TZ] = 0.0;
     out[W] = -sgn(e) * ae;
+}
+
+/* ---------------------------------------------------------------------------
+ * Algorithm 1, greedy largest inscribed spheres over the interior points.
+ * Interior: 1 < t < 2 (targets of Eq. 3-10).  d_in = |S|: the exact SDF is
+ * the distance to the surface, read as the closest distance to the samples
+ * P.  Each round takes the remaining point with the largest d_in (the lowest
+ * index among equal values, as an argmax does), appends it (centre, weight
+ * t) and keeps only the points whose squared distance to it exceeds r^2,
+ * r = its d_in (the printed comparison of a squared distance with r is read
+ * as the squared radius).  The distance and r^2 are float with the support
+ * predicate's operation order, so another implementation can take the same
+ * decisions.  Writes the selected indices in order; returns how many (at
+ * most max_out; more are counted but not written).
+ * Pinned by: coverage, order and non-overlap properties and a hand example. */
+int32_t oracle_inscribed(const float *x, const float *y, const float *z, const float *t, const float *S,
+                         int64_t n, int32_t *out, int32_t max_out) {
+    uint8_t *alive = (uint8_t *)malloc((size_t)(n ? n : 1));
+    int64_t left = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        alive[i] = (1.0f < t[i]) && (t[i] < 2.0f);
+        left += alive[i];
+    }
+    int32_t cnt = 0;
+    while (left > 0) {
+        int64_t best = -1;
+        float bd = -1.0f;
+        for (int64_t i = 0; i < n; ++i)
+            if (alive[i] && fabsf(S[i]) > bd) {
+                bd = fabsf(S[i]);
+                best = i;
+            }
+        if (cnt < max_out) out[cnt] = (int32_t)best;
+        ++cnt;
+        const float r2 = bd * bd;
+        for (int64_t k = 0; k < n; ++k) {
+            if (!alive[k]) continue;
+            const float dx = x[k] - x[best], dy = y[k] - y[best], dz = z[k] - z[best];
+            const float d2 = (dx * dx + dy * dy) + dz * dz;
+            if (!(d2 > r2)) {
+                alive[k] = 0;
+                --left;
+            }
+        }
+    }
+    free(alive);
+    return cnt;
+}
+
+/* ---------------------------------------------------------------------------
+ * Eq. 3-12: isotropic axis parameters from the nearest other centre,
+ *     d_j1 = d_j2 = d_j3 = 2 sqrt(-ln(gamma / w_j^2)) / dhat_j,
+ * dhat_j = min_i ||c_j - c_i||, i != j (a single centre: dhat = 2 r_j, the
+ * diameter of its sphere -- the paper does not cover that case).
+ * Pinned by: Eq. 3-11 (w^2 exp(-d^2 (dhat/2)^2) = gamma) and brute force. */
+void oracle_init_shape(const double *cx, const double *cy, const double *cz, const double *w, const double *r,
+                       int32_t M, double gamma, double *d) {
+    for (int32_t j = 0; j < M; ++j) {
+        double best = INFINITY;
+        for (int32_t i = 0; i < M; ++i) {
+            if (i == j) continue;
+            const double dx = cx[j] - cx[i], dy = cy[j] - cy[i], dz = cz[j] - cz[i];
+            const double dd = sqrt(dx * dx + dy * dy + dz * dz);
+            if (dd < best) best = dd;
+        }
+        if (M == 1) best = 2.0 * r[j];
+        d[j] = 2.0 * sqrt(-log(gamma / (w[j] * w[j]))) / best;
+    }
 }

@@ -86,8 +86,11 @@ typedef struct {
     int32_t do_add;    /* Eq. 3-24 due at the end of this epoch */
     int32_t n_l2;      /* filled entries of l2_hist */
     int32_t n_bf;      /* filled entries of bf_hist */
+    int32_t step;      /* steps done in the current epoch (mini-batches) */
+    int32_t pad;
     double lr;         /* learning rate of the next epoch */
     double alpha, beta;
+    double l2_epoch;   /* sum of the batch L2 values of the current epoch */
     double l2_hist[64];
     int32_t bf_hist[256];
 } oracle_state;
@@ -96,6 +99,8 @@ typedef struct {
     double lr0, lr_p2, lr_min, beta1, beta2, adam_eps;
     double tau_m, tau_d, tau_l1, tau_l2;
     int32_t k_l1, k_l2, T_e, M_e;
+    int32_t epoch_steps; /* optimiser steps per epoch (1: full batch) */
+    int32_t pad;
 } oracle_cfg;
 
 void oracle_state_init(oracle_state *st, const oracle_cfg *cfg);
@@ -113,6 +118,12 @@ int32_t oracle_local_max(const float *x, const float *y, const float *z, const f
                          const uint8_t *mask, int64_t n, const int32_t *cand, int32_t nc, float r2,
                          int32_t *out);
 void oracle_new_kernel(float px, float py, float pz, float e, double dbar, double eps, double out[10]);
+
+/* Algorithm 1 (greedy inscribed spheres) and Eq. 3-12 (isotropic shapes). */
+int32_t oracle_inscribed(const float *x, const float *y, const float *z, const float *t, const float *S,
+                         int64_t n, int32_t *out, int32_t max_out);
+void oracle_init_shape(const double *cx, const double *cy, const double *cz, const double *w, const double *r,
+                       int32_t M, double gamma, double *d);
 
 #ifdef __cplusplus
 }

@@ -36,14 +36,14 @@ class Config(C.Structure):
                 ("adam_eps", C.c_double), ("topk_frac", C.c_double), ("add_radius", C.c_double),
                 ("dbar_min", C.c_double), ("k_l1", C.c_int32), ("k_l2", C.c_int32), ("T_e", C.c_int32),
                 ("M_e", C.c_int32), ("kahan", C.c_int32), ("fwd_warps", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("epoch_steps", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class State(C.Structure):
     _fields_ = [("epoch", C.c_int32), ("l1_optim", C.c_int32), ("phase2", C.c_int32), ("adam_t", C.c_int32),
                 ("do_prune", C.c_int32), ("do_add", C.c_int32), ("n_l2", C.c_int32), ("n_bf", C.c_int32),
-                ("m_added", C.c_int32), ("m_pruned", C.c_int32), ("reserved", C.c_int32 * 2),
-                ("lr", C.c_double), ("alpha", C.c_double), ("beta", C.c_double),
+                ("m_added", C.c_int32), ("m_pruned", C.c_int32), ("step", C.c_int32), ("reserved", C.c_int32),
+                ("lr", C.c_double), ("alpha", C.c_double), ("beta", C.c_double), ("l2_epoch", C.c_double),
                 ("l2_hist", C.c_double * 64), ("bf_hist", C.c_int32 * 256)]
 
 
@@ -86,6 +86,8 @@ _SIGS = {
     "serbf_gather": (C.c_int, [VP, VP, VP, C.c_int64, VP]),
     "serbf_build_neighbors": (C.c_int, [C.POINTER(Points), C.POINTER(Params), C.POINTER(Config),
                                         C.POINTER(Csr), C.POINTER(Csr), C.POINTER(C.c_int64), VP, VP]),
+    "serbf_init_kernels": (C.c_int, [C.POINTER(Points), VP, C.c_double, C.POINTER(Params), C.POINTER(C.c_int32), VP,
+                                     VP]),
     "serbf_forward": (C.c_int, [C.POINTER(Points), C.POINTER(Params), C.POINTER(Config), VP, VP, VP, VP,
                                 VP, VP]),
     "serbf_forward_backward": (C.c_int, [C.POINTER(Points), C.POINTER(Params), C.POINTER(Config), VP, VP, VP, VP,
@@ -219,6 +221,15 @@ def serbf_build_neighbors(pts, prm, cfg, ws_host, kmajor=None, pmajor=None, stre
                                     C.addressof(ws_host), _stream(stream))
     _check("serbf_build_neighbors", rc, ok=(SERBF_OK, SERBF_ECAPACITY))
     return rc, npairs.value
+
+
+def serbf_init_kernels(pts, S_raw, gamma, prm, ws_host, stream=None):
+    """Algorithm 1 + Eq. 3-12; returns (status, number of centres found)."""
+    mo = C.c_int32(0)
+    rc = _lib.serbf_init_kernels(C.byref(pts), _p(S_raw), float(gamma), C.byref(prm), C.byref(mo),
+                                 C.addressof(ws_host), _stream(stream))
+    _check("serbf_init_kernels", rc, ok=(SERBF_OK, SERBF_ECAPACITY))
+    return rc, mo.value
 
 
 def serbf_forward(pts, prm, cfg, psi, err, mask, stats, ws_host, stream=None):

@@ -253,6 +253,7 @@ int serbf_config_default(serbf_config *c) {
     c->T_e = 1600;
     c->M_e = 2000;
     c->kahan = 0;
+    c->epoch_steps = 1;
     return SERBF_OK;
 }
 

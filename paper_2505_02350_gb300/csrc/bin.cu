@@ -9,6 +9,8 @@
 // refinement entry point, which re-bins the grown training set.
 #include <math.h>
 
+#include <utility>
+
 #include "common.cuh"
 
 using namespace serbf;
@@ -219,6 +221,25 @@ int gsz(int64_t n, int t) {
 
 }  // namespace
 
+namespace serbf {
+
+int radix_sort_pairs(uint32_t **k, uint32_t **v, uint32_t **ktmp, uint32_t **vtmp, int64_t n, int bits,
+                     uint32_t *hist, cudaStream_t s) {
+    const int64_t nblk = (n + kSortTile - 1) / kSortTile;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_radix_hist<<<(unsigned)nblk, 256, 0, s>>>(*k, n, shift, hist, nblk);
+        int rc = launch_exscan_u32(hist, 256 * nblk, s);
+        if (rc) return rc;
+        k_radix_scatter<<<(unsigned)nblk, 256, 0, s>>>(*k, *v, *ktmp, *vtmp, n, shift, hist, nblk);
+        std::swap(*k, *ktmp);
+        std::swap(*v, *vtmp);
+    }
+    SERBF_CHECK_LAUNCH();
+    return SERBF_OK;
+}
+
+}  // namespace serbf
+
 extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, int64_t n, const serbf_grid *grid,
                                 uint32_t *perm, float *xb, float *yb, float *zb, serbf_workspace *ws,
                                 void *stream) {
@@ -248,19 +269,8 @@ extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, 
         k_keys<<<gsz(n, 256), 256, 0, s>>>(x, y, z, n, *grid, sf, nsx, nsy, kin, vin);
         int nbits = 1;
         while (nbits < 32 && (1ll << nbits) < ncp) ++nbits;
-        int64_t nblk = (n + kSortTile - 1) / kSortTile;
-        for (int shift = 0; shift < nbits; shift += 8) {
-            k_radix_hist<<<(unsigned)nblk, 256, 0, s>>>(kin, n, shift, ws->hist, nblk);
-            int rc = launch_exscan_u32(ws->hist, 256 * nblk, s);
-            if (rc) return rc;
-            k_radix_scatter<<<(unsigned)nblk, 256, 0, s>>>(kin, vin, kout, vout, n, shift, ws->hist, nblk);
-            uint32_t *t = kin;
-            kin = kout;
-            kout = t;
-            t = vin;
-            vin = vout;
-            vout = t;
-        }
+        int rc = radix_sort_pairs(&kin, &vin, &kout, &vout, n, nbits, ws->hist, s);
+        if (rc) return rc;
         k_apply_perm<<<gsz(n, 256), 256, 0, s>>>(vin, x, y, z, n, perm, xb, yb, zb);
     }
     k_zero_u32<<<gsz(ncp + 1, 256), 256, 0, s>>>(ws->cell_start, ncp + 1);

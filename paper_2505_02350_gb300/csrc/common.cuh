@@ -34,6 +34,13 @@ struct FwdPart {
     unsigned long long pairs;
 };
 
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
+// keys (8 bits per pass, kSortTile elements per block; hist holds
+// 256 x blocks + 1 words).  On return *k and *v point to whichever of the two
+// buffer pairs holds the result.  Defined in bin.cu.
+int radix_sort_pairs(uint32_t **k, uint32_t **v, uint32_t **ktmp, uint32_t **vtmp, int64_t n, int bits,
+                     uint32_t *hist, cudaStream_t s);
+
 }  // namespace serbf
 
 // Host-side description of the caller's scratch buffer.

@@ -137,12 +137,30 @@ __device__ __forceinline__ float adam_param(const StepArgs &a, int r, int j, con
 }
 
 // The epoch tail of Algorithm 3 on a shared-memory copy of the state, run by
-// one warp: histories, deletion due (every k^l2 epochs while l1_optim and
+// one warp after the epoch's last step (mini-batches: every epoch_steps-th
+// step, on the sum of the batch L2 values): histories, deletion due (every k^l2 epochs while l1_optim and
 // e < T^e), Eq. l1_activate (population std of the last k^l2 L2 values <
 // tau^l2), Eq. add_activate (range of the last k^l1 values of b_f < tau^l1),
 // the L2-only phase with a cosine learning rate from T^e.
 __device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float alpha, float beta, int lane) {
-    const double l2 = a.stats[SERBF_STAT_L2];
+    // per step: Adam counter, alpha/beta, the epoch's L2 sum; the gates only
+    // after the epoch's last step (every step when epoch_steps <= 1)
+    const int steps = a.c.epoch_steps > 1 ? a.c.epoch_steps : 1;
+    const double l2_step = a.stats[SERBF_STAT_L2];
+    const double l2 = st.l2_epoch + l2_step;
+    __syncwarp();
+    if (st.step + 1 < steps) {
+        if (lane == 0) {
+            st.l2_epoch = l2;
+            st.step = st.step + 1;
+            st.alpha = alpha;
+            st.beta = beta;
+            st.adam_t = st.adam_t + 1;
+            a.stats[SERBF_STAT_BF] = bf;
+            a.stats[SERBF_STAT_LOSS] = (float)alpha * (float)l2_step + (float)beta * (float)a.stats[SERBF_STAT_L1];
+        }
+        return;
+    }
     const int e = st.epoch + 1;
     const int kl2 = a.c.k_l2, kl1 = a.c.k_l1;
     int l1n = st.l1_optim;
@@ -212,6 +230,8 @@ __device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float 
         st.alpha = alpha;
         st.beta = beta;
         st.adam_t = st.adam_t + 1;
+        st.step = 0;
+        st.l2_epoch = 0.0;
         st.do_prune = do_prune;
         st.do_add = do_add;
         st.l1_optim = l1n;
@@ -219,7 +239,7 @@ __device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float 
         st.lr = lr_next;
         st.epoch = e;
         a.stats[SERBF_STAT_BF] = bf;
-        a.stats[SERBF_STAT_LOSS] = (float)alpha * (float)l2 + (float)beta * (float)a.stats[SERBF_STAT_L1];
+        a.stats[SERBF_STAT_LOSS] = (float)alpha * (float)l2_step + (float)beta * (float)a.stats[SERBF_STAT_L1];
     }
 }
 

@@ -137,6 +137,16 @@ class Problem:
     def prm(self):
         return N.params(self.p, self.m_dev)
 
+    def init_kernels(self, gamma=1e-3):
+        """Replace the kernels by Algorithm 1 + Eq. 3-12 on the current training
+        points (fresh Adam moments).  Returns the number of centres found
+        (kernels beyond the capacity are dropped)."""
+        n = self.n
+        _rc, found = N.serbf_init_kernels(self.pts, self.sb[:n], gamma, self.prm, self.ws)
+        self.adam_m.zero_()
+        self.adam_v.zero_()
+        return found
+
     # ------------------------------------------------------------ hot path
     def build_neighbors(self, kmajor=None, pmajor=None):
         return N.serbf_build_neighbors(self.pts, self.prm, self.cfg, self.ws, kmajor, pmajor)
@@ -266,3 +276,80 @@ class Problem:
         return dict(x=self.xb[:n].cpu().numpy(), y=self.yb[:n].cpu().numpy(), z=self.zb[:n].cpu().numpy(),
                     t=self.tb[:n].cpu().numpy(), S=self.sb[:n].cpu().numpy(),
                     perm=self.perm[:n].cpu().numpy().astype(np.int64))
+
+
+class MiniBatch:
+    """Algorithm 3 with mini-batches of training points (the paper's B_s).
+
+    Every epoch the training points are shuffled (seeded permutation) and cut
+    into batches of `batch_size`; each batch is gathered, binned into a small
+    workspace of its own, and taken through the fused forward + adjoint and
+    one optimiser step on the parent problem's parameters, Adam moments and
+    state (cfg.epoch_steps = batches per epoch, so the gates run after the
+    epoch's last batch on the summed batch L2).  After the epoch: deletion
+    and, when due, the addition, whose residuals come from a forward over all
+    training points with the epoch's final parameters.
+    """
+
+    def __init__(self, problem, batch_size, seed=0):
+        pb = problem
+        self.pb = pb
+        self.bs = int(batch_size)
+        self.rng = np.random.default_rng(seed)
+        dev = pb.dev
+        f32 = dict(dtype=torch.float32, device=dev)
+        B = self.bs
+        self.idx = torch.zeros(pb.max_points, dtype=torch.int32, device=dev)
+        self.raw = [torch.zeros(B, **f32) for _ in range(4)]  # x, y, z, t in batch order
+        self.perm = torch.zeros(B, dtype=torch.int32, device=dev)
+        self.xb, self.yb, self.zb, self.tb = (torch.zeros(B, **f32) for _ in range(4))
+        self.psi, self.err = torch.zeros(B, **f32), torch.zeros(B, **f32)
+        self.mask = torch.zeros(B, dtype=torch.uint8, device=dev)
+        sz = N.WsSizes(B, pb.cap, pb.sizes.max_cells, 0, pb.sizes.super_cap, pb.sizes.super_factor, 0)
+        nbytes = N.serbf_workspace_bytes(sz)
+        self.ws_dev = torch.zeros(nbytes + 256, dtype=torch.uint8, device=dev)
+        off = (-self.ws_dev.data_ptr()) % 256
+        self.ws = N.workspace_struct()
+        N.serbf_workspace_init(self.ws, self.ws_dev[off:off + nbytes], sz)
+        self.cfg = N.Config.from_buffer_copy(pb.cfg)
+        self.batches = []  # host copies of the last epoch's batches (binned indices of the parent)
+
+    def close(self):
+        if self.ws_dev is not None:
+            torch.cuda.synchronize(self.pb.dev)
+            N.serbf_workspace_release(self.ws)
+            self.ws_dev = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def epoch(self):
+        pb, B = self.pb, self.bs
+        n = pb.n
+        order = self.rng.permutation(n).astype(np.int32)
+        self.idx[:n] = torch.as_tensor(order, device=pb.dev)
+        nb = (n + B - 1) // B
+        self.batches = [order[b * B:min(n, (b + 1) * B)] for b in range(nb)]
+        cfg = self.cfg
+        cfg.epoch_steps = nb
+        for b in range(nb):
+            i0, k = b * B, min(n, (b + 1) * B) - b * B
+            sel = self.idx[i0:i0 + k]
+            for src, dst in zip((pb.xb, pb.yb, pb.zb, pb.tb), self.raw):
+                N.serbf_gather(src, sel, dst, k)
+            N.serbf_bin_points(self.raw[0][:k], self.raw[1][:k], self.raw[2][:k], pb.grid, self.perm[:k],
+                               self.xb[:k], self.yb[:k], self.zb[:k], self.ws)
+            N.serbf_gather(self.raw[3], self.perm[:k], self.tb, k)
+            pts = N.points(self.xb[:k], self.yb[:k], self.zb[:k], self.tb[:k], k)
+            N.serbf_build_neighbors(pts, pb.prm, cfg, self.ws)
+            N.serbf_forward_backward(pts, pb.prm, cfg, self.psi[:k], self.err[:k], self.mask[:k], pb.grad,
+                                     pb.stats, self.ws)
+            N.serbf_step(pb.prm, pb.grad, pb.adam_m, pb.adam_v, pb.state, pb.stats, cfg, pb.ws)
+        pb.prune()
+        if pb.state_host().do_add:
+            pb.build_neighbors()
+            pb.forward()
+            pb.add()

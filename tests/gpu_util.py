@@ -1,5 +1,7 @@
 """Helpers shared by the GPU parity tests: build problems from the seeded
-synthetic inputs and pull device results back for comparison with the oracle."""
+synthetic inputs, and give the oracle its own copy of those inputs in the
+binned order (binned by the oracle, targets normalised by the oracle), so
+that no oracle input comes from the GPU path."""
 import numpy as np
 
 import synth
@@ -24,7 +26,23 @@ def problem(name, layers=None, cap=None, **kw):
     grids = cfg["grids"] if layers is None else layers
     spacing = synth.spacing(max(grids))
     m = cfg["m"]
-    return field.Problem(x, y, z, S, P, m, spacing, cap=cap or m, **kw)
+    pb = field.Problem(x, y, z, S, P, m, spacing, cap=cap or m, **kw)
+    pb.test_src = (x, y, z, S, np.asarray(P, np.float64))
+    return pb
+
+
+def oracle_view(pb, orc):
+    """The problem's inputs as the oracle sees them: binned with the oracle's
+    binning (which must give the GPU's permutation -- checked), targets from
+    the oracle's Eq. 3-10.  Returns dict(x, y, z, t, S) in binned order."""
+    x, y, z, S, _ = pb.test_src
+    g = pb.grid
+    perm = orc.bin_points(x, y, z, tuple(g.origin), g.h, tuple(g.n), pb.sizes.super_factor).astype(np.int64)
+    gpu_perm = pb.perm[:pb.n].cpu().numpy().astype(np.int64)
+    assert np.array_equal(perm, gpu_perm), "binning differs from the oracle's"
+    t, _, _ = orc.normalize(S)
+    t = t.astype(np.float32)
+    return dict(x=x[perm], y=y[perm], z=z[perm], t=t[perm], S=S[perm])
 
 
 def host_params(pb):

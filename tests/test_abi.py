@@ -52,7 +52,7 @@ def test_config_defaults_match_algorithm3(native):
 
 def test_struct_sizes_match_header(native):
     assert C.sizeof(native.Config) == 160
-    assert native.STATE_BYTES == 48 + 24 + 64 * 8 + 256 * 4
+    assert native.STATE_BYTES == 48 + 32 + 64 * 8 + 256 * 4
 
 
 def test_workspace_sizing_is_host_only(native):

@@ -4,7 +4,7 @@ differences (h = 1e-3) of the GPU forward, and against the FP64 oracle."""
 import numpy as np
 import pytest
 
-from gpu_util import host_params, problem, rel_l2, torch_cuda
+from gpu_util import host_params, oracle_view, problem, rel_l2, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -31,7 +31,7 @@ def test_autograd_matches_oracle(setup, orc):
     w = _upstream(torch, pb)
     psi = erbf_field(pb, p)
     (psi * w).sum().backward()
-    h = pb.binned_host()
+    h = oracle_view(pb, orc)
     P = host_params(pb)
     g_o, _ = orc.backward(h["x"], h["y"], h["z"], 0.5 * w.cpu().numpy().astype(np.float64), P, m)
     g = p.grad[:, :m].cpu().numpy()

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import torch_cuda
+from gpu_util import oracle_view, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -56,11 +56,12 @@ def test_sphere_fit_tracks_oracle(orc):
     cfg, lay, P = synth.workload("c1")
     x, y, z, S = lay[0]
     pb = field.Problem(x, y, z, S, P, cfg["m"], synth.spacing(32), cap=256)
+    pb.test_src = (x, y, z, S, np.asarray(P, np.float64))
     fit = Fitter(pb)
     hist = fit.run(200, log_every=1)
     msq_gpu = np.array([h["l2"] / max(h["count"], 1) for h in hist])
     assert np.all(np.isfinite(msq_gpu))
-    h = pb.binned_host()
+    h = oracle_view(pb, orc)
     P0 = np.zeros((10, 256))
     P0[:, :cfg["m"]] = P[:, :cfg["m"]]
     ref, m_or = _oracle_run(orc, h["x"], h["y"], h["z"], h["t"], h["S"], P0, cfg["m"], 200, pb.cfg)

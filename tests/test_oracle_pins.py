@@ -428,6 +428,34 @@ def test_gate_phase2_cosine_lr(orc):
     assert all(ph for (e, l1, pr, ad, ph, r) in h if e >= 20)
 
 
+def test_minibatch_epoch_gates_follow_the_epoch_sum(orc):
+    """Algorithm 3 with mini-batches: Adam runs per batch, the gates once per
+    epoch on the sum of the batch L2 values -- the same gate sequence as a
+    full-batch run fed those sums."""
+    m, cap, nb = 4, 4, 3
+    P = np.zeros((10, cap))
+    P[3:6] = 5.0
+    P[9] = 0.5
+    zero = np.zeros((10, m))
+    cfg_b = orc.default_cfg(T_e=40, M_e=50, epoch_steps=nb)
+    cfg_f = orc.default_cfg(T_e=40, M_e=50)
+    sb, sf = orc.state_init(cfg_b), orc.state_init(cfg_f)
+    Pb, Pf = P.copy(), P.copy()
+    mb, vb, mf, vf = (np.zeros((10, cap)) for _ in range(4))
+    for e in range(45):
+        parts = [30.0 - e + 0.25 * k if e < 8 else 1.0 + 0.1 * k for k in range(nb)]
+        for k in range(nb):
+            orc.step(Pb, m, zero, mb, vb, parts[k], 0.5, cfg_b, sb)
+            if k < nb - 1:
+                assert sb.epoch == e and sb.step == k + 1
+        orc.step(Pf, m, zero, mf, vf, (parts[0] + parts[1]) + parts[2], 0.5, cfg_f, sf)
+        assert (sb.epoch, sb.l1_optim, sb.phase2, sb.do_prune, sb.do_add, sb.step) == \
+            (sf.epoch, sf.l1_optim, sf.phase2, sf.do_prune, sf.do_add, 0), e
+        assert list(sb.l2_hist[:10]) == list(sf.l2_hist[:10])
+        assert sb.adam_t == nb * sf.adam_t
+        assert sb.lr == sf.lr
+
+
 # ---------------------------------------------------------------- Eq. 3-27
 def test_prune_keeps_order_and_threshold(orc):
     g = np.random.default_rng(13)
@@ -494,3 +522,59 @@ def test_synthetic_grid_and_sphere_targets(orc):
     t, m, h = orc.normalize(S)
     assert m == S.min()
     assert np.all((t > 1.0) == (S < 0)) and t.max() == pytest.approx(2.0)
+
+
+# ---------------------------------------------------------------- Algorithm 1, Eq. 3-12
+def test_inscribed_hand_example(orc):
+    # five interior points on a line (t in (1, 2)); |S| = 0.30 at x=0 covers
+    # x = 0.25 (d^2 = 0.0625 <= 0.09); the next largest uncovered is x = 0.8
+    # (|S| 0.1) which covers x = 0.72 but not x = 1.1 (d^2 = 0.09 > 0.01)
+    x = np.array([0.0, 0.25, 0.72, 0.8, 1.1], np.float32)
+    z0 = np.zeros(5, np.float32)
+    S = np.array([-0.30, -0.20, -0.05, -0.10, -0.02], np.float32)
+    t = np.full(5, 1.5, np.float32)
+    idx, n = orc.inscribed(x, z0, z0, t, S)
+    assert n == 3 and list(idx) == [0, 3, 4]
+
+
+def test_inscribed_skips_exterior_and_takes_first_of_ties(orc):
+    x = np.array([0.0, 5.0, 10.0, 15.0], np.float32)
+    z0 = np.zeros(4, np.float32)
+    S = np.array([-1.0, -2.0, -2.0, 0.5], np.float32)
+    t = np.array([1.5, 1.5, 1.5, 0.5], np.float32)  # the last point is outside (t < 1)
+    idx, n = orc.inscribed(x, z0, z0, t, S)
+    assert list(idx) == [1, 2, 0]
+
+
+def test_inscribed_properties_on_sphere(orc):
+    x, y, z = synth.grid(24)
+    S = synth.sdf_sphere(x, y, z)
+    t = orc.normalize(S)[0].astype(np.float32)
+    idx, n = orc.inscribed(x, y, z, t, S)
+    interior = np.flatnonzero((t > 1) & (t < 2))
+    r = np.abs(S[idx]).astype(np.float32)
+    # the first centre is the deepest interior point; radii never grow
+    assert idx[0] == interior[np.argmax(np.abs(S[interior]))]
+    assert np.all(np.diff(r) <= 0)
+    d2 = lambda i, j: (np.float32(x[i] - x[j]) ** 2 + np.float32(y[i] - y[j]) ** 2) + np.float32(z[i] - z[j]) ** 2
+    # every interior point lies in some selected sphere; no centre lies in an earlier one
+    cover = np.zeros(interior.size, bool)
+    for c, rc in zip(idx, r):
+        cover |= d2(interior, c) <= rc * rc
+    assert cover.all()
+    for a in range(1, len(idx)):
+        assert np.all(d2(idx[a], idx[:a]) > r[:a] * r[:a])
+
+
+def test_init_shape_satisfies_eq3_11(orc):
+    g = np.random.default_rng(21)
+    c = g.uniform(-1, 1, (7, 3))
+    w = g.uniform(1.05, 2.0, 7)
+    r = g.uniform(0.1, 0.3, 7)
+    gamma = 1e-3
+    d = orc.init_shape(c, w, r, gamma)
+    for j in range(7):
+        dhat = min(np.linalg.norm(c[j] - c[i]) for i in range(7) if i != j)
+        assert w[j] ** 2 * np.exp(-d[j] ** 2 * (dhat / 2) ** 2) == pytest.approx(gamma, rel=1e-12)
+    d1 = orc.init_shape(c[:1], w[:1], r[:1], gamma)
+    assert w[0] ** 2 * np.exp(-d1[0] ** 2 * r[0] ** 2) == pytest.approx(gamma, rel=1e-12)  # dhat = 2 r
