@@ -243,6 +243,18 @@ __device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float 
     }
 }
 
+// The epoch tail (warp 0) on a shared-memory copy of the state, written back.
+__device__ void finish_step(const StepArgs &a, double bf, const float (&sc)[4], uint32_t *s_words) {
+    const uint32_t *gw = reinterpret_cast<const uint32_t *>(a.st);
+    for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) s_words[k] = gw[k];
+    __syncthreads();
+    serbf_state &st = *reinterpret_cast<serbf_state *>(s_words);
+    if (threadIdx.x < 32) epoch_tail(a, st, bf, sc[0], sc[1], threadIdx.x);
+    __syncthreads();
+    uint32_t *gwo = reinterpret_cast<uint32_t *>(a.st);
+    for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) gwo[k] = s_words[k];
+}
+
 // ---------------------------------------------------------------- grid path
 // Stage 1 (one thread per kernel, many blocks): the sums of alpha_terms; the
 // last block turns them into alpha, beta and the Adam bias corrections.
@@ -309,22 +321,13 @@ __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // the last block: b_f, then the epoch tail (warp 0) on a shared copy of the state
-    const uint32_t *gw = reinterpret_cast<const uint32_t *>(a.st);
-    for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) s_words[k] = gw[k];
+    // the last block: b_f, then the epoch tail
     float cnt = 0.f;
     for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) cnt += __ldcg(a.part + b);
     float cc[1] = {cnt};
     block_sums_ff<1>(cc, sh1, tot);
-    const double bf = (double)tot[0].hi + tot[0].lo;
-    serbf_state &st = *reinterpret_cast<serbf_state *>(s_words);
-    if (threadIdx.x < 32) {
-        epoch_tail(a, st, bf, sc[0], sc[1], threadIdx.x);
-        if (threadIdx.x == 0) a.counter[1] = 0u;
-    }
-    __syncthreads();
-    uint32_t *gwo = reinterpret_cast<uint32_t *>(a.st);
-    for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) gwo[k] = s_words[k];
+    finish_step(a, (double)tot[0].hi + tot[0].lo, sc, s_words);
+    if (threadIdx.x == 0) a.counter[1] = 0u;
 }
 
 // Eq. 3-27: stable compaction of the kernels with |w| >= tau_d.
