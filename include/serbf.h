@@ -265,6 +265,45 @@ int serbf_build_neighbors(const serbf_points *pts, const serbf_params *prm, cons
 int serbf_init_kernels(const serbf_points *pts, const float *S_raw, double gamma, serbf_params *prm, int32_t *m_out,
                        serbf_workspace *ws, void *stream);
 
+/* ------------------------------------------------------------------ evaluation (Sec. 4) */
+/* Zero level set of a grid field f (dims[0] x dims[1] x dims[2] values, x
+ * fastest; vertex (i, j, k) at origin + h (i, j, k)) as a triangle soup: each
+ * grid cube is split into six tetrahedra {0, a, a + b, 7} (corner bits x = 1,
+ * y = 2, z = 4; (a, b) = (1,2) (1,4) (2,1) (2,4) (4,1) (4,2)), inside means
+ * f < iso, one or three inside vertices give one triangle, two give two; edge
+ * points interpolate linearly from the edge's lower grid index in float with
+ * a fixed operation order.  Marching tetrahedra stand in for the paper's
+ * marching cubes.  tri: cap x 9 floats (device, caller-owned); *ntri (host)
+ * receives the count; scratch: (cubes + 1) int64 (device).  Triangles are in
+ * cube order.  SYNCHRONISES; ECAPACITY (with *ntri set) when cap is too small. */
+int serbf_marching_tets(const float *f, const int32_t dims[3], const float origin[3], float h, float iso, float *tri,
+                        int64_t cap, int64_t *ntri, int64_t *scratch, void *stream);
+
+/* Area-weighted samples on a triangle soup (Sec. 4 samples 1e5 points per
+ * surface): sample s takes the triangle whose cumulative area interval holds
+ * floor(u[3s] * total) (areas quantised to 2^-40 so the sums are exact), then
+ * the point (1 - r) a + r (1 - u[3s+2]) b + r u[3s+2] c, r = sqrt(u[3s+1]), and
+ * the triangle's unit normal.  u: ns x 3 uniform numbers in [0, 1) (device,
+ * drawn by the caller); pts, nrm: ns x 3 floats; scratch: ntri + 1 int64.
+ * SYNCHRONISES; EINVAL when the soup has no area. */
+int serbf_sample_surface(const float *tri, int64_t ntri, const double *u, int64_t ns, float *pts, float *nrm,
+                         int64_t *scratch, void *stream);
+
+/* Sec. 4 metrics between two sampled surfaces (point-to-point, nearest
+ * point by brute force, ties to the lowest index): out (host) = {HD, CD, CS}
+ * with HD = max(max_a d(a, B), max_b d(b, A)), CD = mean_a d(a, B) / 2 +
+ * mean_b d(b, A) / 2, CS = the same means of |n . n_nearest|.  scratch:
+ * 2 (na + nb) + 6 doubles (device).  SYNCHRONISES. */
+int serbf_surface_metrics(const float *A, const float *nA, int64_t na, const float *B, const float *nB, int64_t nb,
+                          double out[3], double *scratch, void *stream);
+
+/* Inverse of Eq. 3-10 on the branch S >= m: S = m + sqrt(-ln(t / 2) / h), with
+ * (m, h) as written by serbf_normalize_sdf; t >= 2 gives m, t <= 0 gives +inf. */
+int serbf_denormalize_sdf(const float *t, float *S, int64_t n, const double *mh_dev, void *stream);
+
+/* dst[idx[i]] = src[i] (e.g. binned results back to grid order with perm). */
+int serbf_scatter(const float *src, const uint32_t *idx, float *dst, int64_t n, void *stream);
+
 /* ------------------------------------------------------------------ a4 */
 /* Eq. 3-26 forward over the pairs of Eq. 3-15-1, Eq. 3-18 filter and the
  * Eq. 3-19 loss terms: psi[i], mask[i] (1 = in id_all), err[i] = psi - t on

@@ -80,6 +80,12 @@ def lib():
                                        C.c_float, i32p]
         L.oracle_new_kernel.argtypes = [C.c_float, C.c_float, C.c_float, C.c_float, C.c_double,
                                         C.c_double, f64p]
+        L.oracle_marching_tets.restype = C.c_int64
+        L.oracle_marching_tets.argtypes = [f32p, C.c_int, C.c_int, C.c_int, f32p, C.c_float, C.c_float, f32p,
+                                           C.c_int64]
+        L.oracle_sample_surface.restype = C.c_int
+        L.oracle_sample_surface.argtypes = [f32p, C.c_int64, f64p, C.c_int64, f32p, f32p]
+        L.oracle_surface_metrics.argtypes = [f32p, f32p, C.c_int64, f32p, f32p, C.c_int64, f64p]
         L.oracle_inscribed.restype = C.c_int32
         L.oracle_inscribed.argtypes = [f32p, f32p, f32p, f32p, f32p, C.c_int64, i32p, C.c_int32]
         L.oracle_init_shape.argtypes = [f64p, f64p, f64p, f64p, f64p, C.c_int32, C.c_double, f64p]
@@ -272,3 +278,35 @@ def init_shape(c, w, r, gamma=1e-3):
     lib().oracle_init_shape(np.ascontiguousarray(c[:, 0]), np.ascontiguousarray(c[:, 1]),
                             np.ascontiguousarray(c[:, 2]), w, r, len(w), gamma, d)
     return d[:len(w)]
+
+
+def marching_tets(f, shape, origin, h, iso=0.0):
+    """Zero level set (value < iso inside) of a grid field f (x fastest), shape
+    (nx, ny, nz): triangles as an (ntri, 9) float32 array."""
+    f = _f32(f)
+    nx, ny, nz = shape
+    o = np.asarray(origin, np.float32)
+    n = lib().oracle_marching_tets(f, nx, ny, nz, o, h, iso, np.zeros(9, np.float32), 0)
+    tri = np.zeros((max(n, 1), 9), np.float32)
+    lib().oracle_marching_tets(f, nx, ny, nz, o, h, iso, tri, n)
+    return tri[:n]
+
+
+def sample_surface(tri, u):
+    """Area-weighted samples; u: (ns, 3) uniform numbers in [0, 1)."""
+    tri = _f32(tri)
+    u = np.ascontiguousarray(u, np.float64)
+    ns = u.shape[0]
+    pts = np.zeros((ns, 3), np.float32)
+    nrm = np.zeros((ns, 3), np.float32)
+    rc = lib().oracle_sample_surface(tri, tri.shape[0], u, ns, pts, nrm)
+    if rc:
+        raise ValueError("surface has no area")
+    return pts, nrm
+
+
+def surface_metrics(A, nA, B, nB):
+    """(HD, CD, CS) of two sampled surfaces (Sec. 4)."""
+    out = np.zeros(3)
+    lib().oracle_surface_metrics(_f32(A), _f32(nA), A.shape[0], _f32(B), _f32(nB), B.shape[0], out)
+    return tuple(out)

@@ -673,3 +673,183 @@ void oracle_init_shape(const double *cx, const double *cy, const double *cz, con
         d[j] = 2.0 * sqrt(-log(gamma / (w[j] * w[j]))) / best;
     }
 }
+
+/* ---------------------------------------------------------------------------
+ * Surface extraction and the Sec. 4 surface metrics (the paper extracts the
+ * zero level set with marching cubes; this project extracts it with marching
+ * tetrahedra, six per grid cube, which needs no case table).
+ *
+ * Grid: nx*ny*nz values, x fastest; vertex (i, j, k) at o + h (i, j, k).
+ * Cube corners are numbered bit0 = x, bit1 = y, bit2 = z; the six
+ * tetrahedra of a cube are {0, a, a + b, 7} for the axis orders (a, b) =
+ * (1,2) (1,4) (2,1) (2,4) (4,1) (4,2).  Inside means value < iso.  One or
+ * three inside vertices give one triangle on the three edges of the lone
+ * vertex; two give the quad on the four crossing edges as two triangles.
+ * An edge point interpolates linearly from the edge's lower grid index to
+ * its higher one, in float with a fixed operation order (so a shared edge
+ * gives the same point in every tetrahedron).  Output in cube order, then
+ * tetrahedron order. */
+static const int MT_TETS[6][4] = {{0, 1, 3, 7}, {0, 1, 5, 7}, {0, 2, 3, 7}, {0, 2, 6, 7}, {0, 4, 5, 7}, {0, 4, 6, 7}};
+
+static void mt_edge(const float *f, int64_t gu, int64_t gw, int nx, int ny, const float o[3], float h, float iso,
+                    float *out) {
+    if (gu > gw) {
+        int64_t t = gu;
+        gu = gw;
+        gw = t;
+    }
+    const float fu = f[gu], fw = f[gw];
+    const float t = (iso - fu) / (fw - fu);
+    const int64_t iu[3] = {gu % nx, (gu / nx) % ny, gu / ((int64_t)nx * ny)};
+    const int64_t iw[3] = {gw % nx, (gw / nx) % ny, gw / ((int64_t)nx * ny)};
+    for (int a = 0; a < 3; ++a) {
+        const float pu = o[a] + h * (float)iu[a], pw = o[a] + h * (float)iw[a];
+        out[a] = pu + t * (pw - pu);
+    }
+}
+
+/* Writes up to cap triangles (9 floats each); returns the number found. */
+int64_t oracle_marching_tets(const float *f, int nx, int ny, int nz, const float o[3], float h, float iso, float *tri,
+                             int64_t cap) {
+    int64_t cnt = 0;
+    for (int k = 0; k + 1 < nz; ++k)
+        for (int j = 0; j + 1 < ny; ++j)
+            for (int i = 0; i + 1 < nx; ++i) {
+                int64_t g[8];
+                for (int c = 0; c < 8; ++c)
+                    g[c] = ((int64_t)(k + ((c >> 2) & 1)) * ny + (j + ((c >> 1) & 1))) * nx + (i + (c & 1));
+                for (int q = 0; q < 6; ++q) {
+                    int64_t v[4];
+                    int in[4], nin = 0;
+                    for (int a = 0; a < 4; ++a) {
+                        v[a] = g[MT_TETS[q][a]];
+                        in[a] = f[v[a]] < iso;
+                        nin += in[a];
+                    }
+                    if (nin == 0 || nin == 4) continue;
+                    float p[4][3];
+                    if (nin == 1 || nin == 3) {
+                        const int want = nin == 1;
+                        int l = 0;
+                        while (in[l] != want) ++l;
+                        int e = 0;
+                        for (int a = 0; a < 4; ++a)
+                            if (a != l) mt_edge(f, v[l], v[a], nx, ny, o, h, iso, p[e++]);
+                        if (cnt < cap) memcpy(tri + 9 * cnt, p, 9 * sizeof(float));
+                        ++cnt;
+                    } else {
+                        int A = -1, B = -1, Cc = -1, D = -1;
+                        for (int a = 0; a < 4; ++a) {
+                            if (in[a]) {
+                                if (A < 0) A = a; else B = a;
+                            } else {
+                                if (Cc < 0) Cc = a; else D = a;
+                            }
+                        }
+                        float ac[3], ad[3], bd[3], bc[3];
+                        mt_edge(f, v[A], v[Cc], nx, ny, o, h, iso, ac);
+                        mt_edge(f, v[A], v[D], nx, ny, o, h, iso, ad);
+                        mt_edge(f, v[B], v[D], nx, ny, o, h, iso, bd);
+                        mt_edge(f, v[B], v[Cc], nx, ny, o, h, iso, bc);
+                        if (cnt < cap) {
+                            float *t0 = tri + 9 * cnt;
+                            memcpy(t0, ac, 12); memcpy(t0 + 3, ad, 12); memcpy(t0 + 6, bd, 12);
+                        }
+                        ++cnt;
+                        if (cnt < cap) {
+                            float *t1 = tri + 9 * cnt;
+                            memcpy(t1, ac, 12); memcpy(t1 + 3, bd, 12); memcpy(t1 + 6, bc, 12);
+                        }
+                        ++cnt;
+                    }
+                }
+            }
+    return cnt;
+}
+
+/* Triangle area quantised to a 64-bit integer (unit 2^-40): exact prefix
+ * sums, so the sampling below picks the same triangle in any order of
+ * summation.  Area in float: 0.5 |(b - a) x (c - a)|. */
+static uint64_t mt_area_q(const float *t) {
+    const float ux = t[3] - t[0], uy = t[4] - t[1], uz = t[5] - t[2];
+    const float vx = t[6] - t[0], vy = t[7] - t[1], vz = t[8] - t[2];
+    const float cx = uy * vz - uz * vy, cy = uz * vx - ux * vz, cz = ux * vy - uy * vx;
+    const float a = 0.5f * sqrtf((cx * cx + cy * cy) + cz * cz);
+    return (uint64_t)llrint((double)a * 1099511627776.0);
+}
+
+/* Area-weighted uniform samples on a triangle soup: sample s picks the
+ * triangle whose quantised cumulative area interval holds floor(u[3s] *
+ * total), then the point (1 - r) a + r (1 - u[3s+2]) b + r u[3s+2] c with
+ * r = sqrt(u[3s+1]), and the unit normal of the triangle.  u: uniform
+ * numbers in [0, 1) (drawn by the caller).  Returns 0, or -1 when the soup
+ * has no area. */
+int oracle_sample_surface(const float *tri, int64_t ntri, const double *u, int64_t ns, float *pts, float *nrm) {
+    uint64_t *cum = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(ntri + 1));
+    cum[0] = 0;
+    for (int64_t k = 0; k < ntri; ++k) cum[k + 1] = cum[k] + mt_area_q(tri + 9 * k);
+    const uint64_t total = cum[ntri];
+    if (total == 0) {
+        free(cum);
+        return -1;
+    }
+    for (int64_t s = 0; s < ns; ++s) {
+        const uint64_t target = (uint64_t)(u[3 * s] * (double)total);
+        int64_t lo = 0, hi = ntri;  /* the k with cum[k] <= target < cum[k+1] */
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) / 2;
+            if (cum[mid] <= target) lo = mid; else hi = mid;
+        }
+        const float *t = tri + 9 * lo;
+        const float r = sqrtf((float)u[3 * s + 1]), w = (float)u[3 * s + 2];
+        const float ca = 1.0f - r, cb = r * (1.0f - w), cc = r * w;
+        for (int a = 0; a < 3; ++a) pts[3 * s + a] = (ca * t[a] + cb * t[3 + a]) + cc * t[6 + a];
+        const float ux = t[3] - t[0], uy = t[4] - t[1], uz = t[5] - t[2];
+        const float vx = t[6] - t[0], vy = t[7] - t[1], vz = t[8] - t[2];
+        const float cx = uy * vz - uz * vy, cy = uz * vx - ux * vz, cz = ux * vy - uy * vx;
+        const float len = sqrtf((cx * cx + cy * cy) + cz * cz);
+        nrm[3 * s] = cx / len;
+        nrm[3 * s + 1] = cy / len;
+        nrm[3 * s + 2] = cz / len;
+    }
+    free(cum);
+    return 0;
+}
+
+/* Sec. 4 metrics between two sampled surfaces A and B (point-to-point):
+ * HD = max(max_a d(a, B), max_b d(b, A)); CD = mean_a d(a, B) / 2 +
+ * mean_b d(b, A) / 2; CS = the same averages of |n(x) . n(closest(x))|.
+ * Nearest point by brute force on float squared distances (ties: lowest
+ * index); distances and sums in double.  out = {HD, CD, CS}. */
+void oracle_surface_metrics(const float *A, const float *nA, int64_t na, const float *B, const float *nB, int64_t nb,
+                            double out[3]) {
+    double hd = 0.0, cd = 0.0, cs = 0.0;
+    for (int dir = 0; dir < 2; ++dir) {
+        const float *P = dir ? B : A, *nP = dir ? nB : nA, *Q = dir ? A : B, *nQ = dir ? nA : nB;
+        const int64_t np = dir ? nb : na, nq = dir ? na : nb;
+        double dsum = 0.0, csum = 0.0;
+        #pragma omp parallel for reduction(+ : dsum, csum) reduction(max : hd)
+        for (int64_t i = 0; i < np; ++i) {
+            float best = INFINITY;
+            int64_t bi = 0;
+            for (int64_t j = 0; j < nq; ++j) {
+                const float dx = P[3 * i] - Q[3 * j], dy = P[3 * i + 1] - Q[3 * j + 1], dz = P[3 * i + 2] - Q[3 * j + 2];
+                const float d2 = (dx * dx + dy * dy) + dz * dz;
+                if (d2 < best) {
+                    best = d2;
+                    bi = j;
+                }
+            }
+            const double d = sqrt((double)best);
+            dsum += d;
+            if (d > hd) hd = d;
+            csum += fabs((double)nP[3 * i] * nQ[3 * bi] + (double)nP[3 * i + 1] * nQ[3 * bi + 1] +
+                         (double)nP[3 * i + 2] * nQ[3 * bi + 2]);
+        }
+        cd += dsum / (2.0 * (double)np);
+        cs += csum / (2.0 * (double)np);
+    }
+    out[0] = hd;
+    out[1] = cd;
+    out[2] = cs;
+}

@@ -119,6 +119,14 @@ int32_t oracle_local_max(const float *x, const float *y, const float *z, const f
                          int32_t *out);
 void oracle_new_kernel(float px, float py, float pz, float e, double dbar, double eps, double out[10]);
 
+/* Surface extraction (marching tetrahedra), area-weighted sampling and the
+ * Sec. 4 metrics HD, CD, CS. */
+int64_t oracle_marching_tets(const float *f, int nx, int ny, int nz, const float o[3], float h, float iso, float *tri,
+                             int64_t cap);
+int oracle_sample_surface(const float *tri, int64_t ntri, const double *u, int64_t ns, float *pts, float *nrm);
+void oracle_surface_metrics(const float *A, const float *nA, int64_t na, const float *B, const float *nB, int64_t nb,
+                            double out[3]);
+
 /* Algorithm 1 (greedy inscribed spheres) and Eq. 3-12 (isotropic shapes). */
 int32_t oracle_inscribed(const float *x, const float *y, const float *z, const float *t, const float *S,
                          int64_t n, int32_t *out, int32_t max_out);

@@ -88,6 +88,12 @@ _SIGS = {
                                         C.POINTER(Csr), C.POINTER(Csr), C.POINTER(C.c_int64), VP, VP]),
     "serbf_init_kernels": (C.c_int, [C.POINTER(Points), VP, C.c_double, C.POINTER(Params), C.POINTER(C.c_int32), VP,
                                      VP]),
+    "serbf_marching_tets": (C.c_int, [VP, C.POINTER(C.c_int32 * 3), C.POINTER(C.c_float * 3), C.c_float, C.c_float,
+                                      VP, C.c_int64, C.POINTER(C.c_int64), VP, VP]),
+    "serbf_sample_surface": (C.c_int, [VP, C.c_int64, VP, C.c_int64, VP, VP, VP, VP]),
+    "serbf_surface_metrics": (C.c_int, [VP, VP, C.c_int64, VP, VP, C.c_int64, C.POINTER(C.c_double * 3), VP, VP]),
+    "serbf_denormalize_sdf": (C.c_int, [VP, VP, C.c_int64, VP, VP]),
+    "serbf_scatter": (C.c_int, [VP, VP, VP, C.c_int64, VP]),
     "serbf_forward": (C.c_int, [C.POINTER(Points), C.POINTER(Params), C.POINTER(Config), VP, VP, VP, VP,
                                 VP, VP]),
     "serbf_forward_backward": (C.c_int, [C.POINTER(Points), C.POINTER(Params), C.POINTER(Config), VP, VP, VP, VP,
@@ -230,6 +236,35 @@ def serbf_init_kernels(pts, S_raw, gamma, prm, ws_host, stream=None):
                                  C.addressof(ws_host), _stream(stream))
     _check("serbf_init_kernels", rc, ok=(SERBF_OK, SERBF_ECAPACITY))
     return rc, mo.value
+
+
+def serbf_marching_tets(f, dims, origin, h, iso, tri, ntri_cap, scratch, stream=None):
+    """Returns (status, triangle count); tri may be None with ntri_cap 0 to count."""
+    n = C.c_int64(0)
+    rc = _lib.serbf_marching_tets(_p(f), C.byref((C.c_int32 * 3)(*dims)), C.byref((C.c_float * 3)(*origin)), h, iso,
+                                  _p(tri), ntri_cap, C.byref(n), _p(scratch), _stream(stream))
+    _check("serbf_marching_tets", rc, ok=(SERBF_OK, SERBF_ECAPACITY))
+    return rc, n.value
+
+
+def serbf_sample_surface(tri, ntri, u, ns, pts, nrm, scratch, stream=None):
+    return _check("serbf_sample_surface", _lib.serbf_sample_surface(_p(tri), ntri, _p(u), ns, _p(pts), _p(nrm),
+                                                                    _p(scratch), _stream(stream)))
+
+
+def serbf_surface_metrics(A, nA, na, B, nB, nb, scratch, stream=None):
+    out = (C.c_double * 3)()
+    _check("serbf_surface_metrics", _lib.serbf_surface_metrics(_p(A), _p(nA), na, _p(B), _p(nB), nb, C.byref(out),
+                                                               _p(scratch), _stream(stream)))
+    return tuple(out)
+
+
+def serbf_denormalize_sdf(t, S, n, mh, stream=None):
+    return _check("serbf_denormalize_sdf", _lib.serbf_denormalize_sdf(_p(t), _p(S), n, _p(mh), _stream(stream)))
+
+
+def serbf_scatter(src, idx, dst, n, stream=None):
+    return _check("serbf_scatter", _lib.serbf_scatter(_p(src), _p(idx), _p(dst), n, _stream(stream)))
 
 
 def serbf_forward(pts, prm, cfg, psi, err, mask, stats, ws_host, stream=None):

@@ -27,6 +27,21 @@ def grid_for(spacing, lo=-1.0, hi=1.0, points_per_cell=4):
     return g
 
 
+def normalize_layers(S_layers, device="cuda", mh_out=None):
+    """Eq. 3-10 targets of several grid layers from one map (m and h over all
+    of them, as the hierarchical training needs).  Returns float32 numpy
+    arrays, one per layer; mh_out (a 2-double device tensor) receives (m, h)."""
+    sizes = [len(S) for S in S_layers]
+    S = torch.as_tensor(np.concatenate([np.asarray(v, np.float32) for v in S_layers]), device=device)
+    t = torch.zeros_like(S)
+    mh = torch.zeros(2, dtype=torch.float64, device=device)
+    N.serbf_normalize_sdf_noalloc(S, t, mh)
+    if mh_out is not None:
+        mh_out.copy_(mh)
+    t = t.cpu().numpy()
+    return list(np.split(t, np.cumsum(sizes)[:-1]))
+
+
 class Problem:
     """One field: training points, targets, kernels, optimiser state and scratch."""
 
@@ -353,3 +368,44 @@ class MiniBatch:
             pb.build_neighbors()
             pb.forward()
             pb.add()
+
+
+def surface_metrics(problem, sdf, n=129, samples=100000, seed=0, mh=None):
+    """Sec. 4 evaluation of a fit against a closed-form SDF: the fitted field
+    on an n^3 vertex grid over [-1, 1]^3 mapped back to distances (inverse of
+    Eq. 3-10 with the training map (m, h)), the zero level sets of it and of
+    the true SDF on the same grid (marching tetrahedra), `samples` area-
+    weighted points on each, and (HD, CD, CS).  sdf maps float64 arrays
+    (x, y, z) to distances."""
+    import synth
+    dev = problem.dev
+    mh = problem.mh if mh is None else mh
+    x, y, z = synth.grid(n)
+    S_true = np.asarray(sdf(x.astype(np.float64), y.astype(np.float64), z.astype(np.float64)), np.float32)
+    m = problem.m()
+    ev = Problem(x, y, z, S_true, problem.p[:, :m].cpu().numpy(), m, synth.spacing(n), cap=max(m, 1), device=dev)
+    ev.build_neighbors()
+    ev.forward()
+    N_ = ev.n
+    psi = torch.zeros(N_, dtype=torch.float32, device=dev)
+    N.serbf_scatter(ev.psi[:N_], ev.perm[:N_], psi, N_)
+    S_pred = torch.zeros_like(psi)
+    N.serbf_denormalize_sdf(psi, S_pred, N_, mh)
+    ev.close()
+    out = []
+    rng = np.random.default_rng(seed)
+    dims, origin, h = (n, n, n), (-1.0, -1.0, -1.0), float(synth.spacing(n))
+    scratch = torch.zeros((n - 1) ** 3 + 1, dtype=torch.int64, device=dev)
+    for field_ in (torch.as_tensor(S_true, device=dev), S_pred):
+        _rc, nt = N.serbf_marching_tets(field_, dims, origin, h, 0.0, None, 0, scratch)
+        tri = torch.zeros(max(nt, 1), 9, dtype=torch.float32, device=dev)
+        N.serbf_marching_tets(field_, dims, origin, h, 0.0, tri, nt, scratch)
+        u = torch.as_tensor(rng.uniform(size=(samples, 3)), device=dev)
+        pts = torch.zeros(samples, 3, dtype=torch.float32, device=dev)
+        nrm = torch.zeros_like(pts)
+        cum = torch.zeros(nt + 1, dtype=torch.int64, device=dev)
+        N.serbf_sample_surface(tri, nt, u, samples, pts, nrm, cum)
+        out.append((pts, nrm))
+    scr = torch.zeros(4 * samples + 6, dtype=torch.float64, device=dev)
+    (A, nA), (B, nB) = out
+    return N.serbf_surface_metrics(A, nA, samples, B, nB, samples, scr)

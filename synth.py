@@ -203,3 +203,44 @@ def batch_workload(count=64, seed=500, device=None):
         P = init_kernels(seed + 2000 + k, m, length_range=(0.05 * scale, 0.2 * scale), rotate=True)
         out.append(dict(x=x, y=y, z=z, S=S, P=P, m=m, spacing=spacing(n), n=n, prims=nprim))
     return out
+
+
+def octree_layers(sdf, l_min, l_max, lo=-1.0, hi=1.0):
+    """Grid points of an adaptive octree over [lo, hi]^3 (Sec. 3.4.2's
+    hierarchical grids), layer by layer.
+
+    Level l has cells of edge (hi - lo) / 2^l.  Every cell of level l_min is
+    kept; a kept cell of level l is split into its 8 children when the
+    surface may cross it: |sdf(centre)| <= half its diagonal (exact for a
+    true distance function).  Layer l holds the corners of the kept cells of
+    level l that are not corners of a coarser layer.  `sdf` maps float64
+    arrays (x, y, z) to distances.  Returns a list of (x, y, z, S, spacing)
+    with float32 coordinates and S, from l_min to l_max."""
+    layers = []
+    seen = set()
+    res = 2 ** l_max  # integer coordinates on the finest lattice
+    cells = np.stack(np.meshgrid(*[np.arange(2 ** l_min)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    for l in range(l_min, l_max + 1):
+        step = res // (2 ** l)
+        edge = (hi - lo) / 2 ** l
+        corners = (cells[:, None, :] + np.array([[i, j, k] for i in (0, 1) for j in (0, 1) for k in (0, 1)])[None])
+        corners = np.unique(corners.reshape(-1, 3) * step, axis=0)
+        key = (corners[:, 0] * (res + 1) + corners[:, 1]) * (res + 1) + corners[:, 2]
+        new = np.array([k not in seen for k in key.tolist()], bool)
+        seen.update(key[new].tolist())
+        pts = corners[new]
+        # z slowest, x fastest, as the vertex grids
+        order = np.lexsort((pts[:, 0], pts[:, 1], pts[:, 2]))
+        pts = pts[order]
+        xyz = lo + (hi - lo) * pts.astype(np.float64) / res
+        S = np.asarray(sdf(xyz[:, 0], xyz[:, 1], xyz[:, 2]), np.float64)
+        layers.append((xyz[:, 0].astype(np.float32), xyz[:, 1].astype(np.float32), xyz[:, 2].astype(np.float32),
+                       S.astype(np.float32), edge))
+        if l == l_max:
+            break
+        centre = lo + edge * (cells.astype(np.float64) + 0.5)
+        near = np.abs(np.asarray(sdf(centre[:, 0], centre[:, 1], centre[:, 2]), np.float64)) <= 0.5 * math.sqrt(3) * edge
+        kids = cells[near]
+        cells = (2 * kids[:, None, :] + np.array([[i, j, k] for i in (0, 1) for j in (0, 1) for k in (0, 1)])[None]
+                 ).reshape(-1, 3)
+    return layers

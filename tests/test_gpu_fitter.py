@@ -74,3 +74,29 @@ def test_sphere_fit_tracks_oracle(orc):
     assert 1 / 3 < ratio < 3.0, (msq_gpu[-40:].min(), ref[-40:].min())
     # before the gates fire the two runs agree closely (FP32 vs FP64 drift)
     np.testing.assert_allclose(msq_gpu[:40], ref[:40], rtol=1e-4)
+
+
+def test_octree_layers_fit():
+    """Sec. 3.4.2 on an adaptive octree: initial kernels from the coarsest layer
+    (Algorithm 1), finer layers appended at fixed epochs."""
+    torch = torch_cuda()
+    from paper_2505_02350_gb300 import build, field
+    from paper_2505_02350_gb300.fitter import Fitter
+    build.build()
+    sphere = lambda x, y, z: np.sqrt(x * x + y * y + z * z) - 0.5
+    layers = synth.octree_layers(sphere, 4, 6)
+    ts = field.normalize_layers([l[3] for l in layers])
+    total = sum(l[0].size for l in layers)
+    finest = layers[-1][4]
+    g = field.grid_for(finest)
+    x, y, z, S, _ = layers[0]
+    pb = field.Problem(x, y, z, S, np.zeros((10, 2048), np.float32), 0, finest, max_points=total, t=ts[0],
+                       cap=2048, max_cells=g.n[0] * g.n[1] * g.n[2])
+    found = pb.init_kernels()
+    assert 0 < found <= 2048
+    more = [(l[0], l[1], l[2], l[3], t, finest) for l, t in zip(layers[1:], ts[1:])]
+    fit = Fitter(pb, layers=more, refine_at=[10, 20])
+    hist = fit.run(40, log_every=1)
+    assert pb.n == total
+    msq = [h["l2"] / max(h["count"], 1) for h in hist]
+    assert np.isfinite(msq).all() and min(msq[-5:]) < msq[0]

@@ -578,3 +578,74 @@ def test_init_shape_satisfies_eq3_11(orc):
         assert w[j] ** 2 * np.exp(-d[j] ** 2 * (dhat / 2) ** 2) == pytest.approx(gamma, rel=1e-12)
     d1 = orc.init_shape(c[:1], w[:1], r[:1], gamma)
     assert w[0] ** 2 * np.exp(-d1[0] ** 2 * r[0] ** 2) == pytest.approx(gamma, rel=1e-12)  # dhat = 2 r
+
+
+# ---------------------------------------------------------------- Sec. 3.4.2 octree layers (input generator)
+def test_octree_layers_structure():
+    sphere = lambda x, y, z: np.sqrt(x * x + y * y + z * z) - 0.5
+    L = synth.octree_layers(sphere, 3, 6)
+    assert L[0][0].size == 9 ** 3  # every cell of the first level is kept
+    keys = set()
+    for l, (x, y, z, S, edge) in enumerate(L, start=3):
+        assert edge == 2.0 / 2 ** l
+        ijk = np.stack([x, y, z], 1).astype(np.float64)
+        lat = (ijk + 1.0) / edge
+        assert np.allclose(lat, np.round(lat), atol=1e-4)  # on the level-l lattice
+        k = set(map(tuple, np.round((ijk + 1.0) * 2 ** 6 / 2).astype(int).tolist()))
+        assert not (k & keys) and len(k) == x.size  # no point repeats a coarser one
+        keys |= k
+        np.testing.assert_allclose(S, sphere(x.astype(np.float64), y.astype(np.float64), z.astype(np.float64)),
+                                   atol=1e-6)
+        if l > 3:
+            # corners of children of cells the surface may cross
+            assert np.abs(S).max() <= 1.5 * np.sqrt(3) * 2 * edge + 1e-6
+    # every finest-lattice point close to the surface is present
+    x, y, z = synth.grid(2 ** 6 + 1)
+    close = np.abs(sphere(x.astype(np.float64), y.astype(np.float64), z.astype(np.float64))) < 0.5 * 2.0 / 2 ** 6
+    want = set(map(tuple, np.round((np.stack([x, y, z], 1)[close] + 1.0) * 2 ** 6 / 2).astype(int).tolist()))
+    assert want <= keys
+
+
+# ---------------------------------------------------------------- surface extraction and Sec. 4 metrics
+def _vertex_grid_field(n, fn):
+    x, y, z = synth.grid(n)
+    return fn(x.astype(np.float64), y.astype(np.float64), z.astype(np.float64)).astype(np.float32)
+
+
+def _areas(tri):
+    t = tri.astype(np.float64).reshape(-1, 3, 3)
+    return 0.5 * np.linalg.norm(np.cross(t[:, 1] - t[:, 0], t[:, 2] - t[:, 0]), axis=1)
+
+
+def test_marching_tets_plane_is_exact(orc):
+    n = 9
+    f = _vertex_grid_field(n, lambda x, y, z: z - 0.3)
+    tri = orc.marching_tets(f, (n, n, n), (-1, -1, -1), 2.0 / (n - 1))
+    assert np.allclose(tri.reshape(-1, 3)[:, 2], 0.3, atol=1e-6)
+    assert _areas(tri).sum() == pytest.approx(4.0, rel=1e-6)  # the [-1, 1]^2 cross-section
+
+
+def test_marching_tets_sphere_area_converges(orc):
+    errs = []
+    for n in (17, 33, 65):
+        f = _vertex_grid_field(n, lambda x, y, z: np.sqrt(x * x + y * y + z * z) - 0.5)
+        tri = orc.marching_tets(f, (n, n, n), (-1, -1, -1), 2.0 / (n - 1))
+        v = tri.reshape(-1, 3).astype(np.float64)
+        assert np.abs(np.linalg.norm(v, axis=1) - 0.5).max() < 2.0 / (n - 1)  # vertices near the sphere
+        errs.append(abs(_areas(tri).sum() / (4 * np.pi * 0.25) - 1))
+    assert errs[2] < errs[1] < errs[0] and errs[2] < 0.01
+
+
+def test_surface_samples_and_metrics_closed_forms(orc):
+    n = 9
+    tri = orc.marching_tets(_vertex_grid_field(n, lambda x, y, z: z - 0.3), (n, n, n), (-1, -1, -1), 2.0 / (n - 1))
+    u = np.random.default_rng(4).uniform(size=(4000, 3))
+    A, nA = orc.sample_surface(tri, u)
+    assert np.allclose(A[:, 2], 0.3, atol=1e-6) and np.allclose(np.abs(nA[:, 2]), 1.0)
+    assert abs(A[:, 0].mean()) < 0.05 and A[:, 0].var() == pytest.approx(1 / 3, rel=0.05)  # uniform on the square
+    hd, cd, cs = orc.surface_metrics(A, nA, A, nA)
+    assert (hd, cd, cs) == (0.0, 0.0, 1.0)
+    B = A.copy()
+    B[:, 2] += np.float32(0.125)  # translated along the normal: every nearest point is the copy
+    hd, cd, cs = orc.surface_metrics(A, nA, B, nA)
+    assert hd == pytest.approx(0.125, rel=1e-6) and cd == pytest.approx(0.125, rel=1e-6) and cs == 1.0
