@@ -31,7 +31,7 @@ METRIC = "ERBF fwd+bwd point-kernel pairs/s"
 UNIT = "pairs/s"
 FWD_INSTR_PER_PAIR = 17  # minimum FP32-pipe instructions of one forward pair
 ADJ_INSTR_PER_PAIR = 32  # minimum FP32-pipe instructions of one adjoint pair (recompute + ten moments)
-# order (side stream), prep, super lists | forward+adjoint, epilogue | 2 step, prune, 3 addition
+# class count + order (side stream), rebuild | forward+adjoint, epilogue | 2 step, prune, 3 addition
 LAUNCHES_PER_STEP = 11
 WORKLOADS = {
     "c1": ("sphere |x|-0.5 on 32^3, M=64 isotropic", None),

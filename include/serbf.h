@@ -88,7 +88,7 @@ typedef struct {
     int32_t k_l1, k_l2; /* window lengths (50, 10) */
     int32_t T_e, M_e;  /* phase switch and last epoch (1600, 2000) */
     int32_t kahan;     /* 1: compensated per-kernel sums in the adjoint */
-    int32_t fwd_warps; /* warps sharing one forward work item: 1, 2 or 4;
+    int32_t fwd_warps; /* warps sharing one forward work item: 1, 2, 4 or 8;
                           0 = chosen from the problem size (default) */
     int32_t epoch_steps; /* optimiser steps per epoch: 1 = full batch (default);
                             n > 1: mini-batches, the epoch tail runs every n-th step

@@ -412,5 +412,4 @@ __device__ __forceinline__ KBox kernel_box(float cx, float cy, float cz, float r
 namespace serbf {
 int launch_exscan_u32(uint32_t *a, int64_t n, cudaStream_t s);  // in place, a[n] = total
 int launch_exscan_i64(int64_t *a, int64_t n, cudaStream_t s);   // in place, a[n] = total
-int launch_prep(const serbf_params *prm, const serbf_config *cfg, serbf_workspace *ws, cudaStream_t s);
 }  // namespace serbf

@@ -638,7 +638,7 @@ __device__ __forceinline__ void sched_finish(const FwdArgs &a) {
 // depend on timing.  G = 1 when there are enough items to balance the warps,
 // 2 or 4 for small problems.
 template <int G, bool ADJ>
-__global__ void __launch_bounds__(G * 32, (ADJ ? 20 : 24) / G) k_forward(FwdArgs a) {
+__global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? 20 : 24)) / G) k_forward(FwdArgs a) {
     pdl_wait();
     pdl_trigger();
     // two rings per warp (kernels partly / fully covering the item box); a
@@ -859,7 +859,8 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
     if (pts->n > 0 && (!pts->x || !pts->y || !pts->z || !pts->t || !psi || !err || !mask)) return SERBF_EINVAL;
     if (!stats) return SERBF_EINVAL;
     const bool adj = grad != nullptr;
-    if (cfg->fwd_warps != 0 && cfg->fwd_warps != 1 && cfg->fwd_warps != 2 && cfg->fwd_warps != 4) return SERBF_EINVAL;
+    if (cfg->fwd_warps != 0 && cfg->fwd_warps != 1 && cfg->fwd_warps != 2 && cfg->fwd_warps != 4 && cfg->fwd_warps != 8)
+        return SERBF_EINVAL;
     if (adj && (prm->cap < 1 || prm->cap > ws->sz.max_kernels)) return SERBF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     FwdArgs a;
@@ -915,15 +916,18 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
         // group of warps for the heavy-first balancing
         const int64_t ni = ws->nitems;
         int G = ni >= 4 * forward_groups<1>(ws->sm_count) ? 1 : (ni >= 4 * forward_groups<2>(ws->sm_count) ? 2 : 4);
-        if (cfg->fwd_warps == 1 || cfg->fwd_warps == 2 || cfg->fwd_warps == 4) G = cfg->fwd_warps;
-        if (adj)
-            rc = G == 1 ? launch_forward<1, true>(a, ni, ws->sm_count, s)
-                        : (G == 2 ? launch_forward<2, true>(a, ni, ws->sm_count, s)
-                                  : launch_forward<4, true>(a, ni, ws->sm_count, s));
-        else
-            rc = G == 1 ? launch_forward<1, false>(a, ni, ws->sm_count, s)
-                        : (G == 2 ? launch_forward<2, false>(a, ni, ws->sm_count, s)
-                                  : launch_forward<4, false>(a, ni, ws->sm_count, s));
+        if (cfg->fwd_warps == 1 || cfg->fwd_warps == 2 || cfg->fwd_warps == 4 || cfg->fwd_warps == 8)
+            G = cfg->fwd_warps;
+        switch (G * 2 + (adj ? 1 : 0)) {
+            case 2: rc = launch_forward<1, false>(a, ni, ws->sm_count, s); break;
+            case 3: rc = launch_forward<1, true>(a, ni, ws->sm_count, s); break;
+            case 4: rc = launch_forward<2, false>(a, ni, ws->sm_count, s); break;
+            case 5: rc = launch_forward<2, true>(a, ni, ws->sm_count, s); break;
+            case 8: rc = launch_forward<4, false>(a, ni, ws->sm_count, s); break;
+            case 9: rc = launch_forward<4, true>(a, ni, ws->sm_count, s); break;
+            case 16: rc = launch_forward<8, false>(a, ni, ws->sm_count, s); break;
+            default: rc = launch_forward<8, true>(a, ni, ws->sm_count, s); break;
+        }
     }
     if (rc || !adj) return rc;
     launch_pdl(k_adj_epilogue, dim3((prm->cap + 255) / 256), dim3(256), 0, s, prm->p, prm->m, prm->cap, ws->adj_fix, ws->adj_pairs,

@@ -16,11 +16,9 @@ namespace {
 // with Q = log2(e) R^T D^2 R, so that exp(-||D R (v - c)||^2) = 2^(-dv^T Q dv);
 // kbwd: (c, r2) and the rows of R with e_k = log2(e) d_k^2 in .w.
 // R is the App. A matrix (entries r1..r9).
-__global__ void k_prep(const float *p, int cap, const int32_t *m_dev, float nle, float4 *kfwd, float4 *kbwd) {
-    pdl_wait();
-    pdl_trigger();
-    int m = *m_dev;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+__device__ __forceinline__ void prep_kernels(const float *p, int cap, int m, float nle, float4 *kfwd, float4 *kbwd,
+                                             int first, int stride) {
+    for (int j = first; j < m; j += stride) {
         float cx = p[PCX * cap + j], cy = p[PCY * cap + j], cz = p[PCZ * cap + j];
         float d1 = p[PD1 * cap + j], d2 = p[PD2 * cap + j], d3 = p[PD3 * cap + j];
         float w = p[PW * cap + j];
@@ -131,37 +129,46 @@ __global__ void __launch_bounds__(kOrderChunk) k_order_items(const uint8_t *item
     if (cls >= 0) order_rec[s_wcnt[warp][cls] + rank] = r;
 }
 
-// One block per super cell: every kernel whose support may reach the box.
-__global__ void __launch_bounds__(256) k_super_lists(const float4 *kfwd, const int32_t *m_dev, const float4 *slo,
-                                                     const float4 *shi, uint32_t *list, uint32_t *cnt, int cap,
-                                                     int32_t *status, long long *needed) {
+// The per-step rebuild in one launch: blocks [0, nsuper) list, per super
+// cell, every kernel whose support may reach its box (centre and r2 taken
+// from the parameters with the same float operations as the records); the
+// remaining blocks write the per-kernel records.
+__global__ void __launch_bounds__(256) k_rebuild(const float *p, int cap, const int32_t *m_dev, float nle,
+                                                 float4 *kfwd, float4 *kbwd, const float4 *slo, const float4 *shi,
+                                                 int nsuper, uint32_t *list, uint32_t *cnt, int scap, int32_t *status,
+                                                 long long *needed) {
     pdl_wait();
     pdl_trigger();
     __shared__ uint32_t tmp[33];
-    int s = blockIdx.x;
-    float4 lo = slo[s], hi = shi[s];
+    const int m = *m_dev;
+    const int s = blockIdx.x;
+    if (s >= nsuper) {
+        prep_kernels(p, cap, m, nle, kfwd, kbwd, (s - nsuper) * blockDim.x + threadIdx.x,
+                     (gridDim.x - nsuper) * blockDim.x);
+        return;
+    }
+    const float4 lo = slo[s], hi = shi[s];
     if (!(lo.x <= hi.x)) {
         if (threadIdx.x == 0) cnt[s] = 0;
         return;
     }
-    int m = *m_dev;
     uint32_t count = 0;
-    uint32_t *out = list + (size_t)s * cap;
+    uint32_t *out = list + (size_t)s * scap;
     for (int j0 = 0; j0 < m; j0 += 256) {
-        int j = j0 + threadIdx.x;
+        const int j = j0 + threadIdx.x;
         uint32_t hit = 0;
         if (j < m) {
-            float4 k = kfwd[3 * j];
-            hit = box_d2(k.x, k.y, k.z, lo, hi) < k.w;
+            const float r2 = support_r2(p[PD1 * cap + j], p[PD2 * cap + j], p[PD3 * cap + j], nle);
+            hit = box_d2(p[PCX * cap + j], p[PCY * cap + j], p[PCZ * cap + j], lo, hi) < r2;
         }
         uint32_t tot;
-        uint32_t off = block_exscan(hit, tmp, &tot);
-        if (hit && count + off < (uint32_t)cap) out[count + off] = (uint32_t)j;
+        const uint32_t off = block_exscan(hit, tmp, &tot);
+        if (hit && count + off < (uint32_t)scap) out[count + off] = (uint32_t)j;
         count += tot;
     }
     if (threadIdx.x == 0) {
         cnt[s] = count;
-        if (count > (uint32_t)cap) {
+        if (count > (uint32_t)scap) {
             atomicOr(status, SERBF_FLAG_SUPER_LIST);
             atomicMax(needed + 0, (long long)count);
         }
@@ -245,13 +252,6 @@ bool ws_ok(const serbf_workspace *ws) { return ws && ws->magic == kMagic && ws->
 }  // namespace
 
 namespace serbf {
-int launch_prep(const serbf_params *prm, const serbf_config *cfg, serbf_workspace *ws, cudaStream_t s) {
-    float nle = (float)(-log(cfg->eps));
-    int blocks = (prm->cap + 127) / 128;
-    launch_pdl(k_prep, dim3(blocks), dim3(128), 0, s, prm->p, prm->cap, prm->m, nle, ws->kfwd, ws->kbwd);
-    SERBF_CHECK_LAUNCH();
-    return SERBF_OK;
-}
 }  // namespace serbf
 
 extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg,
@@ -276,10 +276,15 @@ extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params
         SERBF_CHECK_LAUNCH();
         if (cudaEventRecord(ws->ev_join, ws->aux) != cudaSuccess) return SERBF_ECUDA;
     }
-    int rc = launch_prep(prm, cfg, ws, s);
-    if (rc) return rc;
-    launch_pdl(k_super_lists, dim3(ws->nsuper), dim3(256), 0, s, ws->kfwd, prm->m, ws->sup_lo, ws->sup_hi, ws->sup_list, ws->sup_cnt,
-                                              ws->sz.super_cap, ws->status, ws->needed);
+    {
+        const float nle = (float)(-log(cfg->eps));
+        const int prep_blocks = (prm->cap + 255) / 256;
+        launch_pdl(k_rebuild, dim3(ws->nsuper + prep_blocks), dim3(256), 0, s, (const float *)prm->p, prm->cap,
+                   (const int32_t *)prm->m, nle, ws->kfwd, ws->kbwd, (const float4 *)ws->sup_lo,
+                   (const float4 *)ws->sup_hi, ws->nsuper, ws->sup_list, ws->sup_cnt, ws->sz.super_cap, ws->status,
+                   ws->needed);
+    }
+    int rc = SERBF_OK;
     SERBF_CHECK_LAUNCH();
     // join the side stream
     if (fork && cudaStreamWaitEvent(s, ws->ev_join, 0) != cudaSuccess) return SERBF_ECUDA;

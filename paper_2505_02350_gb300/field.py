@@ -194,14 +194,14 @@ class Problem:
                             self.adam_v, self.state, self.stats, self.cfg, self.ws, force=force)
 
     def autotune(self, reps=5):
-        """Times the forward (+ adjoint when fused) with 1, 2 and 4 warps per
+        """Times the forward (+ adjoint when fused) with 1, 2, 4 and 8 warps per
         work item on the current parameters and keeps the fastest in
         cfg.fwd_warps.  Returns {warps: ms per call}.  Parameters are not
         changed; the outputs of the last call are left in psi/err/grad."""
         fn = self.forward_backward if self.fused else self.forward
         self.build_neighbors()
         times = {}
-        for g in (1, 2, 4):
+        for g in (1, 2, 4, 8):
             self.cfg.fwd_warps = g
             fn()  # files the work costs for this configuration's order
             torch.cuda.synchronize(self.dev)

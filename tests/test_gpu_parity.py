@@ -256,9 +256,9 @@ def test_fused_forward_backward_c2(torch, orc, c2):
     _fused_check(torch, orc, c2)
 
 
-@pytest.mark.parametrize("warps", [1, 2, 4])
+@pytest.mark.parametrize("warps", [1, 2, 4, 8])
 def test_forward_backward_every_warp_split(torch, orc, warps):
-    """Each work-item split (1, 2 or 4 warps per item) meets the bars."""
+    """Each work-item split (1, 2, 4 or 8 warps per item) meets the bars."""
     pb = problem("c2", layers=[32])
     pb.cfg.fwd_warps = warps
     _fused_check(torch, orc, pb)
@@ -270,7 +270,7 @@ def test_forward_backward_every_warp_split(torch, orc, warps):
 def test_autotune_picks_a_split(torch):
     pb = problem("c1")
     times = pb.autotune(reps=2)
-    assert set(times) == {1, 2, 4} and all(t > 0 for t in times.values())
+    assert set(times) == {1, 2, 4, 8} and all(t > 0 for t in times.values())
     assert pb.cfg.fwd_warps == min(times, key=times.get)
 
 
