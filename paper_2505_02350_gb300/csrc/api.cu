@@ -75,7 +75,6 @@ void carve(Carver &c, serbf_workspace *w, const serbf_ws_sizes *s) {
     w->sup_cnt = c.take<uint32_t>(S);
     w->fwd_part = c.take<FwdPart>(T + 1);
     w->fwd_gpart = c.take<FwdPart>(T / kFwdGroup + 2);
-    w->fwd_group_done = c.take<uint32_t>(T / kFwdGroup + 2);
     w->bwd_pairs = c.take<unsigned long long>(K);
     w->adj_fix = c.take<unsigned long long>(K * 10);
     w->adj_pairs = c.take<unsigned long long>(8);
@@ -285,9 +284,6 @@ int serbf_workspace_init(serbf_workspace *ws, void *dev, size_t bytes, const ser
     if (cudaMemset(ws->status, 0, 16 * sizeof(int32_t)) != cudaSuccess) return SERBF_ECUDA;
     if (cudaMemset(ws->needed, 0, 4 * sizeof(long long)) != cudaSuccess) return SERBF_ECUDA;
     if (cudaMemset(ws->counters, 0, 16 * sizeof(uint32_t)) != cudaSuccess) return SERBF_ECUDA;
-    if (cudaMemset(ws->fwd_group_done, 0, sizeof(uint32_t) * (size_t)(ws->max_tiles / kFwdGroup + 2)) !=
-        cudaSuccess)
-        return SERBF_ECUDA;
     {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return SERBF_ECUDA;

@@ -97,7 +97,6 @@ struct serbf_workspace {
     // reductions
     serbf::FwdPart *fwd_part;     // max_tiles
     serbf::FwdPart *fwd_gpart;    // max_tiles / kFwdGroup + 1
-    uint32_t *fwd_group_done;     // max_tiles / kFwdGroup + 1 (kept zero between launches)
     unsigned long long *bwd_pairs;
     unsigned long long *adj_fix;    // max_kernels x 10: fixed-point moments of the fused adjoint
     unsigned long long *adj_pairs;  // [8]: [0] adjoint pairs of the fused adjoint

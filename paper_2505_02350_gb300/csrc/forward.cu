@@ -45,12 +45,8 @@ struct FwdArgs {
     float *psi, *err;
     uint8_t *mask;
     FwdPart *part;        // one partial per tile
-    FwdPart *gpart;       // one partial per group of kFwdGroup tiles
-    uint32_t *group_done; // tiles finished per group
-    uint32_t *counter;    // groups finished
     uint32_t *item_next;  // next work item to take (zero between launches)
     uint32_t *exit_count; // blocks that have exited (zero between launches)
-    double *stats;
 };
 
 constexpr int kTouch = 128;  // kernels remembered per warp and item for the adjoint (more: re-scan the list)
@@ -172,6 +168,7 @@ __device__ __forceinline__ FwdPart reduce_parts(const FwdPart *p, uint32_t b, ui
     ff l{0.f, 0.f};
     float mx = 0.f;
     unsigned long long c = 0, pr = 0;
+#pragma unroll 4
     for (uint32_t q = b + lane; q < e; q += 32) {
         l = ff_add(l, ff{__ldcg(&p[q].l2hi), __ldcg(&p[q].l2lo)});
         mx = fmaxf(mx, __ldcg(&p[q].maxe));
@@ -185,58 +182,25 @@ __device__ __forceinline__ FwdPart reduce_parts(const FwdPart *p, uint32_t b, ui
     return FwdPart{l.hi, l.lo, mx, (uint32_t)c, pr};
 }
 
-// Loss terms of one tile: stored as the tile's partial.  The warp that
-// completes a group of kFwdGroup tiles reduces the group; the warp that
-// completes the last group writes the totals.  Sums run in tile order, so
-// they do not depend on which warp handled which tile.
+// Loss terms of one tile, stored as the tile's partial (lane order within the
+// tile).  The partials are reduced in tile order after the launch, so the
+// totals do not depend on which warp handled which tile.
 __device__ __forceinline__ void finish_tile(const FwdArgs &a, uint32_t t, float l2, float mx_l, uint32_t cnt_l,
                                             uint32_t pairs_l, int lane) {
     const ff l2s = warp_sum_ff(ff{l2, 0.f});
     const float mx = warp_max(mx_l);
     const uint32_t cnt = warp_sum(cnt_l), pr = warp_sum(pairs_l);
-    uint32_t done = 0;
-    if (lane == 0) {
-        a.part[t] = FwdPart{l2s.hi, l2s.lo, mx, cnt, (unsigned long long)pr};
-        __threadfence();
-        done = atomicAdd(a.group_done + t / kFwdGroup, 1u);
-    }
-    done = __shfl_sync(0xffffffffu, done, 0);
-    const uint32_t g = t / kFwdGroup;
-    const uint32_t gb = g * kFwdGroup;
-    const uint32_t ge = (uint32_t)min((int64_t)gb + kFwdGroup, a.ntiles);
-    if (done != ge - gb - 1) return;
-    __threadfence();
-    const FwdPart gp = reduce_parts(a.part, gb, ge, lane);
-    const uint32_t ngroups = (uint32_t)((a.ntiles + kFwdGroup - 1) / kFwdGroup);
-    uint32_t gdone = 0;
-    if (lane == 0) {
-        a.gpart[g] = gp;
-        a.group_done[g] = 0u;
-        __threadfence();
-        gdone = atomicAdd(a.counter, 1u);
-    }
-    gdone = __shfl_sync(0xffffffffu, gdone, 0);
-    if (gdone != ngroups - 1) return;
-    __threadfence();
-    const FwdPart tot = reduce_parts(a.gpart, 0, ngroups, lane);
-    if (lane == 0) {
-        a.stats[SERBF_STAT_L2] = (double)tot.l2hi + (double)tot.l2lo;
-        a.stats[SERBF_STAT_MAXE] = tot.maxe;
-        a.stats[SERBF_STAT_COUNT] = (double)tot.cnt;
-        a.stats[SERBF_STAT_PAIRS_FWD] = (double)tot.pairs;
-        *a.counter = 0u;
-    }
+    if (lane == 0) a.part[t] = FwdPart{l2s.hi, l2s.lo, mx, cnt, (unsigned long long)pr};
 }
 
 // Eq. 3-18 filter and residual of one point; returns its loss contributions.
-__device__ __forceinline__ float point_out(const FwdArgs &a, int64_t i, bool valid, float ps, uint32_t np, float &l2,
-                                           float &mx, uint32_t &cnt, uint32_t &pairs) {
+__device__ __forceinline__ float point_out(const FwdArgs &a, int64_t i, bool valid, float t, float ps, uint32_t np,
+                                           float &l2, float &mx, uint32_t &cnt, uint32_t &pairs) {
     l2 = 0.f;
     mx = 0.f;
     cnt = 0u;
     pairs = 0u;
     if (!valid) return 0.f;
-    const float t = a.t[i];
     const bool m0 = (a.tau1 < t) && (t < a.tau2);
     const bool m1 = (t <= a.tau1) && (ps > a.tau1);
     const bool m2 = (t >= a.tau2) && (ps < a.tau2);
@@ -285,7 +249,7 @@ __device__ __forceinline__ ItemInfo item_info(uint4 r, int lane) {
 template <int G, bool ADJ>
 __device__ __forceinline__ void forward_share(const FwdArgs &a, const ItemInfo &it, int w, float *ringP, float *ringF,
                                               int lane, f2 (&acc)[2], uint32_t (&n)[2], uint32_t &cost,
-                                              uint32_t *touch, int &ntouch) {
+                                              uint32_t *touch, int &ntouch, float (&tv)[2]) {
     const unsigned lt = (1u << lane) - 1u;
     // invalid lanes carry NaN so the support test fails for them
     const float qnan = __int_as_float(0x7fc00000);
@@ -299,6 +263,9 @@ __device__ __forceinline__ void forward_share(const FwdArgs &a, const ItemInfo &
         P[1][0] = f2_pack(x1, x1);
         P[1][1] = f2_pack(y1, y1);
         P[1][2] = f2_pack(z1, z1);
+        // the targets, for the residuals after the sums (loaded early)
+        tv[0] = it.v0 ? a.t[it.i0] : 0.f;
+        tv[1] = it.v1 ? a.t[it.i1] : 0.f;
     }
     float4 lo = a.tile_lo[it.t0], hi = a.tile_hi[it.t0];
     if (it.two) {
@@ -664,14 +631,18 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? 20 : 24)) / G) k
     uint4 rec = s_rec;  // the item's record; no points (w = 0) when done
     while (rec.w != 0u) {
         const ItemInfo it = item_info(rec, lane);
-        // the next claim is made now; it is only resolved at the end
+        // the next claim is made now, its record is fetched after the sums
+        // and used at the end, so neither round trip is on the item's path
         uint32_t knext = 0;
         if (threadIdx.x == 0) knext = atomicAdd(a.item_next, 1u);
         f2 acc[2];
         uint32_t n[2], cost;
         int ntouch = 0;
+        float tv[2];
         forward_share<G, ADJ>(a, it, warp, ringP[warp], ringF[warp], lane, acc, n, cost, touch[ADJ ? warp : 0],
-                              ntouch);
+                              ntouch, tv);
+        uint4 rn = make_uint4(0u, 0u, 0u, 0u);
+        if (threadIdx.x == 0) rn = resolve(a, knext);
         if (G == 1) {
             // one warp: finish both tiles directly
             float l0, h0, l1, h1;
@@ -679,11 +650,11 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? 20 : 24)) / G) k
             f2_unpack(acc[1], l1, h1);
             float l2, mx;
             uint32_t cnt, pr;
-            const float e0 = point_out(a, it.i0, it.v0, l0 + h0, n[0], l2, mx, cnt, pr);
+            const float e0 = point_out(a, it.i0, it.v0, tv[0], l0 + h0, n[0], l2, mx, cnt, pr);
             finish_tile(a, it.t0, l2, mx, cnt, pr, lane);
             float e1 = 0.f;
             if (it.two) {
-                e1 = point_out(a, it.i1, it.v1, l1 + h1, n[1], l2, mx, cnt, pr);
+                e1 = point_out(a, it.i1, it.v1, tv[1], l1 + h1, n[1], l2, mx, cnt, pr);
                 finish_tile(a, it.t0 + 1, l2, mx, cnt, pr, lane);
             }
             if (ADJ) {
@@ -698,11 +669,7 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? 20 : 24)) / G) k
                                      ntouch, adjq[0], lane, cost);
                 __syncwarp();
             }
-            uint4 rn = make_uint4(0u, 0u, 0u, 0u);
-            if (lane == 0) {
-                note_cost(a, mean, rec, cost);
-                rn = resolve(a, knext);
-            }
+            if (lane == 0) note_cost(a, mean, rec, cost);
             rec.x = __shfl_sync(0xffffffffu, rn.x, 0);
             rec.y = __shfl_sync(0xffffffffu, rn.y, 0);
             rec.z = __shfl_sync(0xffffffffu, rn.z, 0);
@@ -733,7 +700,7 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? 20 : 24)) / G) k
             uint32_t cnt, pr;
             const int64_t i = warp ? it.i1 : it.i0;
             const bool v = warp ? it.v1 : it.v0;
-            const float e = point_out(a, i, v, ps, np, l2, mx, cnt, pr);
+            const float e = point_out(a, i, v, warp ? tv[1] : tv[0], ps, np, l2, mx, cnt, pr);
             finish_tile(a, it.t0 + warp, l2, mx, cnt, pr, lane);
             if (ADJ) {
                 float4 lo, hi;
@@ -753,7 +720,7 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? 20 : 24)) / G) k
                     for (int q = 0; q < G; ++q) c += red_cost[q];
                     note_cost(a, mean, rec, c);
                 }
-                s_rec = resolve(a, knext);
+                s_rec = rn;
             }
         }
         if (ADJ) {
@@ -813,43 +780,79 @@ int64_t forward_groups(int sm_count) {
     return (int64_t)sm_count * per_sm;
 }
 
-// Fused adjoint epilogue: one thread per kernel turns its fixed-point moments
-// into the ten App. A gradients and clears the accumulators; the last block
-// publishes the adjoint pair count.
+// After the forward: the Eq. 3-19 loss terms from the tile partials in tile
+// order (a warp per group of kFwdGroup tiles, then the last block over the
+// group partials), and with the fused adjoint the ten App. A gradients of each
+// kernel from its fixed-point moments (a thread per kernel, accumulators
+// cleared for the next launch).  The last block writes the totals.
 constexpr float kFixUnitF = 1.4551915228366852e-11f;  // 2^-36
+constexpr int kFinishThreads = 256;
 
-__global__ void k_adj_epilogue(const float *p, const int32_t *m_dev, int cap, unsigned long long *fix,
-                               unsigned long long *pairs, uint32_t *counter, float *grad, double *stats) {
+struct FinishArgs {
+    const FwdPart *part;
+    FwdPart *gpart;
+    int64_t ntiles;
+    const float *p;
+    const int32_t *m_dev;
+    int cap;
+    unsigned long long *fix, *pairs;
+    float *grad;
+    uint32_t *counter;
+    double *stats;
+};
+
+template <bool ADJ>
+__global__ void __launch_bounds__(kFinishThreads) k_fwd_finish(FinishArgs f) {
     pdl_wait();
     pdl_trigger();
     __shared__ bool s_last;
-    const int m = *m_dev;
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < m) {
-        unsigned long long *o = fix + 10 * (size_t)j;
-        float M[10];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t ngroups = (f.ntiles + kFwdGroup - 1) / kFwdGroup;
+    const int64_t g = (int64_t)blockIdx.x * (kFinishThreads / 32) + warp;
+    if (g < ngroups) {
+        const uint32_t gb = (uint32_t)(g * kFwdGroup);
+        const uint32_t ge = (uint32_t)min((int64_t)gb + kFwdGroup, f.ntiles);
+        const FwdPart gp = reduce_parts(f.part, gb, ge, lane);
+        if (lane == 0) f.gpart[g] = gp;
+    }
+    if (ADJ) {
+        const int m = *f.m_dev;
+        const int j = blockIdx.x * blockDim.x + threadIdx.x;
+        if (j < m) {
+            unsigned long long *o = f.fix + 10 * (size_t)j;
+            float M[10];
 #pragma unroll
-        for (int r = 0; r < 10; ++r) {
-            // int64 -> float through two 32-bit conversions (the 64-bit one runs
-        // on the slow double-precision unit); relative error ~1e-7
-        const long long v = (long long)o[r];
-        const float hi = (float)(int)(v >> 32), lo = (float)(uint32_t)(v & 0xffffffffll);
-        M[r] = fmaf(hi, 4294967296.f, lo) * kFixUnitF;
-            o[r] = 0ull;
+            for (int r = 0; r < 10; ++r) {
+                // int64 -> float through two 32-bit conversions (the 64-bit
+                // one runs on the slow double-precision unit); relative error ~1e-7
+                const long long v = (long long)o[r];
+                const float hi = (float)(int)(v >> 32), lo = (float)(uint32_t)(v & 0xffffffffll);
+                M[r] = fmaf(hi, 4294967296.f, lo) * kFixUnitF;
+                o[r] = 0ull;
+            }
+            grad_from_moments(f.p, f.cap, j, M, f.grad);
         }
-        grad_from_moments(p, cap, j, M, grad);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(f.counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last || warp != 0) return;
     __threadfence();
-    stats[SERBF_STAT_PAIRS_BWD] = (double)__ldcg(pairs);
-    *pairs = 0ull;
-    *counter = 0u;
+    const FwdPart tot = reduce_parts(f.gpart, 0, (uint32_t)ngroups, lane);
+    if (lane == 0) {
+        f.stats[SERBF_STAT_L2] = (double)tot.l2hi + (double)tot.l2lo;
+        f.stats[SERBF_STAT_MAXE] = tot.maxe;
+        f.stats[SERBF_STAT_COUNT] = (double)tot.cnt;
+        f.stats[SERBF_STAT_PAIRS_FWD] = (double)tot.pairs;
+        if (ADJ) {
+            f.stats[SERBF_STAT_PAIRS_BWD] = (double)__ldcg(f.pairs);
+            *f.pairs = 0ull;
+        }
+        *f.counter = 0u;
+    }
 }
 
 int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi, float *err,
@@ -900,18 +903,10 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
     a.err = err;
     a.mask = mask;
     a.part = ws->fwd_part;
-    a.gpart = ws->fwd_gpart;
-    a.group_done = ws->fwd_group_done;
-    a.counter = ws->counters + 0;
     a.item_next = ws->counters + 4;
     a.exit_count = ws->counters + 6;
-    a.stats = stats;
     int rc = SERBF_OK;
-    if (ws->ntiles == 0) {
-        // nothing to evaluate: the loss terms are zero
-        cudaMemsetAsync(stats + SERBF_STAT_L2, 0, 4 * sizeof(double), s);
-        SERBF_CHECK_LAUNCH();
-    } else {
+    if (ws->ntiles > 0) {
         // warps per item: the fewest that still leave about four items per
         // group of warps for the heavy-first balancing
         const int64_t ni = ws->nitems;
@@ -929,9 +924,27 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
             default: rc = launch_forward<8, true>(a, ni, ws->sm_count, s); break;
         }
     }
-    if (rc || !adj) return rc;
-    launch_pdl(k_adj_epilogue, dim3((prm->cap + 255) / 256), dim3(256), 0, s, prm->p, prm->m, prm->cap, ws->adj_fix, ws->adj_pairs,
-                                                          ws->counters + 5, grad, stats);
+    if (rc) return rc;
+    FinishArgs f;
+    f.part = ws->fwd_part;
+    f.gpart = ws->fwd_gpart;
+    f.ntiles = ws->ntiles;
+    f.p = prm->p;
+    f.m_dev = prm->m;
+    f.cap = prm->cap;
+    f.fix = ws->adj_fix;
+    f.pairs = ws->adj_pairs;
+    f.grad = grad;
+    f.counter = ws->counters + 5;
+    f.stats = stats;
+    const int64_t ngroups = (ws->ntiles + kFwdGroup - 1) / kFwdGroup;
+    int64_t nb = (ngroups + kFinishThreads / 32 - 1) / (kFinishThreads / 32);
+    if (adj) nb = max(nb, (int64_t)((prm->cap + kFinishThreads - 1) / kFinishThreads));
+    if (nb < 1) nb = 1;
+    if (adj)
+        launch_pdl(k_fwd_finish<true>, dim3((unsigned)nb), dim3(kFinishThreads), 0, s, f);
+    else
+        launch_pdl(k_fwd_finish<false>, dim3((unsigned)nb), dim3(kFinishThreads), 0, s, f);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;
 }
