@@ -163,6 +163,25 @@ __device__ __forceinline__ void eval_pairs(const float *ring, int pb, int npairs
     }
 }
 
+// Whole-warp reductions in one instruction (redux.sync, sm_100 family): exact
+// for integers; min / max of floats select one of the inputs, so the result
+// does not depend on the order.
+__device__ __forceinline__ uint32_t redux_add(uint32_t v) {
+    uint32_t r;
+    asm volatile("redux.sync.add.u32 %0, %1, 0xffffffff;" : "=r"(r) : "r"(v));
+    return r;
+}
+__device__ __forceinline__ float redux_min(float v) {
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float redux_max(float v) {
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+
 // Fixed-order warp reduction of tile partials [b, e) into one partial.
 __device__ __forceinline__ FwdPart reduce_parts(const FwdPart *p, uint32_t b, uint32_t e, int lane) {
     ff l{0.f, 0.f};
@@ -188,8 +207,8 @@ __device__ __forceinline__ FwdPart reduce_parts(const FwdPart *p, uint32_t b, ui
 __device__ __forceinline__ void finish_tile(const FwdArgs &a, uint32_t t, float l2, float mx_l, uint32_t cnt_l,
                                             uint32_t pairs_l, int lane) {
     const ff l2s = warp_sum_ff(ff{l2, 0.f});
-    const float mx = warp_max(mx_l);
-    const uint32_t cnt = warp_sum(cnt_l), pr = warp_sum(pairs_l);
+    const float mx = redux_max(mx_l);
+    const uint32_t cnt = redux_add(cnt_l), pr = redux_add(pairs_l);
     if (lane == 0) a.part[t] = FwdPart{l2s.hi, l2s.lo, mx, cnt, (unsigned long long)pr};
 }
 
@@ -498,7 +517,7 @@ __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &
     }
     if (qn > 0) adjoint_batch(a, q, head, qn, nz, nc0, nc1, lane, pairs);
     __syncwarp();
-    const uint32_t tot = warp_sum(pairs);
+    const uint32_t tot = redux_add(pairs);
     if (lane == 0 && tot) atomicAdd(a.adj_pairs, (unsigned long long)tot);
     cost += (uint32_t)(nk * (nc0 + nc1)) / 4u + 32u;
 }
@@ -529,15 +548,12 @@ __device__ __forceinline__ int nz_tile(NzPoints &nzp, int base, bool nz, float x
     float mnx = nz ? x : INFINITY, mny = nz ? y : INFINITY, mnz = nz ? z : INFINITY;
     float mxx = nz ? x : -INFINITY, mxy = nz ? y : -INFINITY, mxz = nz ? z : -INFINITY;
     if (bal) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
-            mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
-            mnz = fminf(mnz, __shfl_xor_sync(0xffffffffu, mnz, o));
-            mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
-            mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
-            mxz = fmaxf(mxz, __shfl_xor_sync(0xffffffffu, mxz, o));
-        }
+        mnx = redux_min(mnx);
+        mny = redux_min(mny);
+        mnz = redux_min(mnz);
+        mxx = redux_max(mxx);
+        mxy = redux_max(mxy);
+        mxz = redux_max(mxz);
     }
     lo = make_float4(mnx, mny, mnz, 0.f);
     hi = make_float4(mxx, mxy, mxz, 0.f);
@@ -603,9 +619,12 @@ __device__ __forceinline__ void sched_finish(const FwdArgs &a) {
 // The G warps of a block share an item (its candidate list split by 32-entry
 // chunks); their partial sums are combined in warp order, so Psi does not
 // depend on timing.  G = 1 when there are enough items to balance the warps,
-// 2 or 4 for small problems.
+// 2 or 4 for small problems.  Resident warps per SM (the register budget):
+// 16 for the fused variants with 1 or 4 warps per item and 20 with 2, 24 for
+// eight warps and for the forward alone (20 with one warp); more resident
+// warps measured slower on every workload.
 template <int G, bool ADJ>
-__global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? 20 : 24)) / G) k_forward(FwdArgs a) {
+__global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 16) : (G == 1 ? 20 : 24))) / G) k_forward(FwdArgs a) {
     pdl_wait();
     pdl_trigger();
     // two rings per warp (kernels partly / fully covering the item box); a
