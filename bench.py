@@ -150,11 +150,11 @@ def build_problem(name, device, sf=None):
     return pb, desc
 
 
-def timed_steps(K, flush, step_graph, split_graphs, stats):
+def timed_steps(K, flush, step_graph, split_graphs, stats, reset):
     """2K steps, alternately the one-graph step (timed for the value) and the
     same step as graphs split at the forward (timed for the forward's own
-    duration), so that both see the same stage of the fit.  Each step first
-    writes the L2 flush buffer (untimed), then replays its graph(s) between
+    duration).  Each step first restores the fit's state (reset) and writes
+    the L2 flush buffer (both untimed), then replays its graph(s) between
     CUDA events on this stream.  Returns the one-graph step times (ms), the
     split steps' segment times (ms, one list per graph) and the (forward,
     adjoint) pair counts of both kinds of step."""
@@ -166,11 +166,13 @@ def timed_steps(K, flush, step_graph, split_graphs, stats):
     pairs = torch.zeros(2, K, 2, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
     for k in range(K):
+        reset()
         flush.fill_(k & 255)
         ev1[k][0].record()
         step_graph.replay()
         ev1[k][1].record()
         pairs[0, k].copy_(stats[4:6])
+        reset()
         flush.fill_((k + 128) & 255)
         ev2[k][0].record()
         for i, g in enumerate(split_graphs):
@@ -209,6 +211,10 @@ def run_native(args, ws, rank, local):
     flags, needed = pb.status()
     if flags:
         raise RuntimeError("capacity flags %d needed %s" % (flags, needed))
+    # every timed step runs the same epoch of the fit: the state after the
+    # warm-up is restored before each one, so the workload does not drift
+    # with the number of steps (pruning shrinks M as a fit goes on)
+    snap = pb.snapshot()
     K = args.steps
     sampler = ClockSampler(local)
     if ws > 1:
@@ -220,7 +226,8 @@ def run_native(args, ws, rank, local):
     t0_wall = time.time()
     # value: one graph per step; roofline: the forward's own events in the
     # interleaved steps split at the forward
-    step_ms, seg, pr, pr2 = timed_steps(K, flush, g_step, [g_build, g_fwd, g_rest], pb.stats)
+    step_ms, seg, pr, pr2 = timed_steps(K, flush, g_step, [g_build, g_fwd, g_rest], pb.stats,
+                                        lambda: pb.restore(snap))
     wall = time.perf_counter() - t0
     sampler.mark(t0_wall, time.time())
     if ws > 1:
@@ -242,6 +249,7 @@ def run_native(args, ws, rank, local):
     e2e_pairs = 0.0
     te = time.perf_counter()
     for k in range(K):
+        pb.restore(snap)
         for r in range(4):
             dev_pts[r][:n].copy_(host_pts[r], non_blocking=True)
         pb.epoch_graph()
@@ -268,7 +276,8 @@ def run_native(args, ws, rank, local):
                    "autotune_ms": {str(k): round(v, 4) for k, v in tune.items()},
                    "pairs_fwd_per_step": float(pf.mean()), "pairs_bwd_per_step": float(pbk.mean()),
                    "l2_flush": "256 MiB buffer written between timed steps", "parallelism": "replicas",
-                   "timing": "K one-graph steps (value) interleaved with K steps split at the forward (roofline)"},
+                   "timing": "K one-graph steps (value) interleaved with K steps split at the forward (roofline)",
+                   "state": "the fit's state after the warm-up, restored before every step (untimed)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 128},
         "gpu_launches": LAUNCHES_PER_STEP * K,
         "roofline": {"bound": "alu", "kernel": "k_forward<G, adjoint> + k_fwd_finish<adjoint>", "achieved": achieved / 1e12,
