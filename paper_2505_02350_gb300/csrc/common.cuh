@@ -107,7 +107,7 @@ struct serbf_workspace {
     float4 *nz;         // 32 slots per tile: (x, y, z, E) of its nonzero-residual points
     // optimiser step scratch
     float *step_part;   // per-block partial sums
-    double *step_scal;  // use_l1, Adam step, lr for the update stage
+    double *step_scal;  // alpha, beta, Adam bias corrections
     // addition scratch
     unsigned long long *sel_key;  // max(max_kernels, 8192)
     uint32_t *sel_keep;           // max(max_kernels, 8192)

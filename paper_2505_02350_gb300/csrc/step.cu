@@ -2,9 +2,8 @@
 // Adam, and the epoch-tail gates (Eq. 3-27 deletion due, Eq. l1_activate,
 // Eq. add_activate, L2-only phase with a cosine learning rate from T^e).  The
 // state machine lives on the device so that a step needs no host round trip.
-// Two grid-wide launches: per-block sums of the Eq. 3-21 terms, then the
-// update, in which one block owns the weight row and runs the epoch tail.
-// Also the Eq. 3-27 compaction.
+// Two grid-wide launches whose last blocks finish the reductions.  Also the
+// Eq. 3-27 compaction.
 #include <math.h>
 
 #include "common.cuh"
@@ -14,7 +13,6 @@ using namespace serbf;
 namespace {
 
 constexpr int kStepThreads = 256;
-constexpr int kOwnerBatch = 8;  // weights per thread and round in the block that owns the weight row
 
 // Block sums of NV float values with float-float trees (FP64 is slow here).
 template <int NV>
@@ -74,8 +72,9 @@ struct StepArgs {
     serbf_state *st;
     double *stats;
     serbf_config c;
-    float *part;      // per-block partial sums of the first stage (float-float pairs)
-    double *scal;     // the state's scalars for the second stage: use_l1, Adam step t, lr
+    float *part;      // per block partial sums (float-float pairs)
+    double *scal;     // alpha, beta, bias corrections for the update kernel
+    uint32_t *counter;
 };
 
 constexpr int kStateWords = (int)(sizeof(serbf_state) / 4);
@@ -95,18 +94,21 @@ __device__ __forceinline__ void alpha_terms(const StepArgs &a, int j, bool use_l
 }
 
 // alpha (clamped to [0, 1]; 1 when the L1 term is off or the two gradients
-// coincide), beta = 1 - alpha, the Adam bias corrections at step t.
+// coincide), beta = 1 - alpha, the Adam bias corrections; writes the stats.
 // sc = {alpha, beta, 1 - beta1^t, 1 - beta2^t}.
-__device__ __forceinline__ void alpha_scalars(const StepArgs &a, bool use_l1, const ff (&fin)[3], float t,
-                                              float (&sc)[4]) {
+__device__ __forceinline__ void alpha_finish(const StepArgs &a, bool use_l1, const ff (&fin)[3], float (&sc)[4]) {
     // float arithmetic (FP64 is slow on this part): alpha to ~1e-7
     const float num = fin[1].hi + fin[1].lo, den = fin[2].hi + fin[2].lo;
     float al = 1.f;
     if (use_l1 && den > 0.f) al = fminf(1.f, fmaxf(0.f, num / den));
+    const float t = (float)(a.st->adam_t + 1);
     sc[0] = al;
     sc[1] = 1.f - al;
     sc[2] = 1.f - powf((float)a.c.beta1, t);
     sc[3] = 1.f - powf((float)a.c.beta2, t);
+    a.stats[SERBF_STAT_L1] = (double)fin[0].hi + (double)fin[0].lo;
+    a.stats[SERBF_STAT_ALPHA] = al;
+    a.stats[SERBF_STAT_BETA] = 1.f - al;
 }
 
 // tau_d rounded up to float: |w| >= taud decides as in double.
@@ -116,26 +118,18 @@ __device__ __forceinline__ float tau_d_float(double tau_d) {
     return t;
 }
 
-// The inputs of parameter (r, j): value, gradient, Adam moments.
-struct AdamIn {
-    float pv, gr, m, v;
-};
-__device__ __forceinline__ AdamIn adam_load(const StepArgs &a, int r, int j) {
-    const int64_t q = (int64_t)r * a.cap + j;
-    return AdamIn{a.p[q], a.grad[q], a.am[q], a.av[q]};
-}
-
 // Combined gradient of Eq. grad (App. A) and the Adam update of parameter
 // (r, j); returns 1 when it is a weight that stays at or above tau_d (b_f).
-__device__ __forceinline__ float adam_apply(const StepArgs &a, int r, int j, const AdamIn &in, const float (&sc)[4],
-                                            float lr, float taud) {
+__device__ __forceinline__ float adam_param(const StepArgs &a, int r, int j, const float (&sc)[4], float lr,
+                                            float taud) {
     const float b1 = (float)a.c.beta1, b2 = (float)a.c.beta2, eps = (float)a.c.adam_eps;
     const int64_t q = (int64_t)r * a.cap + j;
-    float g = sc[0] * in.gr;
-    if (r == PW) g = fmaf(sc[1], sgnf(in.pv), g);
-    const float mo = fmaf(b1, in.m, (1.f - b1) * g);
-    const float vo = fmaf(b2, in.v, (1.f - b2) * g * g);
-    const float pn = in.pv - lr * (mo / sc[2]) / (sqrtf(vo / sc[3]) + eps);
+    const float pv = a.p[q];
+    float g = sc[0] * a.grad[q];
+    if (r == PW) g = fmaf(sc[1], sgnf(pv), g);
+    const float mo = fmaf(b1, a.am[q], (1.f - b1) * g);
+    const float vo = fmaf(b2, a.av[q], (1.f - b2) * g * g);
+    const float pn = pv - lr * (mo / sc[2]) / (sqrtf(vo / sc[3]) + eps);
     a.am[q] = mo;
     a.av[q] = vo;
     a.p[q] = pn;
@@ -148,8 +142,7 @@ __device__ __forceinline__ float adam_apply(const StepArgs &a, int r, int j, con
 // e < T^e), Eq. l1_activate (population std of the last k^l2 L2 values <
 // tau^l2), Eq. add_activate (range of the last k^l1 values of b_f < tau^l1),
 // the L2-only phase with a cosine learning rate from T^e.
-__device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float alpha, float beta, double l1,
-                           int lane) {
+__device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float alpha, float beta, int lane) {
     // per step: Adam counter, alpha/beta, the epoch's L2 sum; the gates only
     // after the epoch's last step (every step when epoch_steps <= 1)
     const int steps = a.c.epoch_steps > 1 ? a.c.epoch_steps : 1;
@@ -164,7 +157,7 @@ __device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float 
             st.beta = beta;
             st.adam_t = st.adam_t + 1;
             a.stats[SERBF_STAT_BF] = bf;
-            a.stats[SERBF_STAT_LOSS] = (float)alpha * (float)l2_step + (float)beta * (float)l1;
+            a.stats[SERBF_STAT_LOSS] = (float)alpha * (float)l2_step + (float)beta * (float)a.stats[SERBF_STAT_L1];
         }
         return;
     }
@@ -246,18 +239,30 @@ __device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float 
         st.lr = lr_next;
         st.epoch = e;
         a.stats[SERBF_STAT_BF] = bf;
-        a.stats[SERBF_STAT_LOSS] = (float)alpha * (float)l2_step + (float)beta * (float)l1;
+        a.stats[SERBF_STAT_LOSS] = (float)alpha * (float)l2_step + (float)beta * (float)a.stats[SERBF_STAT_L1];
     }
 }
 
-// ---------------------------------------------------------------- the update
-// Stage 1 (a thread per kernel): per-block float-float sums of the three
-// Eq. 3-21 terms; block 0 also copies the state's scalars that stage 2 needs,
-// so that in stage 2 only the block that rewrites the state reads it.
+// The epoch tail (warp 0) on a shared-memory copy of the state, written back.
+__device__ void finish_step(const StepArgs &a, double bf, const float (&sc)[4], uint32_t *s_words) {
+    const uint32_t *gw = reinterpret_cast<const uint32_t *>(a.st);
+    for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) s_words[k] = gw[k];
+    __syncthreads();
+    serbf_state &st = *reinterpret_cast<serbf_state *>(s_words);
+    if (threadIdx.x < 32) epoch_tail(a, st, bf, sc[0], sc[1], threadIdx.x);
+    __syncthreads();
+    uint32_t *gwo = reinterpret_cast<uint32_t *>(a.st);
+    for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) gwo[k] = s_words[k];
+}
+
+// ---------------------------------------------------------------- grid path
+// Stage 1 (one thread per kernel, many blocks): the sums of alpha_terms; the
+// last block turns them into alpha, beta and the Adam bias corrections.
 __global__ void __launch_bounds__(kStepThreads) k_step_alpha(StepArgs a) {
     pdl_wait();
     pdl_trigger();
     __shared__ ff sh3[33][3];
+    __shared__ bool s_last;
     const int m = *a.m;
     const bool use_l1 = a.st->l1_optim && (a.stats[SERBF_STAT_MAXE] < a.c.tau_m);
     float part[3] = {0.f, 0.f, 0.f};
@@ -271,82 +276,58 @@ __global__ void __launch_bounds__(kStepThreads) k_step_alpha(StepArgs a) {
             o[2 * k] = tot[k].hi;
             o[2 * k + 1] = tot[k].lo;
         }
-        if (blockIdx.x == 0) {
-            a.scal[0] = use_l1 ? 1.0 : 0.0;
-            a.scal[1] = (double)(a.st->adam_t + 1);
-            a.scal[2] = (double)a.st->lr;
-        }
+        __threadfence();
+        s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
     }
-}
-
-// Stage 2, grid (stage-1 blocks, ten parameter rows): every block sums the
-// stage-1 partials in block order (so all get the same alpha and beta), then
-// updates its 256 kernels of its row.  The weight row belongs to block
-// (0, PW) alone: it updates every weight (which also gives b_f, the count of
-// weights that stay at or above tau_d), writes the step's stats and runs the
-// epoch tail on a shared-memory copy of the state.  No block waits for
-// another.
-__global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
-    pdl_wait();
-    pdl_trigger();
-    __shared__ ff sh3[33][3];
-    __shared__ ff sh1[33][1];
-    __shared__ __align__(8) uint32_t s_words[kStateWords];
-    const int r = blockIdx.y;
-    if (r == PW && blockIdx.x != 0) return;
-    const bool owner = r == PW;
-    if (owner) {
-        const uint32_t *gw = reinterpret_cast<const uint32_t *>(a.st);
-        for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) s_words[k] = gw[k];
-    }
-    const int m = *a.m;
-    const unsigned nb1 = gridDim.x;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
     ff acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    for (unsigned b = threadIdx.x; b < nb1; b += blockDim.x)
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
         for (int k = 0; k < 3; ++k)
             acc[k] = ff_add(acc[k], ff{__ldcg(a.part + 6 * b + 2 * k), __ldcg(a.part + 6 * b + 2 * k + 1)});
     ff fin[3];
     block_sums_ff3(acc, sh3, fin);
-    const bool use_l1 = __ldcg(a.scal) != 0.0;
-    const float t = (float)__ldcg(a.scal + 1), lr = (float)__ldcg(a.scal + 2);
-    float sc[4];
-    alpha_scalars(a, use_l1, fin, t, sc);
-    const float taud = tau_d_float(a.c.tau_d);
-    if (!owner) {
-        const int j = blockIdx.x * blockDim.x + threadIdx.x;
-        if (j < m) adam_apply(a, r, j, adam_load(a, r, j), sc, lr, taud);
-        return;
-    }
-    // the weight row, kOwnerBatch weights per thread per round: all loads of
-    // a round are issued before its stores
-    float cnt = 0.f;
-    for (int j0 = 0; j0 < m; j0 += kStepThreads * kOwnerBatch) {
-        AdamIn in[kOwnerBatch];
-#pragma unroll
-        for (int u = 0; u < kOwnerBatch; ++u) {
-            const int j = j0 + u * kStepThreads + threadIdx.x;
-            if (j < m) in[u] = adam_load(a, PW, j);
-        }
-#pragma unroll
-        for (int u = 0; u < kOwnerBatch; ++u) {
-            const int j = j0 + u * kStepThreads + threadIdx.x;
-            if (j < m) cnt += adam_apply(a, PW, j, in[u], sc, lr, taud);
-        }
-    }
-    float cc[1] = {cnt};
-    ff tot[1];
-    block_sums_ff<1>(cc, sh1, tot);
-    const double l1 = (double)fin[0].hi + (double)fin[0].lo;
     if (threadIdx.x == 0) {
-        a.stats[SERBF_STAT_L1] = l1;
-        a.stats[SERBF_STAT_ALPHA] = sc[0];
-        a.stats[SERBF_STAT_BETA] = sc[1];
+        float sc[4];
+        alpha_finish(a, use_l1, fin, sc);
+        for (int k = 0; k < 4; ++k) a.scal[k] = sc[k];
+        *a.counter = 0u;
     }
-    serbf_state &st = *reinterpret_cast<serbf_state *>(s_words);
-    if (threadIdx.x < 32) epoch_tail(a, st, (double)tot[0].hi + tot[0].lo, sc[0], sc[1], l1, threadIdx.x);
+}
+
+// Stage 2 (one thread per parameter, many blocks): adam_param; then the last
+// block runs the epoch tail.
+__global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ ff sh1[33][1];
+    __shared__ bool s_last;
+    __shared__ __align__(8) uint32_t s_words[kStateWords];
+    const int m = *a.m;
+    const int r = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+    const float sc[4] = {(float)a.scal[0], (float)a.scal[1], (float)a.scal[2], (float)a.scal[3]};
+    const float lr = (float)a.st->lr, taud = tau_d_float(a.c.tau_d);
+    float bfc[1] = {0.f};
+    if (j < m) bfc[0] = adam_param(a, r, j, sc, lr, taud);
+    ff tot[1];
+    block_sums_ff<1>(bfc, sh1, tot);
+    const unsigned nblocks = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0) {
+        a.part[bid] = tot[0].hi;
+        __threadfence();
+        s_last = atomicAdd(a.counter + 1, 1u) == nblocks - 1;
+    }
     __syncthreads();
-    uint32_t *gwo = reinterpret_cast<uint32_t *>(a.st);
-    for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) gwo[k] = s_words[k];
+    if (!s_last) return;
+    __threadfence();
+    // the last block: b_f, then the epoch tail
+    float cnt = 0.f;
+    for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) cnt += __ldcg(a.part + b);
+    float cc[1] = {cnt};
+    block_sums_ff<1>(cc, sh1, tot);
+    finish_step(a, (double)tot[0].hi + tot[0].lo, sc, s_words);
+    if (threadIdx.x == 0) a.counter[1] = 0u;
 }
 
 // Eq. 3-27: stable compaction of the kernels with |w| >= tau_d.
@@ -409,7 +390,8 @@ extern "C" int serbf_step(serbf_params *prm, const float *grad, float *adam_m, f
     if (cfg->k_l2 < 1 || cfg->k_l2 > 64 || cfg->k_l1 < 1 || cfg->k_l1 > 256) return SERBF_EINVAL;
     if (!(cfg->lr >= 0.0) || !(cfg->beta1 >= 0.0 && cfg->beta1 < 1.0) || !(cfg->beta2 >= 0.0 && cfg->beta2 < 1.0))
         return SERBF_EINVAL;
-    StepArgs a{prm->p, prm->m, prm->cap, grad, adam_m, adam_v, st_dev, stats, *cfg, ws->step_part, ws->step_scal};
+    StepArgs a{prm->p, prm->m, prm->cap, grad, adam_m, adam_v, st_dev, stats, *cfg,
+               ws->step_part, ws->step_scal, ws->counters + 2};
     cudaStream_t s = (cudaStream_t)stream;
     const unsigned nb = (unsigned)((prm->cap + kStepThreads - 1) / kStepThreads);
     launch_pdl(k_step_alpha, dim3(nb), dim3(kStepThreads), 0, s, a);
