@@ -416,11 +416,18 @@ __device__ __forceinline__ long long to_fix36(float v) {
     return (b >> 31) ? -r : r;
 }
 
-// Lane = kernel q[(head + lane) % 64] for lane < cnt; all nz points.
+// A batch of cnt <= 32 kernels from queue slot head: all nz points of the
+// item against each kernel.  A short batch spreads each kernel over
+// L = 2, 4 or 8 neighbouring lanes (cnt <= 16, 8, 4) that take every L-th
+// point pair; their moments are combined with xor shuffles within the group
+// (a fixed order for a given cnt) before the atomics, so short batches do
+// not leave most lanes idle.
 __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *q, int head, int cnt,
                                               const NzPoints &nz, int nc0, int nc1, int lane, uint32_t &pairs) {
-    if (lane >= cnt) return;
-    const uint32_t j = q[(head + lane) & (kQueue - 1)];
+    const int sh = cnt > 16 ? 0 : (cnt > 8 ? 1 : (cnt > 4 ? 2 : 3));
+    const int L = 1 << sh, kl = lane >> sh, sub = lane & (L - 1);
+    const bool act = kl < cnt;  // whole groups of L lanes are inactive together
+    const uint32_t j = q[(head + (act ? kl : 0)) & (kQueue - 1)];
     const float4 k0 = a.kbwd[4 * j], k1 = a.kbwd[4 * j + 1], k2 = a.kbwd[4 * j + 2], k3 = a.kbwd[4 * j + 3];
     const f2 cx = f2_dup(k0.x), cy = f2_dup(k0.y), cz = f2_dup(k0.z);
     const f2 r11 = f2_dup(k1.x), r12 = f2_dup(k1.y), r13 = f2_dup(k1.z), e1 = f2_dup(k1.w);
@@ -432,9 +439,9 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
     uint32_t np = 0;
 #pragma unroll 1
     for (int seg = 0; seg < 2; ++seg) {
-        const int base = seg ? kTile : 0, cntp = ((seg ? nc1 : nc0) + 1) >> 1;
+        const int base = seg ? kTile : 0, cntp = act ? ((seg ? nc1 : nc0) + 1) >> 1 : 0;
 #pragma unroll 2
-        for (int pp = 0; pp < cntp; ++pp) {
+        for (int pp = sub; pp < cntp; pp += L) {
             const int i = base + 2 * pp;
             const f2 px = *reinterpret_cast<const f2 *>(&nz.x[i]), py = *reinterpret_cast<const f2 *>(&nz.y[i]);
             const f2 pz = *reinterpret_cast<const f2 *>(&nz.z[i]), pe = *reinterpret_cast<const f2 *>(&nz.e[i]);
@@ -468,17 +475,24 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
             acc[9] = f2_fma(su3, u3, acc[9]);
         }
     }
-    if (np) {
+    float v[10];
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        float lo, hi;
+        f2_unpack(acc[r], lo, hi);
+        v[r] = lo + hi;
+    }
+    for (int o = 1; o < L; o <<= 1) {
+#pragma unroll
+        for (int r = 0; r < 10; ++r) v[r] += __shfl_xor_sync(0xffffffffu, v[r], o);
+    }
+    if (act && sub == 0) {
         unsigned long long *o = a.adj_fix + 10 * (size_t)j;
 #pragma unroll
-        for (int r = 0; r < 10; ++r) {
-            float lo, hi;
-            f2_unpack(acc[r], lo, hi);
-            const float v = lo + hi;
-            if (v != 0.f) atomicAdd(o + r, (unsigned long long)to_fix36(v));
-        }
-        pairs += np;
+        for (int r = 0; r < 10; ++r)
+            if (v[r] != 0.f) atomicAdd(o + r, (unsigned long long)to_fix36(v[r]));
     }
+    pairs += np;
 }
 
 // One warp's share of an item's adjoint: the kernels this warp found
