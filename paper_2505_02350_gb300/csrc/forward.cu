@@ -423,8 +423,7 @@ __device__ __forceinline__ long long to_fix36(float v) {
 // (a fixed order for a given cnt) before the atomics, so short batches do
 // not leave most lanes idle.
 __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *q, int head, int cnt,
-                                              const NzPoints &nz, int nc0, int nc1, int lane, uint32_t &pairs,
-                                              unsigned long long *stg) {
+                                              const NzPoints &nz, int nc0, int nc1, int lane, uint32_t &pairs) {
     const int sh = cnt > 16 ? 0 : (cnt > 8 ? 1 : (cnt > 4 ? 2 : 3));
     const int L = 1 << sh, kl = lane >> sh, sub = lane & (L - 1);
     const bool act = kl < cnt;  // whole groups of L lanes are inactive together
@@ -487,21 +486,12 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
 #pragma unroll
         for (int r = 0; r < 10; ++r) v[r] += __shfl_xor_sync(0xffffffffu, v[r], o);
     }
-    // the batch's moments in fixed point, staged kernel-major in shared
-    // memory and added with consecutive lanes on consecutive moments: one
-    // atomic instruction then covers the 80-byte rows of about three kernels
-    // instead of one word in each of 32 rows
     if (act && sub == 0) {
+        unsigned long long *o = a.adj_fix + 10 * (size_t)j;
 #pragma unroll
-        for (int r = 0; r < 10; ++r) stg[10 * kl + r] = v[r] != 0.f ? (unsigned long long)to_fix36(v[r]) : 0ull;
+        for (int r = 0; r < 10; ++r)
+            if (v[r] != 0.f) atomicAdd(o + r, (unsigned long long)to_fix36(v[r]));
     }
-    __syncwarp();
-    for (int e = lane; e < 10 * cnt; e += 32) {
-        const unsigned long long val = stg[e];
-        const int k = e / 10;
-        if (val) atomicAdd(a.adj_fix + 10 * (size_t)q[(head + k) & (kQueue - 1)] + (e - 10 * k), val);
-    }
-    __syncwarp();
     pairs += np;
 }
 
@@ -511,8 +501,7 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
 template <int G>
 __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &it, int w, const NzPoints &nz,
                                               int nc0, int nc1, float4 lo, float4 hi, const uint32_t *touch,
-                                              int ntouch, uint32_t *q, unsigned long long *stg, int lane,
-                                              uint32_t &cost) {
+                                              int ntouch, uint32_t *q, int lane, uint32_t &cost) {
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t *lst = a.slist + (size_t)it.sup * a.scap;
     const bool listed = ntouch <= kTouch;
@@ -534,13 +523,13 @@ __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &
         nk += __popc(bal);
         __syncwarp();
         if (qn >= 32) {
-            adjoint_batch(a, q, head, 32, nz, nc0, nc1, lane, pairs, stg);
+            adjoint_batch(a, q, head, 32, nz, nc0, nc1, lane, pairs);
             head = (head + 32) & (kQueue - 1);
             qn -= 32;
             __syncwarp();
         }
     }
-    if (qn > 0) adjoint_batch(a, q, head, qn, nz, nc0, nc1, lane, pairs, stg);
+    if (qn > 0) adjoint_batch(a, q, head, qn, nz, nc0, nc1, lane, pairs);
     __syncwarp();
     const uint32_t tot = redux_add(pairs);
     if (lane == 0 && tot) atomicAdd(a.adj_pairs, (unsigned long long)tot);
@@ -667,7 +656,6 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
     __shared__ int s_nc[2];
     __shared__ float4 s_box[2][2];
     __shared__ uint32_t adjq[ADJ ? G : 1][ADJ ? kQueue : 1];
-    __shared__ unsigned long long adjstg[ADJ ? G : 1][ADJ ? 10 * 32 : 1];
     __shared__ uint32_t touch[ADJ ? G : 1][ADJ ? kTouch : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t mean = a.sched[0];
@@ -711,7 +699,7 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
                 __syncwarp();
                 if (nc0 + nc1 > 0)
                     adjoint_share<1>(a, it, 0, nzl[0], nc0, nc1, box_min(lo0, lo1), box_max(hi0, hi1), touch[0],
-                                     ntouch, adjq[0], adjstg[0], lane, cost);
+                                     ntouch, adjq[0], lane, cost);
                 __syncwarp();
             }
             if (lane == 0) note_cost(a, mean, rec, cost);
@@ -775,8 +763,7 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
                 const float4 lo = nc1 ? (nc0 ? box_min(s_box[0][0], s_box[1][0]) : s_box[1][0]) : s_box[0][0];
                 const float4 hi = nc1 ? (nc0 ? box_max(s_box[0][1], s_box[1][1]) : s_box[1][1]) : s_box[0][1];
                 uint32_t c = 0;
-                adjoint_share<G>(a, it, warp, nzl[0], nc0, nc1, lo, hi, touch[warp], ntouch, adjq[warp], adjstg[warp],
-                                 lane, c);
+                adjoint_share<G>(a, it, warp, nzl[0], nc0, nc1, lo, hi, touch[warp], ntouch, adjq[warp], lane, c);
                 if (lane == 0) red_cost[warp] += c;
             }
             __syncthreads();
