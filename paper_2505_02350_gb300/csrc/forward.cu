@@ -416,21 +416,19 @@ __device__ __forceinline__ long long to_fix36(float v) {
     return (b >> 31) ? -r : r;
 }
 
-// A batch of cnt <= 32 kernels from queue slot head (indices in q, records
-// staged in rc / rr): all nz points of the item against each kernel.  A short batch spreads each kernel over
+// A batch of cnt <= 32 kernels from queue slot head: all nz points of the
+// item against each kernel.  A short batch spreads each kernel over
 // L = 2, 4 or 8 neighbouring lanes (cnt <= 16, 8, 4) that take every L-th
 // point pair; their moments are combined with xor shuffles within the group
 // (a fixed order for a given cnt) before the atomics, so short batches do
 // not leave most lanes idle.
-__device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *q, const float4 *rc,
-                                              const float4 *rr, int head, int cnt, const NzPoints &nz, int nc0,
-                                              int nc1, int lane, uint32_t &pairs) {
+__device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *q, int head, int cnt,
+                                              const NzPoints &nz, int nc0, int nc1, int lane, uint32_t &pairs) {
     const int sh = cnt > 16 ? 0 : (cnt > 8 ? 1 : (cnt > 4 ? 2 : 3));
     const int L = 1 << sh, kl = lane >> sh, sub = lane & (L - 1);
     const bool act = kl < cnt;  // whole groups of L lanes are inactive together
-    const int slot = (head + (act ? kl : 0)) & (kQueue - 1);
-    const uint32_t j = q[slot];
-    const float4 k0 = rc[slot], k1 = rr[3 * slot], k2 = rr[3 * slot + 1], k3 = rr[3 * slot + 2];
+    const uint32_t j = q[(head + (act ? kl : 0)) & (kQueue - 1)];
+    const float4 k0 = a.kbwd[4 * j], k1 = a.kbwd[4 * j + 1], k2 = a.kbwd[4 * j + 2], k3 = a.kbwd[4 * j + 3];
     const f2 cx = f2_dup(k0.x), cy = f2_dup(k0.y), cz = f2_dup(k0.z);
     const f2 r11 = f2_dup(k1.x), r12 = f2_dup(k1.y), r13 = f2_dup(k1.z), e1 = f2_dup(k1.w);
     const f2 r21 = f2_dup(k2.x), r22 = f2_dup(k2.y), r23 = f2_dup(k2.z), e2 = f2_dup(k2.w);
@@ -500,18 +498,10 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
 // One warp's share of an item's adjoint: the kernels this warp found
 // reaching the item box (or, if it found more than kTouch, its candidate
 // chunks of the super cell's list again), filtered against the nz box.
-// The accepted kernels' records are staged in the warp's forward rings,
-// which are free once the item's sums are done: centre and r^2 in rc, the
-// rows of R with their scales in rr.  All four parts of a candidate's record
-// are loaded together before the box test, so a batch waits for no global
-// load.
 template <int G>
 __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &it, int w, const NzPoints &nz,
                                               int nc0, int nc1, float4 lo, float4 hi, const uint32_t *touch,
-                                              int ntouch, uint32_t *q, float *ringP, float *ringF, int lane,
-                                              uint32_t &cost) {
-    float4 *rr = reinterpret_cast<float4 *>(ringP);  // 3 per slot: 64 x 48 B = one ring
-    float4 *rc = reinterpret_cast<float4 *>(ringF);  // 1 per slot
+                                              int ntouch, uint32_t *q, int lane, uint32_t &cost) {
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t *lst = a.slist + (size_t)it.sup * a.scap;
     const bool listed = ntouch <= kTouch;
@@ -523,34 +513,23 @@ __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &
         const bool live = b + lane < L;
         const uint32_t j = live ? (listed ? touch[b + lane] : lst[b + lane]) : 0u;
         bool hit = false;
-        float4 k0, k1, k2, k3;
         if (live) {
-            k0 = a.kbwd[4 * j];
-            k1 = a.kbwd[4 * j + 1];
-            k2 = a.kbwd[4 * j + 2];
-            k3 = a.kbwd[4 * j + 3];
+            const float4 k0 = a.kbwd[4 * j];
             hit = box_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
-        if (hit) {
-            const int slot = (head + qn + __popc(bal & lt)) & (kQueue - 1);
-            q[slot] = j;
-            rc[slot] = k0;
-            rr[3 * slot] = k1;
-            rr[3 * slot + 1] = k2;
-            rr[3 * slot + 2] = k3;
-        }
+        if (hit) q[(head + qn + __popc(bal & lt)) & (kQueue - 1)] = j;
         qn += __popc(bal);
         nk += __popc(bal);
         __syncwarp();
         if (qn >= 32) {
-            adjoint_batch(a, q, rc, rr, head, 32, nz, nc0, nc1, lane, pairs);
+            adjoint_batch(a, q, head, 32, nz, nc0, nc1, lane, pairs);
             head = (head + 32) & (kQueue - 1);
             qn -= 32;
             __syncwarp();
         }
     }
-    if (qn > 0) adjoint_batch(a, q, rc, rr, head, qn, nz, nc0, nc1, lane, pairs);
+    if (qn > 0) adjoint_batch(a, q, head, qn, nz, nc0, nc1, lane, pairs);
     __syncwarp();
     const uint32_t tot = redux_add(pairs);
     if (lane == 0 && tot) atomicAdd(a.adj_pairs, (unsigned long long)tot);
@@ -720,7 +699,7 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
                 __syncwarp();
                 if (nc0 + nc1 > 0)
                     adjoint_share<1>(a, it, 0, nzl[0], nc0, nc1, box_min(lo0, lo1), box_max(hi0, hi1), touch[0],
-                                     ntouch, adjq[0], ringP[0], ringF[0], lane, cost);
+                                     ntouch, adjq[0], lane, cost);
                 __syncwarp();
             }
             if (lane == 0) note_cost(a, mean, rec, cost);
@@ -784,8 +763,7 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
                 const float4 lo = nc1 ? (nc0 ? box_min(s_box[0][0], s_box[1][0]) : s_box[1][0]) : s_box[0][0];
                 const float4 hi = nc1 ? (nc0 ? box_max(s_box[0][1], s_box[1][1]) : s_box[1][1]) : s_box[0][1];
                 uint32_t c = 0;
-                adjoint_share<G>(a, it, warp, nzl[0], nc0, nc1, lo, hi, touch[warp], ntouch, adjq[warp], ringP[warp],
-                                 ringF[warp], lane, c);
+                adjoint_share<G>(a, it, warp, nzl[0], nc0, nc1, lo, hi, touch[warp], ntouch, adjq[warp], lane, c);
                 if (lane == 0) red_cost[warp] += c;
             }
             __syncthreads();
