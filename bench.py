@@ -31,8 +31,13 @@ METRIC = "ERBF fwd+bwd point-kernel pairs/s"
 UNIT = "pairs/s"
 FWD_INSTR_PER_PAIR = 17  # minimum FP32-pipe instructions of one forward pair
 ADJ_INSTR_PER_PAIR = 32  # minimum FP32-pipe instructions of one adjoint pair (recompute + ten moments)
-# class count + order (side stream), rebuild | forward+adjoint, epilogue | 2 step, prune, 3 addition
+# class count + order (side stream), rebuild | forward+adjoint, finish | 2 step, prune, 3 addition
 LAUNCHES_PER_STEP = 11
+# DRAM bytes (read + write) of one launch of k_forward<G, adjoint> plus
+# k_fwd_finish<adjoint>, from one ncu capture of the current kernels on the
+# workload and warp split named (profiles/k_forward_adjoint_c2.md); other
+# workloads report null
+TRAFFIC_BYTES = {("c2", 4): 5295360 + 304128}
 WORKLOADS = {
     "c1": ("sphere |x|-0.5 on 32^3, M=64 isotropic", None),
     "c2": ("torus R=0.5 r=0.2 on 32^3+64^3 union (after 32^3->64^3 refinement), M=512 anisotropic", [32, 64]),
@@ -282,7 +287,7 @@ def run_native(args, ws, rank, local):
         "gpu_launches": LAUNCHES_PER_STEP * K,
         "roofline": {"bound": "alu", "kernel": "k_forward<G, adjoint> + k_fwd_finish<adjoint>", "achieved": achieved / 1e12,
                      "peak": peak_instr / 1e12, "unit": "T FP32-instr/s", "frac": achieved / peak_instr,
-                     "traffic": None, "instr_per_pair": {"forward": FWD_INSTR_PER_PAIR, "adjoint": ADJ_INSTR_PER_PAIR},
+                     "traffic": TRAFFIC_BYTES.get((args.config, pb.cfg.fwd_warps)), "instr_per_pair": {"forward": FWD_INSTR_PER_PAIR, "adjoint": ADJ_INSTR_PER_PAIR},
                      "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (of measured max clock)" % (nsm, sm_mhz),
                      "timing": "CUDA events around the forward graph of the interleaved split steps"},
         "breakdown_ms": {"build_neighbors": statistics.mean(seg[0]), "forward_adjoint": statistics.mean(fwd_ms),
