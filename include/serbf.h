@@ -309,7 +309,8 @@ int serbf_scatter(const float *src, const uint32_t *idx, float *dst, int64_t n, 
  * Eq. 3-19 loss terms: psi[i], mask[i] (1 = in id_all), err[i] = psi - t on
  * id_all and 0 elsewhere; stats[L2], stats[MAXE], stats[COUNT] and
  * stats[PAIRS_FWD] (device doubles, deterministic).  Pair arithmetic in
- * float, loss sums in double.  Uses the lists of the last
+ * float; the loss sums are float-float (about 48 bits), reduced in tile
+ * order after the pair kernel.  Two launches.  Uses the lists of the last
  * serbf_build_neighbors call for these parameters. */
 int serbf_forward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi,
                   float *err, uint8_t *mask, double *stats, serbf_workspace *ws, void *stream);
