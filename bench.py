@@ -367,9 +367,13 @@ def run_batched(args, ws, rank, local):
     }
 
 
-def time_oracle(name, budget_s=12.0, min_steps=1):
+def time_oracle(name, budget_s=12.0, steps=None, warmup=0, total_s=90.0):
     """The FP64 oracle as it stands on the host cores, on the same workload:
-    brute-force neighbour test + forward + App. A gradients per step."""
+    brute-force neighbour test + forward + App. A gradients per step, on a
+    random sample of the points (all kernels).  steps=None: as many steps as
+    fit in budget_s on a sample of at most 2e8 point-kernel tests.  steps=K:
+    `warmup` untimed steps, then exactly K timed ones, on a sample sized so
+    that all of them take about total_s."""
     import oracle
     desc, layers = WORKLOADS[name]
     cfg, lay, P = synth.workload(name, layers=layers)
@@ -384,20 +388,32 @@ def time_oracle(name, budget_s=12.0, min_steps=1):
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
     n = x.size
-    # bounded sample: a random subset of the points, all kernels
-    frac = 1.0 if n * m <= 2e8 else 2e8 / (n * m)
     g = np.random.default_rng(0)
-    idx = np.sort(g.choice(n, int(n * frac), replace=False)) if frac < 1 else np.arange(n)
-    xs, ys, zs, ts = x[idx], y[idx], z[idx], t[idx]
-    steps, pairs, t0 = 0, 0.0, time.perf_counter()
-    while steps < min_steps or time.perf_counter() - t0 < budget_s:
-        psi, err, mask, st = oracle.forward(xs, ys, zs, ts, P64, m)
-        g2, npb = oracle.backward(xs, ys, zs, err, P64, m)
-        pairs += st[4] + npb
-        steps += 1
+
+    def run(idx):
+        psi, err, mask, st = oracle.forward(x[idx], y[idx], z[idx], t[idx], P64, m)
+        _g2, npb = oracle.backward(x[idx], y[idx], z[idx], err, P64, m)
+        return st[4] + npb
+
+    if steps is None:
+        ns = n if n * m <= 2e8 else int(2e8 / m)
+    else:
+        # the time of one step on a small sample sets the sample size
+        nc = min(n, 4096)
+        tc = time.perf_counter()
+        run(np.sort(g.choice(n, nc, replace=False)))
+        per_point = (time.perf_counter() - tc) / nc
+        ns = int(min(n, max(256, total_s / max(steps + warmup, 1) / max(per_point, 1e-9))))
+    idx = np.sort(g.choice(n, ns, replace=False)) if ns < n else np.arange(n)
+    for _ in range(warmup if steps is not None else 0):
+        run(idx)
+    done, pairs, t0 = 0, 0.0, time.perf_counter()
+    while (done < steps) if steps is not None else (done < 1 or time.perf_counter() - t0 < budget_s):
+        pairs += run(idx)
+        done += 1
     dt = time.perf_counter() - t0
-    sample = "%d of %d points (all %d kernels), %d oracle steps" % (idx.size, n, m, steps)
-    return pairs / dt, cores, sample, steps, dt, desc
+    sample = "%d of %d points (all %d kernels), %d timed oracle steps" % (idx.size, n, m, done)
+    return pairs / dt, cores, sample, done, dt, desc
 
 
 def run_reference(args, ws, rank):
@@ -406,9 +422,9 @@ def run_reference(args, ws, rank):
     if args.config == "c5":
         return {"impl": "reference", "unavailable": "c5 is a time-to-fit comparison of two GPU schedules of the same "
                 "kernels; the oracle's own rate is reported on c1-c4"}
-    v, cores, sample, steps, dt, desc = time_oracle(args.config)
+    v, cores, sample, steps, dt, desc = time_oracle(args.config, steps=args.steps, warmup=args.warmup)
     return {
-        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": steps, "warmup": 0,
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": desc, "config": args.config},
