@@ -284,7 +284,9 @@ def run_native(args, ws, rank, local):
                    "timing": "K one-graph steps (value) interleaved with K steps split at the forward (roofline)",
                    "state": "the fit's state after the warm-up, restored before every step (untimed)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 128},
-        "gpu_launches": LAUNCHES_PER_STEP * K,
+        "gpu_launches": 2 * LAUNCHES_PER_STEP * K,
+        "gpu_launches_basis": "%d kernels per step; %d one-graph steps and %d split steps in the timed loop"
+                              % (LAUNCHES_PER_STEP, K, K),
         "roofline": {"bound": "alu", "kernel": "k_forward<G, adjoint> + k_fwd_finish<adjoint>", "achieved": achieved / 1e12,
                      "peak": peak_instr / 1e12, "unit": "T FP32-instr/s", "frac": achieved / peak_instr,
                      "traffic": TRAFFIC_BYTES.get((args.config, pb.cfg.fwd_warps)), "instr_per_pair": {"forward": FWD_INSTR_PER_PAIR, "adjoint": ADJ_INSTR_PER_PAIR},
