@@ -31,8 +31,6 @@ METRIC = "ERBF fwd+bwd point-kernel pairs/s"
 UNIT = "pairs/s"
 FWD_INSTR_PER_PAIR = 17  # minimum FP32-pipe instructions of one forward pair
 ADJ_INSTR_PER_PAIR = 32  # minimum FP32-pipe instructions of one adjoint pair (recompute + ten moments)
-# class count + order (side stream), rebuild | forward+adjoint, finish | 2 step, prune, 3 addition
-LAUNCHES_PER_STEP = 11
 # DRAM bytes (read + write) of one launch of k_forward<G, adjoint> plus
 # k_fwd_finish<adjoint>, from one ncu capture of the current kernels on the
 # workload and warp split named (profiles/k_forward_adjoint_c2.md); other
@@ -284,9 +282,9 @@ def run_native(args, ws, rank, local):
                    "timing": "K one-graph steps (value) interleaved with K steps split at the forward (roofline)",
                    "state": "the fit's state after the warm-up, restored before every step (untimed)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 128},
-        "gpu_launches": 2 * LAUNCHES_PER_STEP * K,
+        "gpu_launches": 2 * pb.launches_per_epoch() * K,
         "gpu_launches_basis": "%d kernels per step; %d one-graph steps and %d split steps in the timed loop"
-                              % (LAUNCHES_PER_STEP, K, K),
+                              % (pb.launches_per_epoch(), K, K),
         "roofline": {"bound": "alu", "kernel": "k_forward<G, adjoint> + k_fwd_finish<adjoint>", "achieved": achieved / 1e12,
                      "peak": peak_instr / 1e12, "unit": "T FP32-instr/s", "frac": achieved / peak_instr,
                      "traffic": TRAFFIC_BYTES.get((args.config, pb.cfg.fwd_warps)), "instr_per_pair": {"forward": FWD_INSTR_PER_PAIR, "adjoint": ADJ_INSTR_PER_PAIR},

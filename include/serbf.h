@@ -93,7 +93,11 @@ typedef struct {
     int32_t epoch_steps; /* optimiser steps per epoch: 1 = full batch (default);
                             n > 1: mini-batches, the epoch tail runs every n-th step
                             on the sum of the n batch L2 values */
-    int32_t reserved[1];
+    int32_t rebuild_levels; /* how serbf_build_neighbors forms the candidate list of each super
+                               cell: 1 = tests every kernel; 2 = lists the kernels of each block of
+                               2 x 2 x 2 super cells first and filters that list (the same lists,
+                               less work when there are many super cells and kernels); 0 = chosen
+                               from the problem size (default) */
 } serbf_config;
 
 /* Optimiser state of Algorithm 3; lives in DEVICE memory (sizeof bytes). */

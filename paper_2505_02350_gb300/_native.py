@@ -36,7 +36,7 @@ class Config(C.Structure):
                 ("adam_eps", C.c_double), ("topk_frac", C.c_double), ("add_radius", C.c_double),
                 ("dbar_min", C.c_double), ("k_l1", C.c_int32), ("k_l2", C.c_int32), ("T_e", C.c_int32),
                 ("M_e", C.c_int32), ("kahan", C.c_int32), ("fwd_warps", C.c_int32),
-                ("epoch_steps", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("epoch_steps", C.c_int32), ("rebuild_levels", C.c_int32)]
 
 
 class State(C.Structure):

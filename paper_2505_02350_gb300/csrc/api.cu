@@ -73,6 +73,11 @@ void carve(Carver &c, serbf_workspace *w, const serbf_ws_sizes *s) {
     w->kbwd = c.take<float4>(4 * K);
     w->sup_list = c.take<uint32_t>(S * (int64_t)s->super_cap);
     w->sup_cnt = c.take<uint32_t>(S);
+    // balanced grids have about S / 8 blocks of 2 x 2 x 2 super cells; flat
+    // ones more, and those rebuild in one level
+    w->max_coarse = S / 4 + 16;
+    w->crs_list = c.take<uint32_t>(w->max_coarse * (int64_t)s->super_cap);
+    w->crs_cnt = c.take<uint32_t>(w->max_coarse);
     w->fwd_part = c.take<FwdPart>(T + 1);
     w->fwd_gpart = c.take<FwdPart>(T / kFwdGroup + 2);
     w->bwd_pairs = c.take<unsigned long long>(K);

@@ -94,6 +94,8 @@ struct serbf_workspace {
     float4 *kbwd;  // 4 per kernel
     // candidate lists (ascending kernel index) per super cell
     uint32_t *sup_list, *sup_cnt;
+    uint32_t *crs_list, *crs_cnt;  // lists of blocks of 2 x 2 x 2 super cells (two-level rebuild)
+    int64_t max_coarse;            // blocks the coarse lists have room for
     // reductions
     serbf::FwdPart *fwd_part;     // max_tiles
     serbf::FwdPart *fwd_gpart;    // max_tiles / kFwdGroup + 1

@@ -175,6 +175,115 @@ __global__ void __launch_bounds__(256) k_rebuild(const float *p, int cap, const 
     }
 }
 
+// Two-level rebuild, for many super cells and kernels.  First launch: blocks
+// [0, ncoarse) list, per block of 2 x 2 x 2 super cells, every kernel whose
+// support may reach the union of their boxes (as k_rebuild does per super
+// cell); the remaining blocks write the per-kernel records.
+__global__ void __launch_bounds__(256) k_coarse_lists(const float *p, int cap, const int32_t *m_dev, float nle,
+                                                      float4 *kfwd, float4 *kbwd, const float4 *slo,
+                                                      const float4 *shi, int nsx, int nsy, int nsz, int ncoarse,
+                                                      uint32_t *list, uint32_t *cnt, int scap) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ uint32_t tmp[33];
+    __shared__ float4 s_lo, s_hi;
+    const int m = *m_dev;
+    const int c = blockIdx.x;
+    if (c >= ncoarse) {
+        prep_kernels(p, cap, m, nle, kfwd, kbwd, (c - ncoarse) * blockDim.x + threadIdx.x,
+                     (gridDim.x - ncoarse) * blockDim.x);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        const int ncx = (nsx + 1) >> 1, ncy = (nsy + 1) >> 1;
+        const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
+        float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f), hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int sx = 2 * cx + dx, sy = 2 * cy + dy, sz = 2 * cz + dz;
+                    if (sx >= nsx || sy >= nsy || sz >= nsz) continue;
+                    const int sc = (sz * nsy + sy) * nsx + sx;
+                    const float4 a = slo[sc], b = shi[sc];
+                    lo = make_float4(fminf(lo.x, a.x), fminf(lo.y, a.y), fminf(lo.z, a.z), 0.f);
+                    hi = make_float4(fmaxf(hi.x, b.x), fmaxf(hi.y, b.y), fmaxf(hi.z, b.z), 0.f);
+                }
+        s_lo = lo;
+        s_hi = hi;
+    }
+    __syncthreads();
+    const float4 lo = s_lo, hi = s_hi;
+    if (!(lo.x <= hi.x)) {
+        if (threadIdx.x == 0) cnt[c] = 0;
+        return;
+    }
+    uint32_t count = 0;
+    uint32_t *out = list + (size_t)c * scap;
+    for (int j0 = 0; j0 < m; j0 += 256) {
+        const int j = j0 + threadIdx.x;
+        uint32_t hit = 0;
+        if (j < m) {
+            const float r2 = support_r2(p[PD1 * cap + j], p[PD2 * cap + j], p[PD3 * cap + j], nle);
+            hit = box_d2(p[PCX * cap + j], p[PCY * cap + j], p[PCZ * cap + j], lo, hi) < r2;
+        }
+        uint32_t tot;
+        const uint32_t off = block_exscan(hit, tmp, &tot);
+        if (hit && count + off < (uint32_t)scap) out[count + off] = (uint32_t)j;
+        count += tot;
+    }
+    if (threadIdx.x == 0) cnt[c] = count;
+}
+
+// Second launch: each super cell keeps the kernels of its block's list that
+// reach its own box, with the centre and r2 of the records (the values
+// k_rebuild computes), so the lists equal the one-level ones: a kernel that
+// reaches a super cell's box reaches the block's box, which contains it.  A
+// block list that overflowed is not used: its super cells test every kernel.
+__global__ void __launch_bounds__(256) k_fine_lists(const int32_t *m_dev, const float4 *kfwd, const float4 *slo,
+                                                    const float4 *shi, int nsx, int nsy, int nsuper,
+                                                    const uint32_t *clist, const uint32_t *ccnt, uint32_t *list,
+                                                    uint32_t *cnt, int scap, int32_t *status, long long *needed) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ uint32_t tmp[33];
+    const int s = blockIdx.x;
+    if (s >= nsuper) return;
+    const float4 lo = slo[s], hi = shi[s];
+    if (!(lo.x <= hi.x)) {
+        if (threadIdx.x == 0) cnt[s] = 0;
+        return;
+    }
+    const int sx = s % nsx, sy = (s / nsx) % nsy, sz = s / (nsx * nsy);
+    const int ncx = (nsx + 1) >> 1, ncy = (nsy + 1) >> 1;
+    const int c = ((sz >> 1) * ncy + (sy >> 1)) * ncx + (sx >> 1);
+    const uint32_t cc = ccnt[c];
+    const bool whole = cc > (uint32_t)scap;  // the block's list overflowed
+    const int L = whole ? *m_dev : (int)cc;
+    const uint32_t *src = clist + (size_t)c * scap;
+    uint32_t count = 0;
+    uint32_t *out = list + (size_t)s * scap;
+    for (int q0 = 0; q0 < L; q0 += 256) {
+        const int q = q0 + threadIdx.x;
+        uint32_t hit = 0, j = 0;
+        if (q < L) {
+            j = whole ? (uint32_t)q : src[q];
+            const float4 k = kfwd[3 * j];
+            hit = box_d2(k.x, k.y, k.z, lo, hi) < k.w;
+        }
+        uint32_t tot;
+        const uint32_t off = block_exscan(hit, tmp, &tot);
+        if (hit && count + off < (uint32_t)scap) out[count + off] = j;
+        count += tot;
+    }
+    if (threadIdx.x == 0) {
+        cnt[s] = count;
+        if (count > (uint32_t)scap) {
+            atomicOr(status, SERBF_FLAG_SUPER_LIST);
+            atomicMax(needed + 0, (long long)count);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- point-major CSR
 // One warp per tile; lanes are points.  The super cell's list is walked in
 // ascending kernel order (entries whose support misses the tile box are
@@ -249,6 +358,13 @@ __global__ void k_zero_i64(int64_t *a, int64_t n) {
 
 bool ws_ok(const serbf_workspace *ws) { return ws && ws->magic == kMagic && ws->binned; }
 
+// Two levels when asked, or by default once super cells x kernel capacity
+// reaches 2^22 box tests (below that the extra launch costs more than the
+// tests it saves).
+bool rebuild_two_level(int levels, int64_t nsuper, int cap) {
+    return levels == 2 || (levels == 0 && nsuper * (int64_t)cap >= (int64_t)1 << 22);
+}
+
 }  // namespace
 
 namespace serbf {
@@ -261,6 +377,7 @@ extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params
     if (!prm->p || !prm->m || prm->cap < 1 || prm->cap > ws->sz.max_kernels) return SERBF_EINVAL;
     if (pts->n != ws->npoints || (pts->n > 0 && (!pts->x || !pts->y || !pts->z))) return SERBF_EINVAL;
     if (!(cfg->eps > 0.0 && cfg->eps < 1.0)) return SERBF_EINVAL;
+    if (cfg->rebuild_levels < 0 || cfg->rebuild_levels > 2) return SERBF_EINVAL;
     if (kmajor && (!kmajor->rowptr || (kmajor->cap > 0 && !kmajor->col))) return SERBF_EINVAL;
     if (pmajor && (!pmajor->rowptr || (pmajor->cap > 0 && !pmajor->col))) return SERBF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -279,10 +396,23 @@ extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params
     {
         const float nle = (float)(-log(cfg->eps));
         const int prep_blocks = (prm->cap + 255) / 256;
-        launch_pdl(k_rebuild, dim3(ws->nsuper + prep_blocks), dim3(256), 0, s, (const float *)prm->p, prm->cap,
-                   (const int32_t *)prm->m, nle, ws->kfwd, ws->kbwd, (const float4 *)ws->sup_lo,
-                   (const float4 *)ws->sup_hi, ws->nsuper, ws->sup_list, ws->sup_cnt, ws->sz.super_cap, ws->status,
-                   ws->needed);
+        const int nsx = ws->ns[0], nsy = ws->ns[1], nsz = ws->ns[2];
+        const int64_t ncoarse = (int64_t)((nsx + 1) / 2) * ((nsy + 1) / 2) * ((nsz + 1) / 2);
+        if (rebuild_two_level(cfg->rebuild_levels, ws->nsuper, prm->cap) && ncoarse <= ws->max_coarse) {
+            launch_pdl(k_coarse_lists, dim3((unsigned)(ncoarse + prep_blocks)), dim3(256), 0, s,
+                       (const float *)prm->p, prm->cap, (const int32_t *)prm->m, nle, ws->kfwd, ws->kbwd,
+                       (const float4 *)ws->sup_lo, (const float4 *)ws->sup_hi, nsx, nsy, nsz, (int)ncoarse,
+                       ws->crs_list, ws->crs_cnt, ws->sz.super_cap);
+            launch_pdl(k_fine_lists, dim3(ws->nsuper), dim3(256), 0, s, (const int32_t *)prm->m,
+                       (const float4 *)ws->kfwd, (const float4 *)ws->sup_lo, (const float4 *)ws->sup_hi, nsx, nsy,
+                       ws->nsuper, (const uint32_t *)ws->crs_list, (const uint32_t *)ws->crs_cnt, ws->sup_list,
+                       ws->sup_cnt, ws->sz.super_cap, ws->status, ws->needed);
+        } else {
+            launch_pdl(k_rebuild, dim3(ws->nsuper + prep_blocks), dim3(256), 0, s, (const float *)prm->p, prm->cap,
+                       (const int32_t *)prm->m, nle, ws->kfwd, ws->kbwd, (const float4 *)ws->sup_lo,
+                       (const float4 *)ws->sup_hi, ws->nsuper, ws->sup_list, ws->sup_cnt, ws->sz.super_cap,
+                       ws->status, ws->needed);
+        }
     }
     int rc = SERBF_OK;
     SERBF_CHECK_LAUNCH();

@@ -215,6 +215,21 @@ class Problem:
         self.cfg.fwd_warps = min(times, key=times.get)
         return times
 
+    def launches_per_epoch(self):
+        """Kernel launches of one fused full-batch epoch: item order (2, side
+        stream), rebuild (1, or 2 when the library builds the candidate lists
+        in two levels: cfg.rebuild_levels == 2, or 0 with super cells x
+        kernel capacity >= 2^22 on a grid whose blocks of 2 x 2 x 2 super
+        cells fit the workspace), forward + finish (2), step (2), deletion
+        (1), addition (3)."""
+        sf = self.sizes.super_factor
+        ns = [(self.grid.n[k] + sf - 1) // sf for k in range(3)]
+        nsuper = ns[0] * ns[1] * ns[2]
+        ncoarse = ((ns[0] + 1) // 2) * ((ns[1] + 1) // 2) * ((ns[2] + 1) // 2)
+        lv = self.cfg.rebuild_levels
+        two = (lv == 2 or (lv == 0 and nsuper * self.cap >= 1 << 22)) and ncoarse <= nsuper // 4 + 16
+        return 11 + (1 if two else 0)
+
     def epoch(self):
         """One Algorithm 3 epoch with the full batch: no host synchronisation."""
         self.build_neighbors()

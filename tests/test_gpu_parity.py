@@ -501,3 +501,72 @@ def test_graph_captured_epochs_match_eager(torch):
     assert m == b.m()
     assert torch.equal(a.p[:, :m], b.p[:, :m])
     assert torch.equal(a.stats[:6], b.stats[:6])
+
+
+# ------------------------------------------------------------------ a3, two-level rebuild
+def _list_lengths(pb):
+    """Approximate candidate-list lengths per super cell and per block of
+    2 x 2 x 2 super cells, from the binned points on the host (float32 box
+    tests, used only to pick a capacity between the two maxima)."""
+    n, sf = pb.n, pb.sizes.super_factor
+    g = pb.grid
+    x, y, z = (v[:n].cpu().numpy() for v in (pb.xb, pb.yb, pb.zb))
+    pts = np.stack([x, y, z], 1)
+    cell = np.clip(np.floor((pts - np.asarray(g.origin, np.float32)) / np.float32(g.h)).astype(np.int64), 0,
+                   np.asarray(g.n) - 1)
+    ns = [(g.n[k] + sf - 1) // sf for k in range(3)]
+    P = host_params(pb)
+    m = pb.m()
+    c = P[0:3, :m].T.astype(np.float32)
+    d2 = (P[3:6, :m].astype(np.float32) ** 2).min(0)
+    r2 = np.float32(-math.log(1e-7)) / d2
+
+    def count(lo, hi):
+        dd = np.maximum(np.maximum(lo - c, 0), c - hi)
+        return int(((dd * dd).sum(1) < r2).sum())
+
+    sup = cell // sf
+    out = {}
+    for level, div in (("super", 1), ("block", 2)):
+        key = sup // div
+        k1 = (key[:, 2] * (ns[1] // div + 2) + key[:, 1]) * (ns[0] // div + 2) + key[:, 0]
+        best = 0
+        for kk in np.unique(k1):
+            sel = pts[k1 == kk]
+            best = max(best, count(sel.min(0), sel.max(0)))
+        out[level] = best
+    return out
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_csr_bitexact_rebuild_levels(torch, orc, levels):
+    pb = problem("c2", layers=[32, 64])
+    pb.cfg.rebuild_levels = levels
+    assert _csr_check(torch, orc, pb) > 1000000
+    _forward_check(torch, orc, pb)
+
+
+def test_two_level_rebuild_with_overflowing_block_lists(torch, orc):
+    """A block list longer than the capacity is not used: its super cells test
+    every kernel, and the lists stay exact."""
+    probe = problem("c2", layers=[32, 64])
+    L = _list_lengths(probe)
+    probe.close()
+    if L["block"] - L["super"] < 8:
+        pytest.skip("block and super-cell lists too close in length: %s" % L)
+    cap = (L["block"] + L["super"]) // 2
+    pb = problem("c2", layers=[32, 64], super_cap=cap)
+    pb.cfg.rebuild_levels = 2
+    _csr_check(torch, orc, pb)
+
+
+def test_two_level_rebuild_tiny_ragged(torch, orc):
+    from paper_2505_02350_gb300 import field
+    x, y, z = synth.grid(23)
+    S = synth.sdf_sphere(x, y, z)
+    P = synth.init_kernels(5, 40, rotate=True, length_range=(0.05, 0.3))
+    pb = field.Problem(x, y, z, S, P, 40, spacing=synth.spacing(23))
+    pb.test_src = (x, y, z, S, np.asarray(P, np.float64))
+    pb.cfg.rebuild_levels = 2
+    _csr_check(torch, orc, pb)
+    _forward_check(torch, orc, pb)
