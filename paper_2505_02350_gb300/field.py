@@ -219,7 +219,7 @@ class Problem:
         """Kernel launches of one fused full-batch epoch: item order (2, side
         stream), rebuild (1, or 2 when the library builds the candidate lists
         in two levels: cfg.rebuild_levels == 2, or 0 with super cells x
-        kernel capacity >= 2^22 on a grid whose blocks of 2 x 2 x 2 super
+        kernel capacity >= 2^25 on a grid whose blocks of 2 x 2 x 2 super
         cells fit the workspace), forward + finish (2), step (2), deletion
         (1), addition (3)."""
         sf = self.sizes.super_factor
@@ -227,7 +227,7 @@ class Problem:
         nsuper = ns[0] * ns[1] * ns[2]
         ncoarse = ((ns[0] + 1) // 2) * ((ns[1] + 1) // 2) * ((ns[2] + 1) // 2)
         lv = self.cfg.rebuild_levels
-        two = (lv == 2 or (lv == 0 and nsuper * self.cap >= 1 << 22)) and ncoarse <= nsuper // 4 + 16
+        two = (lv == 2 or (lv == 0 and nsuper * self.cap >= 1 << 25)) and ncoarse <= nsuper // 4 + 16
         return 11 + (1 if two else 0)
 
     def epoch(self):

@@ -546,18 +546,31 @@ def test_csr_bitexact_rebuild_levels(torch, orc, levels):
     _forward_check(torch, orc, pb)
 
 
+def _small_kernel_problem(**kw):
+    """48^3 sphere samples, 400 small kernels (lengths 0.02-0.06) and super
+    cells of 2^3 cells: lists of blocks of 2 x 2 x 2 super cells are several
+    times longer than the super cells' own."""
+    from paper_2505_02350_gb300 import field
+    x, y, z = synth.grid(48)
+    S = synth.sdf_sphere(x, y, z)
+    P = synth.init_kernels(11, 400, rotate=True, length_range=(0.02, 0.06))
+    pb = field.Problem(x, y, z, S, P, 400, spacing=synth.spacing(48), super_factor=2, **kw)
+    pb.test_src = (x, y, z, S, np.asarray(P, np.float64))
+    return pb
+
+
 def test_two_level_rebuild_with_overflowing_block_lists(torch, orc):
     """A block list longer than the capacity is not used: its super cells test
     every kernel, and the lists stay exact."""
-    probe = problem("c2", layers=[32, 64])
+    probe = _small_kernel_problem()
     L = _list_lengths(probe)
     probe.close()
-    if L["block"] - L["super"] < 8:
-        pytest.skip("block and super-cell lists too close in length: %s" % L)
+    assert L["block"] - L["super"] >= 8, L
     cap = (L["block"] + L["super"]) // 2
-    pb = problem("c2", layers=[32, 64], super_cap=cap)
+    pb = _small_kernel_problem(super_cap=cap)
     pb.cfg.rebuild_levels = 2
     _csr_check(torch, orc, pb)
+    _forward_check(torch, orc, pb)
 
 
 def test_two_level_rebuild_tiny_ragged(torch, orc):
