@@ -225,6 +225,7 @@ extern "C" int serbf_add_kernels(const serbf_points *pts, const float *S_raw, co
                                  serbf_params *prm, float *adam_m, float *adam_v, serbf_state *st_dev,
                                  const double *stats, const serbf_config *cfg, int force, serbf_workspace *ws,
                                  void *stream) {
+    SERBF_TRACE();
     if (!pts || !prm || !cfg || !ws || ws->magic != kMagic || !ws->binned) return SERBF_EINVAL;
     if (pts->n != ws->npoints || !prm->p || !prm->m || prm->cap < 1 || prm->cap > ws->sz.max_kernels)
         return SERBF_EINVAL;

@@ -348,6 +348,7 @@ int serbf_state_init(serbf_state *st_dev, const serbf_config *cfg, void *stream)
 
 int serbf_normalize_sdf(const float *S, float *t, int64_t n, double *mh_dev, serbf_workspace *ws,
                         void *stream) {
+    SERBF_TRACE();
     if (!S || !t || n <= 0 || !ws || ws->magic != kMagic) return SERBF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     int *slot = ws->status + 8;

@@ -250,6 +250,7 @@ __global__ void k_grad_epilogue(const float *p, const int32_t *m_dev, int cap, c
 
 extern "C" int serbf_backward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg,
                               const float *err, float *grad, double *stats, serbf_workspace *ws, void *stream) {
+    SERBF_TRACE();
     if (!pts || !prm || !cfg || !ws || ws->magic != kMagic || !ws->binned) return SERBF_EINVAL;
     if (pts->n != ws->npoints || !prm->p || !prm->m || prm->cap < 1 || prm->cap > ws->sz.max_kernels)
         return SERBF_EINVAL;

@@ -243,6 +243,7 @@ int radix_sort_pairs(uint32_t **k, uint32_t **v, uint32_t **ktmp, uint32_t **vtm
 extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, int64_t n, const serbf_grid *grid,
                                 uint32_t *perm, float *xb, float *yb, float *zb, serbf_workspace *ws,
                                 void *stream) {
+    SERBF_TRACE();
     if (!ws || ws->magic != kMagic || !grid || n < 0) return SERBF_EINVAL;
     if (n > 0 && (!x || !y || !z || !perm || !xb || !yb || !zb)) return SERBF_EINVAL;
     if (n > ws->sz.max_points) return SERBF_EINVAL;
@@ -319,6 +320,7 @@ extern "C" int serbf_refine(float *x_all, float *y_all, float *z_all, float *t_a
                             const float *x_new, const float *y_new, const float *z_new, const float *t_new,
                             const float *s_new, int64_t n_new, const serbf_grid *grid, uint32_t *perm, float *xb,
                             float *yb, float *zb, float *tb, float *sb, serbf_workspace *ws, void *stream) {
+    SERBF_TRACE();
     if (!ws || ws->magic != kMagic || n_old < 0 || n_new < 0) return SERBF_EINVAL;
     if (!x_all || !y_all || !z_all || !t_all || !s_all || !tb || !sb) return SERBF_EINVAL;
     if (n_new > 0 && (!x_new || !y_new || !z_new || !t_new || !s_new)) return SERBF_EINVAL;

@@ -6,8 +6,18 @@
 #include <stdint.h>
 
 #include "serbf.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace serbf {
+
+// An NVTX range named after a host entry point, for timelines and ncu --nvtx
+// filters; without an attached tool the calls return at once.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+};
+#define SERBF_TRACE() serbf::TraceRange serbf_trace_range_(__func__)
+
 
 constexpr uint64_t kMagic = 0x53455242465753ull;  // "SERBFWS"
 constexpr int kTile = 32;                         // points per forward/backward tile (one warp)

@@ -275,6 +275,7 @@ int blocks_for(int64_t n) {
 
 extern "C" int serbf_marching_tets(const float *f, const int32_t dims[3], const float origin[3], float h, float iso,
                                    float *tri, int64_t cap, int64_t *ntri, int64_t *scratch, void *stream) {
+    SERBF_TRACE();
     if (!f || !dims || !origin || !ntri || !scratch || !(h > 0.f)) return SERBF_EINVAL;
     if (dims[0] < 2 || dims[1] < 2 || dims[2] < 2 || (cap > 0 && !tri)) return SERBF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -296,6 +297,7 @@ extern "C" int serbf_marching_tets(const float *f, const int32_t dims[3], const 
 
 extern "C" int serbf_sample_surface(const float *tri, int64_t ntri, const double *u, int64_t ns, float *pts, float *nrm,
                                     int64_t *scratch, void *stream) {
+    SERBF_TRACE();
     if (!tri || ntri < 1 || !u || ns < 0 || (ns > 0 && (!pts || !nrm)) || !scratch) return SERBF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     k_area_q<<<blocks_for(ntri), 256, 0, s>>>(tri, ntri, scratch);
@@ -313,6 +315,7 @@ extern "C" int serbf_sample_surface(const float *tri, int64_t ntri, const double
 
 extern "C" int serbf_surface_metrics(const float *A, const float *nA, int64_t na, const float *B, const float *nB,
                                      int64_t nb, double out[3], double *scratch, void *stream) {
+    SERBF_TRACE();
     if (!A || !nA || !B || !nB || na < 1 || nb < 1 || !out || !scratch) return SERBF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     double *dA = scratch, *cA = dA + na, *dB = cA + na, *cB = dB + nb, *red = cB + nb;

@@ -986,12 +986,14 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
 
 extern "C" int serbf_forward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi,
                              float *err, uint8_t *mask, double *stats, serbf_workspace *ws, void *stream) {
+    SERBF_TRACE();
     return forward_impl(pts, prm, cfg, psi, err, mask, nullptr, stats, ws, stream);
 }
 
 extern "C" int serbf_forward_backward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg,
                                       float *psi, float *err, uint8_t *mask, float *grad, double *stats,
                                       serbf_workspace *ws, void *stream) {
+    SERBF_TRACE();
     if (!grad) return SERBF_EINVAL;
     return forward_impl(pts, prm, cfg, psi, err, mask, grad, stats, ws, stream);
 }

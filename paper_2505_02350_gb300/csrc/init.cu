@@ -157,6 +157,7 @@ __global__ void k_init_params(const float *x, const float *y, const float *z, co
 
 extern "C" int serbf_init_kernels(const serbf_points *pts, const float *S_raw, double gamma, serbf_params *prm,
                                   int32_t *m_out, serbf_workspace *ws, void *stream) {
+    SERBF_TRACE();
     if (!pts || !prm || !prm->p || !prm->m || prm->cap < 1 || !ws || ws->magic != kMagic || !ws->binned)
         return SERBF_EINVAL;
     if (pts->n != ws->npoints || prm->cap > ws->sz.max_kernels || !(gamma > 0.0 && gamma < 1.0)) return SERBF_EINVAL;

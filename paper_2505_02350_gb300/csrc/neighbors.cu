@@ -374,6 +374,7 @@ namespace serbf {
 extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg,
                                      serbf_csr *kmajor, serbf_csr *pmajor, int64_t *npairs, serbf_workspace *ws,
                                      void *stream) {
+    SERBF_TRACE();
     if (!pts || !prm || !cfg || !ws_ok(ws)) return SERBF_EINVAL;
     if (!prm->p || !prm->m || prm->cap < 1 || prm->cap > ws->sz.max_kernels) return SERBF_EINVAL;
     if (pts->n != ws->npoints || (pts->n > 0 && (!pts->x || !pts->y || !pts->z))) return SERBF_EINVAL;

@@ -384,6 +384,7 @@ __global__ void __launch_bounds__(kStepThreads) k_prune(float *p, float *am, flo
 
 extern "C" int serbf_step(serbf_params *prm, const float *grad, float *adam_m, float *adam_v, serbf_state *st_dev,
                           double *stats, const serbf_config *cfg, serbf_workspace *ws, void *stream) {
+    SERBF_TRACE();
     if (!prm || !prm->p || !prm->m || prm->cap < 1 || !grad || !adam_m || !adam_v || !st_dev || !stats || !cfg)
         return SERBF_EINVAL;
     if (!ws || ws->magic != kMagic || prm->cap > ws->sz.max_kernels) return SERBF_EINVAL;
@@ -402,6 +403,7 @@ extern "C" int serbf_step(serbf_params *prm, const float *grad, float *adam_m, f
 
 extern "C" int serbf_prune(serbf_params *prm, float *adam_m, float *adam_v, serbf_state *st_dev,
                            const serbf_config *cfg, void *stream) {
+    SERBF_TRACE();
     if (!prm || !prm->p || !prm->m || prm->cap < 1 || !adam_m || !adam_v || !st_dev || !cfg) return SERBF_EINVAL;
     launch_pdl(k_prune, dim3(1), dim3(kStepThreads), 0, (cudaStream_t)stream, prm->p, adam_m, adam_v, prm->m, prm->cap, st_dev,
                                                            cfg->tau_d, 0);
