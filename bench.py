@@ -247,15 +247,18 @@ def run_native(args, ws, rank, local):
     # the epoch are ordered on one stream, so the host need not wait between
     # steps; it reads the ring once the last step is done.
     n = pb.n
-    host_pts = torch.stack([pb.xb[:n], pb.yb[:n], pb.zb[:n], pb.tb[:n]]).cpu().pin_memory()
+    host_pts = pb.binned[:4, :n].cpu().pin_memory()
     host_stats = torch.zeros(K, 16, dtype=torch.float64).pin_memory()
-    dev_pts = [pb.xb, pb.yb, pb.zb, pb.tb]
+    # one copy when the rows hold exactly n points (contiguous), else one per row
+    one = n == pb.binned.shape[1]
+    dev_rows = [pb.binned[:4, :n]] if one else [pb.binned[r, :n] for r in range(4)]
+    host_rows = [host_pts] if one else [host_pts[r] for r in range(4)]
     torch.cuda.synchronize()
     te = time.perf_counter()
     for k in range(K):
         pb.restore(snap)
-        for r in range(4):
-            dev_pts[r][:n].copy_(host_pts[r], non_blocking=True)
+        for d, h in zip(dev_rows, host_rows):
+            d.copy_(h, non_blocking=True)
         pb.epoch_graph()
         host_stats[k].copy_(pb.stats, non_blocking=True)
     torch.cuda.synchronize()

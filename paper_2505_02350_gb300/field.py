@@ -73,11 +73,11 @@ class Problem:
         self.s_all[:n] = torch.as_tensor(np.asarray(S, np.float32), device=dev)
         self.mh = torch.zeros(2, dtype=torch.float64, device=dev)
         self.perm = torch.zeros(self.max_points, dtype=torch.int32, device=dev)
-        self.xb = torch.zeros(self.max_points, **f32)
-        self.yb = torch.zeros(self.max_points, **f32)
-        self.zb = torch.zeros(self.max_points, **f32)
-        self.tb = torch.zeros(self.max_points, **f32)
-        self.sb = torch.zeros(self.max_points, **f32)
+        # binned x, y, z, t, S_raw as rows of one block (rows 256-byte
+        # aligned), so that one copy can move the training points of a step
+        stride = -(-self.max_points // 64) * 64
+        self.binned = torch.zeros(5, stride, **f32)
+        self.xb, self.yb, self.zb, self.tb, self.sb = self.binned[:, :self.max_points].unbind(0)
         self.psi = torch.zeros(self.max_points, **f32)
         self.err = torch.zeros(self.max_points, **f32)
         self.mask = torch.zeros(self.max_points, dtype=torch.uint8, device=dev)
