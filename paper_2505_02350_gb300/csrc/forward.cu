@@ -49,7 +49,7 @@ struct FwdArgs {
     uint32_t *exit_count; // blocks that have exited (zero between launches)
 };
 
-constexpr int kTouch = 128;  // kernels remembered per warp and item for the adjoint (more: re-scan the list)
+constexpr int kTouch = 256;  // kernels remembered per warp and item for the adjoint (more: re-scan the list)
 constexpr int kNz = 2 * kTile;
 
 // Two float32 lanes in one 64-bit register: the packed f32x2 arithmetic of
