@@ -121,18 +121,12 @@ __global__ void __launch_bounds__(kAddThreads) k_add_select(const float *E, cons
     if (threadIdx.x == 0) info[1] = (int32_t)ns;
 }
 
-// One warp per selected point: reject it if an id_all point within the
-// radius has a larger |E| (distance in float, same operation order as the
-// support test, <= r2).
-__global__ void k_add_localmax(const float *x, const float *y, const float *z, const float *E,
-                               const uint8_t *mask, const uint32_t *cell_start, serbf_grid g, int sf, int nsx,
-                               int nsy, float r2, int reach, const unsigned long long *sel, const int32_t *info,
-                               uint32_t *keep) {
-    pdl_wait();
-    pdl_trigger();
-    if (!info[0]) return;
-    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (s >= info[1]) return;
+// One selected point s (a warp): keep[s] = 0 if an id_all point within the
+// radius has a larger |E|.
+__device__ __forceinline__ void localmax_one(const float *x, const float *y, const float *z, const float *E,
+                                             const uint8_t *mask, const uint32_t *cell_start, serbf_grid g, int sf,
+                                             int nsx, int nsy, float r2, int reach, const unsigned long long *sel,
+                                             uint32_t *keep, int s, int lane) {
     const uint32_t i = (uint32_t)(sel[s] & 0xffffffffull);
     const float xi = x[i], yi = y[i], zi = z[i], ei = fabsf(E[i]);
     const int kx = cell_axis(xi, g.origin[0], g.h, g.n[0]);
@@ -157,6 +151,22 @@ __global__ void k_add_localmax(const float *x, const float *y, const float *z, c
                 }
             }
     if (lane == 0) keep[s] = !bad;
+}
+
+// Warps over the selected points (grid-stride): reject a point if an id_all
+// point within the radius has a larger |E| (distance in float, same operation
+// order as the support test, <= r2).  One block per SM, so a step without an
+// addition retires few blocks.
+__global__ void k_add_localmax(const float *x, const float *y, const float *z, const float *E,
+                               const uint8_t *mask, const uint32_t *cell_start, serbf_grid g, int sf, int nsx,
+                               int nsy, float r2, int reach, const unsigned long long *sel, const int32_t *info,
+                               uint32_t *keep) {
+    pdl_wait();
+    pdl_trigger();
+    if (!info[0]) return;
+    const int lane = threadIdx.x & 31, nsel = info[1];
+    for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nsel; s += (gridDim.x * blockDim.x) >> 5)
+        localmax_one(x, y, z, E, mask, cell_start, g, sf, nsx, nsy, r2, reach, sel, keep, s, lane);
 }
 
 __global__ void __launch_bounds__(kAddThreads) k_add_append(const float *x, const float *y, const float *z,
@@ -245,7 +255,7 @@ extern "C" int serbf_add_kernels(const serbf_points *pts, const float *S_raw, co
     const float r2 = (float)(cfg->add_radius * cfg->add_radius);
     int reach = (int)ceil(cfg->add_radius / ws->grid.h) + 1;
     if (reach > 1 << 20) reach = 1 << 20;
-    unsigned lm_blocks = (unsigned)((kSelMax * 32 + 255) / 256);
+    const unsigned lm_blocks = (unsigned)(ws->sm_count > 0 ? ws->sm_count : 1);
     launch_pdl(k_add_localmax, dim3(lm_blocks), dim3(256), 0, s, pts->x, pts->y, pts->z, err, mask, ws->cell_start, ws->grid, ws->sf,
                                             ws->ns[0], ws->ns[1], r2, reach, ws->sel_key, ws->add_info,
                                             ws->sel_keep);
