@@ -35,7 +35,7 @@ ADJ_INSTR_PER_PAIR = 32  # minimum FP32-pipe instructions of one adjoint pair (r
 # k_fwd_finish<adjoint>, from one ncu capture of the current kernels on the
 # workload and warp split named (profiles/k_forward_adjoint_c2.md); other
 # workloads report null
-TRAFFIC_BYTES = {("c2", 4): 5295104 + 303616}
+TRAFFIC_BYTES = {("c2", 4): 5296128 + 304128}
 WORKLOADS = {
     "c1": ("sphere |x|-0.5 on 32^3, M=64 isotropic", None),
     "c2": ("torus R=0.5 r=0.2 on 32^3+64^3 union (after 32^3->64^3 refinement), M=512 anisotropic", [32, 64]),
