@@ -349,6 +349,89 @@ def test_adam_matches_torch(orc):
         np.testing.assert_allclose(q, p.detach().numpy(), rtol=1e-13, atol=1e-15)
 
 
+def _line_search_alpha(g2, g1):
+    """argmin over [0, 1] of ||a g2 + (1 - a) g1||^2 by ternary search on the
+    convex objective (no use of the Eq. 3-21 closed form)."""
+    f = lambda a: float(np.sum((a * g2 + (1.0 - a) * g1) ** 2))
+    lo, hi = 0.0, 1.0
+    for _ in range(200):
+        a, b = lo + (hi - lo) / 3.0, hi - (hi - lo) / 3.0
+        if f(a) <= f(b):
+            hi = b
+        else:
+            lo = a
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("gscale", [0.3, 3.0])
+def test_step_with_l1_term_is_adam_on_the_combined_gradient(orc, gscale):
+    """Eq. 3-21 inside the Algorithm 3 step: with l1_optim set and max|E| <
+    tau_m, the update is Adam on alpha g for the centre, axis and angle rows
+    and on alpha g_w + beta sign(w) for the weight row (App. A, Eq. grad),
+    with alpha the minimiser of ||a g2 + (1 - a) g1||^2 over [0, 1] found by
+    a line search here.  Reference: torch.optim.Adam in float64 on those
+    gradients; two steps in a row, so the moments carry over."""
+    torch = pytest.importorskip("torch")
+    g = np.random.default_rng(21)
+    m, cap = 23, 29
+    cfg = orc.default_cfg()
+    st = orc.state_init(cfg)
+    st.l1_optim = 1
+    P = np.zeros((10, cap))
+    P[:, :m] = g.normal(0, 1, (10, m))
+    P[9, :3] = 0.0  # sign(0) = 0: no L1 pull on these weights
+    P[9, 3:6] = -np.abs(P[9, 3:6])
+    mo, v = np.zeros((10, cap)), np.zeros((10, cap))
+    tp = torch.tensor(P[:, :m].copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=cfg.lr0, betas=(cfg.beta1, cfg.beta2), eps=cfg.adam_eps)
+    alphas = []
+    for it in range(2):
+        grad = g.normal(0, gscale, (10, m))
+        w = tp.detach().numpy()[9].copy()
+        g1 = np.sign(w)
+        a_ls = _line_search_alpha(grad[9], g1)
+        assert 0.0 < a_ls < 1.0  # the branch under test mixes both terms
+        orc.step(P, m, grad, mo, v, 1.0, 0.5 * cfg.tau_m, cfg, st)
+        # the flat minimum limits the search to about sqrt(machine eps)
+        assert st.alpha == pytest.approx(a_ls, abs=1e-7)
+        assert st.beta == 1.0 - st.alpha
+        a = st.alpha
+        comb = a * grad
+        comb[9] += (1.0 - a) * g1
+        tp.grad = torch.tensor(comb)
+        opt.step()
+        alphas.append(a)
+        assert st.adam_t == it + 1
+        np.testing.assert_allclose(P[:, :m], tp.detach().numpy(), rtol=1e-9, atol=1e-11)
+        s = opt.state[tp]
+        np.testing.assert_allclose(mo[:, :m], s["exp_avg"].numpy(), rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(v[:, :m], s["exp_avg_sq"].numpy(), rtol=1e-9, atol=1e-14)
+        assert not P[:, m:].any() and not mo[:, m:].any()  # columns past m untouched
+    assert alphas[0] != alphas[1]
+
+
+def test_step_without_the_gate_is_plain_adam(orc):
+    """l1_optim set but max|E| >= tau_m (Eq. l1_activate2 false), and l1_optim
+    off with a small max|E|: alpha = 1, beta = 0, Adam on the raw gradient."""
+    torch = pytest.importorskip("torch")
+    g = np.random.default_rng(22)
+    m = 17
+    cfg = orc.default_cfg()
+    for l1, maxe in ((1, 2.0 * cfg.tau_m), (0, 0.1 * cfg.tau_m)):
+        st = orc.state_init(cfg)
+        st.l1_optim = l1
+        P = g.normal(0, 1, (10, m))
+        mo, v = np.zeros((10, m)), np.zeros((10, m))
+        tp = torch.tensor(P.copy(), dtype=torch.float64, requires_grad=True)
+        opt = torch.optim.Adam([tp], lr=cfg.lr0, betas=(cfg.beta1, cfg.beta2), eps=cfg.adam_eps)
+        grad = g.normal(0, 1, (10, m))
+        tp.grad = torch.tensor(grad)
+        opt.step()
+        orc.step(P, m, grad, mo, v, 1.0, maxe, cfg, st)
+        assert st.alpha == 1.0 and st.beta == 0.0
+        np.testing.assert_allclose(P, tp.detach().numpy(), rtol=1e-12, atol=1e-14)
+
+
 # ---------------------------------------------------------------- Algorithm 3 gates
 def _run_gates(orc, l2_seq, w_seq, cfg, maxE=1.0):
     m = len(w_seq[0])
