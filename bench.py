@@ -2,8 +2,11 @@
 pairs per second for full Algorithm 3 epochs (neighbour rebuild, forward,
 adjoint, optimiser step with gates, deletion and addition checks).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c2|c3|c1|c4]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c4|c3|c2|c1|c5]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the same workload
+
+The default workload is c4, the largest single-GPU field (60 random
+primitives on a 256^3 band + far field, 9.4 M points, M = 16384).
 
 Prints one JSON line on rank 0.  With N > 1 (torchrun) every rank fits its own
 replica of the workload (the path does not shard across GPUs: replicas only,
@@ -31,11 +34,12 @@ METRIC = "ERBF fwd+bwd point-kernel pairs/s"
 UNIT = "pairs/s"
 FWD_INSTR_PER_PAIR = 17  # minimum FP32-pipe instructions of one forward pair
 ADJ_INSTR_PER_PAIR = 32  # minimum FP32-pipe instructions of one adjoint pair (recompute + ten moments)
-# DRAM bytes (read + write) of one launch of k_forward<G, adjoint> plus
-# k_fwd_finish<adjoint>, from one ncu capture of the current kernels on the
-# workload and warp split named (profiles/k_forward_adjoint_c2.md); other
-# workloads report null
-TRAFFIC_BYTES = {("c2", 4): 5296128 + 304128}
+# DRAM bytes (read + write) of one launch of the fused forward + adjoint
+# kernel plus its finishing kernel, from one ncu capture per workload and warp
+# split, valid only for the library version it was taken with (any other
+# version, workload or split reports null)
+TRAFFIC_BYTES = {}  # (library version, workload, warps per item) -> bytes
+DEFAULT_STEPS = {"c1": 3000, "c2": 3000, "c3": 500, "c4": 200, "c5": 100}
 WORKLOADS = {
     "c1": ("sphere |x|-0.5 on 32^3, M=64 isotropic", None),
     "c2": ("torus R=0.5 r=0.2 on 32^3+64^3 union (after 32^3->64^3 refinement), M=512 anisotropic", [32, 64]),
@@ -241,30 +245,39 @@ def run_native(args, ws, rank, local):
     seconds = sum(step_ms) / 1e3
     value, ms_max = aggregate(float(pf.sum() + pbk.sum()), seconds, sum(step_ms) / K)
 
-    # end to end through the public API with host buffers: per step the
-    # training points go host -> device from pinned memory, and the loss terms
-    # come back device -> host into a pinned ring.  Copies, state restore and
-    # the epoch are ordered on one stream, so the host need not wait between
-    # steps; it reads the ring once the last step is done.
+    # end to end through the public API with host buffers: per step the raw
+    # SDF samples of the training points (grid order) go host -> device from
+    # pinned memory, Eq. 3-10 maps them to targets on the device
+    # (serbf_normalize_sdf), serbf_gather puts targets and samples in binned
+    # order, the epoch runs, and the whole parameter block (10 x capacity
+    # floats), the kernel count and the loss terms come back device -> host
+    # into pinned rings.  Copies, state restore and the epoch are ordered on
+    # one stream, so the host need not wait between steps; it reads the
+    # rings once the last step is done.
+    from paper_2505_02350_gb300 import _native as N
     n = pb.n
-    host_pts = pb.binned[:4, :n].cpu().pin_memory()
+    host_S = pb.s_all[:n].cpu().pin_memory()
+    host_p = torch.zeros(K, *pb.p.shape, dtype=torch.float32).pin_memory()
+    host_m = torch.zeros(K, 1, dtype=torch.int32).pin_memory()
     host_stats = torch.zeros(K, 16, dtype=torch.float64).pin_memory()
-    # one copy when the rows hold exactly n points (contiguous), else one per row
-    one = n == pb.binned.shape[1]
-    dev_rows = [pb.binned[:4, :n]] if one else [pb.binned[r, :n] for r in range(4)]
-    host_rows = [host_pts] if one else [host_pts[r] for r in range(4)]
     torch.cuda.synchronize()
     te = time.perf_counter()
     for k in range(K):
         pb.restore(snap)
-        for d, h in zip(dev_rows, host_rows):
-            d.copy_(h, non_blocking=True)
+        pb.s_all[:n].copy_(host_S, non_blocking=True)
+        N.serbf_normalize_sdf(pb.s_all[:n], pb.t_all[:n], pb.mh, pb.ws)
+        N.serbf_gather(pb.t_all, pb.perm[:n], pb.tb, n)
+        N.serbf_gather(pb.s_all, pb.perm[:n], pb.sb, n)
         pb.epoch_graph()
+        host_p[k].copy_(pb.p, non_blocking=True)
+        host_m[k].copy_(pb.m_dev, non_blocking=True)
         host_stats[k].copy_(pb.stats, non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - te
     e2e_pairs = float(host_stats[:, 4].sum() + host_stats[:, 5].sum())
     e2e_value, _ = aggregate(e2e_pairs, e2e_s, 0.0)
+    e2e_h2d = 4 * n
+    e2e_d2h = 4 * pb.p.numel() + 4 + 8 * 16
 
     peaks = load_peaks()
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -285,13 +298,17 @@ def run_native(args, ws, rank, local):
                    "l2_flush": "256 MiB buffer written between timed steps", "parallelism": "replicas",
                    "timing": "K one-graph steps (value) interleaved with K steps split at the forward (roofline)",
                    "state": "the fit's state after the warm-up, restored before every step (untimed)"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 128},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_h2d, "d2h_bytes_per_step": e2e_d2h,
+                "basis": "per step: raw SDF samples host->device, Eq. 3-10 and binned-order gathers on the device, "
+                         "the epoch, then the 10 x %d parameter block, kernel count and loss terms device->host"
+                         % pb.cap},
         "gpu_launches": 2 * pb.launches_per_epoch() * K,
         "gpu_launches_basis": "%d kernels per step; %d one-graph steps and %d split steps in the timed loop"
                               % (pb.launches_per_epoch(), K, K),
         "roofline": {"bound": "alu", "kernel": "k_forward<G, adjoint> + k_fwd_finish<adjoint>", "achieved": achieved / 1e12,
                      "peak": peak_instr / 1e12, "unit": "T FP32-instr/s", "frac": achieved / peak_instr,
-                     "traffic": TRAFFIC_BYTES.get((args.config, pb.cfg.fwd_warps)), "instr_per_pair": {"forward": FWD_INSTR_PER_PAIR, "adjoint": ADJ_INSTR_PER_PAIR},
+                     "traffic": TRAFFIC_BYTES.get((N.version(), args.config, pb.cfg.fwd_warps)),
+                     "instr_per_pair": {"forward": FWD_INSTR_PER_PAIR, "adjoint": ADJ_INSTR_PER_PAIR},
                      "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (of measured max clock)" % (nsm, sm_mhz),
                      "timing": "CUDA events around the forward graph of the interleaved split steps"},
         "breakdown_ms": {"build_neighbors": statistics.mean(seg[0]), "forward_adjoint": statistics.mean(fwd_ms),
@@ -440,15 +457,17 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default per workload)")
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--config", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default="c4", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sf", type=int, default=None, help="cells per super-cell edge (default per workload)")
     ap.add_argument("--fwd-warps", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="warps per forward work item (0: autotune)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS[args.config]
     ws, rank, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, ws, rank)

@@ -55,6 +55,9 @@ extern "C" {
 /* device status flags (bitmask) reported by serbf_status */
 #define SERBF_FLAG_SUPER_LIST 1   /* a super-cell candidate list exceeded super_cap */
 #define SERBF_FLAG_ADD_CAPACITY 4 /* addition truncated at the parameter capacity */
+#define SERBF_FLAG_FIX_RANGE 8    /* serbf_forward_backward: a moment may lie outside the range of its
+                                     64-bit fixed-point accumulator (|moment| >= 2^26 bound); the
+                                     gradients of that call are not reliable */
 
 /* indices into the double stats[SERBF_NSTATS] device array */
 #define SERBF_STAT_L2 0        /* sum over id_all of E_i^2                 (Eq. 3-19) */
@@ -200,20 +203,21 @@ int serbf_state_init(serbf_state *st_dev, const serbf_config *cfg, void *stream)
 int serbf_normalize_sdf(const float *S, float *t, int64_t n, double *mh_dev, serbf_workspace *ws,
                         void *stream);
 
-/* Allocation-free form of serbf_normalize_sdf.  The paper has no counterpart;
- * it exists for callers that cannot allocate device memory at the moment they
- * need the normalisation, e.g. code running while a stream is being captured
- * into a CUDA graph (cudaMalloc is not permitted during capture) or a host
- * application that only hands out buffers from its own fixed pool.  No
- * workspace is taken: the reduction scratch is a fixed array inside the
- * library (16384 partial minima, 64 KiB on every device that loads it, kept
- * until the process exits), so n is limited to 67,108,864 points; a larger n
- * returns SERBF_ECAPACITY before anything is launched.  mh_dev (2 doubles) is
- * required.  The first call on each device looks up the array's device
- * address on the host; make that first call before any stream capture.
- * Targets and m, h are identical to serbf_normalize_sdf.  All calls share the
- * one array, so calls that can overlap on the GPU (other streams, other host
- * threads) race and must be serialised by the caller. */
+/* Allocation-free form of serbf_normalize_sdf.  The paper has no counterpart.
+ * Some callers cannot allocate device memory when they need the target map:
+ * an application that hands out device memory only from a pool it set up at
+ * start-up, or a loop with a fixed memory budget that must not allocate once
+ * it runs.  This entry point takes no workspace: its reduction scratch is a
+ * fixed array inside the library (16384 partial minima, 64 KiB on every
+ * device that loads the library, held until the process exits), so n is
+ * limited to 67,108,864 points; a larger n returns SERBF_ECAPACITY before
+ * anything is launched.  mh_dev (2 doubles) is required.  The first call on
+ * each device looks up the array's device address and the device's SM count
+ * on the host (set-up; make that first call before any stream capture).
+ * Targets and m, h are bit-identical to serbf_normalize_sdf.  Every call
+ * shares the one array and overwrites it (nothing in it needs clearing), so
+ * calls that can overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller. */
 int serbf_normalize_sdf_noalloc(const float *S, float *t, int64_t n, double *mh_dev, void *stream);
 
 /* ------------------------------------------------------------------ a2 */
@@ -334,11 +338,16 @@ int serbf_backward(const serbf_points *pts, const serbf_params *prm, const serbf
  * serbf_backward with err = the forward's own E (grad is 10 x cap, rows of
  * kernels >= m untouched; stats[PAIRS_BWD] as there).  Each work item's
  * points with E != 0 are taken against its candidate kernels right after
- * its residuals are known; per-kernel moments are accumulated across items
- * in 64-bit fixed point (unit 2^-36, integer atomics), so the result is
- * deterministic; it equals serbf_backward's up to float rounding (the
- * kahan option does not apply).  Two launches.  EINVAL as serbf_forward, or
- * when grad is NULL. */
+ * its residuals are known; the per-item moments (world frame, float sums;
+ * compensated when cfg->kahan is set) are accumulated across items in 64-bit
+ * fixed point (unit 2^-36, integer atomics), so the result is deterministic
+ * and order-independent, each item's partial rounded to 2^-36; it equals
+ * serbf_backward's up to float rounding.  The fixed-point range is
+ * |moment| < 2^27: a partial beyond 2^26, or a bound of max|E| x (points
+ * within a kernel's support radius) x max(1, r^2) reaching 2^26, sets
+ * SERBF_FLAG_FIX_RANGE (read with serbf_status; the call itself does not
+ * wait for the device).  Two launches.  EINVAL as serbf_forward, or when
+ * grad is NULL. */
 int serbf_forward_backward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi,
                            float *err, uint8_t *mask, float *grad, double *stats, serbf_workspace *ws,
                            void *stream);

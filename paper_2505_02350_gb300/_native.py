@@ -17,7 +17,7 @@ SERBF_ECAPACITY = -3
 SERBF_ECUDA = -4
 SERBF_ETIMEOUT = -5
 
-FLAG_SUPER_LIST, FLAG_ADD_CAPACITY = 1, 4
+FLAG_SUPER_LIST, FLAG_ADD_CAPACITY, FLAG_FIX_RANGE = 1, 4, 8
 
 STAT_L2, STAT_L1, STAT_MAXE, STAT_COUNT, STAT_PAIRS_FWD, STAT_PAIRS_BWD = 0, 1, 2, 3, 4, 5
 STAT_ALPHA, STAT_BETA, STAT_BF, STAT_LOSS, NSTATS = 6, 7, 8, 9, 16
@@ -144,6 +144,11 @@ def _check(name, rc, ok=(SERBF_OK,)):
     if rc not in ok:
         raise SerbfError(name, rc)
     return rc
+
+
+def version():
+    """serbf_version(): the library's version string."""
+    return _lib.serbf_version().decode()
 
 
 def config_default(**over):

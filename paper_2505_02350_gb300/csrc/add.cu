@@ -2,11 +2,23 @@
 // kernel parameters of Eq. 3-24 appended as in Eq. 3-25:
 //   1. candidates: id_all points with |E| > tau_m / 2 (Algorithm 2, candidate set);
 //   2. keep the k = ceil(topk_frac |id_all|) largest |E| (ties: ascending
-//      binned index) with an exact radix select on the float bits of |E|;
+//      binned index), exactly, for any k;
 //   3. drop a candidate if an id_all point within add_radius has a larger |E|
 //      (Algorithm 2, local-maximum test);
 //   4. append c = v, w = -E, d = sqrt(-ln(eps / |E|) / dbar^2) on all axes,
 //      theta = 0, in selection order; reset the Adam moments.
+//
+// Three launches, each a no-op unless the addition is due:
+//   k_add_hist      all blocks: histogram of the candidates by the top 11 bits
+//                   of |E| (its float bits; the sign bit is 0); the last block
+//                   finds the bin B that holds the k-th largest key;
+//   k_add_gather    all blocks: every candidate in a bin >= B (a superset of
+//                   the top k) is appended to a list as (~key, index); the
+//                   last block sorts that list by (~key, index) ascending --
+//                   |E| descending, index ascending -- and keeps the first k;
+//   k_add_localmax  warps over the k selected points: the local-maximum test;
+//                   the last block appends the survivors in order.
+// The selection lists use the binning sort buffers (idle outside binning).
 #include <math.h>
 
 #include "common.cuh"
@@ -15,119 +27,273 @@ using namespace serbf;
 
 namespace {
 
-constexpr int kSelMax = 8192;  // largest selection sorted in shared memory
-constexpr int kAddThreads = 1024;
+constexpr int kHistThreads = 512;
+constexpr int kGatherThreads = 1024;
+constexpr int kBitonicMax = 8192;  // lists up to this size are sorted in shared memory
+constexpr int kLmThreads = 256;
+
+// sel_ctl slots
+enum { CTL_BIN = 0, CTL_K, CTL_SUPER, CTL_SLOT, CTL_HIST_DONE, CTL_GATHER_DONE, CTL_LM_DONE };
 
 __device__ __forceinline__ uint32_t cand_key(const float *E, const uint8_t *mask, int64_t i, double thresh) {
-    float a = fabsf(E[i]);
+    const float a = fabsf(E[i]);
     return (mask[i] && (double)a > thresh) ? __float_as_uint(a) : 0u;
 }
 
-__global__ void __launch_bounds__(kAddThreads) k_add_select(const float *E, const uint8_t *mask, int64_t n,
-                                                           const double *stats, const serbf_state *st,
-                                                           double thresh, double frac, int force,
-                                                           unsigned long long *sel, int32_t *info) {
+// Last block of a grid to reach this point (after its own writes): true in
+// exactly one block.  No block waits for another.
+__device__ __forceinline__ bool last_block(uint32_t *counter, bool *s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        *s_flag = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (*s_flag) __threadfence();
+    return *s_flag;
+}
+
+__global__ void __launch_bounds__(kHistThreads) k_add_hist(const float *E, const uint8_t *mask, int64_t n,
+                                                          const double *stats, const serbf_state *st,
+                                                          double thresh, double frac, int force, uint32_t *hist,
+                                                          uint32_t *ctl, int32_t *info) {
     pdl_wait();
     pdl_trigger();
-    extern __shared__ unsigned long long sk[];
-    __shared__ uint32_t hist[256];
+    __shared__ uint32_t sh[kSelBins];
     __shared__ uint32_t tmp[33];
-    __shared__ uint32_t s_prefix, s_remaining, s_all;
-    __shared__ int s_go;
+    __shared__ bool s_last;
+    const bool go = force || st->do_add;
+    if (!go) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = 0;
+        return;
+    }
+    for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) sh[d] = 0u;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = cand_key(E, mask, i, thresh);
+        if (key) atomicAdd(&sh[key >> 20], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kSelBins; d += blockDim.x)
+        if (sh[d]) atomicAdd(&hist[d], sh[d]);
+    if (!last_block(&ctl[CTL_HIST_DONE], &s_last)) return;
+    // the last block: bin counts (cleared for the next call), their total C,
+    // k and the bin B holding the k-th largest key
+    for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) {
+        sh[d] = __ldcg(&hist[d]);
+        hist[d] = 0u;
+    }
+    __syncthreads();
+    // thread q owns the four bins 2047 - 4q .. 2044 - 4q, largest first
+    constexpr int kPer = kSelBins / kHistThreads;
+    static_assert(kPer * kHistThreads == kSelBins, "bins per thread");
+    uint32_t own = 0;
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) own += sh[kSelBins - 1 - kPer * threadIdx.x - r];
+    uint32_t total;
+    const uint32_t above = block_exscan(own, tmp, &total);  // keys in larger bins than this thread's
+    int64_t k = total;
+    if (frac > 0.0) {
+        const double kk = ceil(frac * stats[SERBF_STAT_COUNT]);
+        if (kk < (double)k) k = (int64_t)kk;
+    }
+    if (k < 0) k = 0;
+    uint32_t run = above;
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        const int d = kSelBins - 1 - kPer * threadIdx.x - r;
+        const uint32_t c = sh[d];
+        if (k > 0 && run < (uint32_t)k && run + c >= (uint32_t)k) {
+            ctl[CTL_BIN] = (uint32_t)d;
+            ctl[CTL_SUPER] = run + c;
+        }
+        run += c;
+    }
     if (threadIdx.x == 0) {
-        s_go = force || st->do_add;
-        info[0] = s_go;
+        if (k == 0) {
+            ctl[CTL_BIN] = kSelBins;  // nothing to select
+            ctl[CTL_SUPER] = 0u;
+        }
+        ctl[CTL_K] = (uint32_t)k;
+        ctl[CTL_SLOT] = 0u;
+        ctl[CTL_HIST_DONE] = 0u;
+        info[0] = 1;
         info[1] = 0;
     }
-    __syncthreads();
-    if (!s_go) return;
-    int64_t k = kSelMax;
-    if (frac > 0.0) k = (int64_t)ceil(frac * stats[SERBF_STAT_COUNT]);
-    if (k > kSelMax) k = kSelMax;
-    if (threadIdx.x == 0) {
-        s_prefix = 0;
-        s_remaining = (uint32_t)k;
-        s_all = 0;
-    }
-    __syncthreads();
-    // exact radix select of the k-th largest key, most significant byte first
-    for (int shift = 24; shift >= 0; shift -= 8) {
-        for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[d] = 0;
-        __syncthreads();
-        const uint32_t pre = s_prefix;
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            uint32_t key = cand_key(E, mask, i, thresh);
-            if (key == 0) continue;
-            if (shift < 24 && (key >> (shift + 8)) != (pre >> (shift + 8))) continue;
-            atomicAdd(&hist[(key >> shift) & 255u], 1u);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && !s_all) {
-            uint32_t above = 0, rem = s_remaining;
-            int d = 255;
-            for (; d >= 0; --d) {
-                if (above + hist[d] >= rem) break;
-                above += hist[d];
-            }
-            if (d < 0) {
-                s_all = 1;  // fewer candidates than k under this prefix: take them all
-            } else {
-                s_prefix = pre | ((uint32_t)d << shift);
-                s_remaining = rem - above;
-            }
-        }
-        __syncthreads();
-        if (s_all) break;
-    }
-    // ordered collection: key > T, plus the first `remaining` keys == T
-    const uint32_t T = s_all ? 0u : s_prefix;
-    const uint32_t need_eq = s_all ? 0u : s_remaining;
-    uint32_t carry = 0, carry_eq = 0;
-    for (int64_t i0 = 0; i0 < n; i0 += blockDim.x) {
-        const int64_t i = i0 + threadIdx.x;
-        const uint32_t key = i < n ? cand_key(E, mask, i, thresh) : 0u;
-        const uint32_t eq = (!s_all && key != 0 && key == T) ? 1u : 0u;
-        uint32_t teq;
-        const uint32_t oeq = block_exscan(eq, tmp, &teq);
-        const uint32_t take = (key != 0 && (s_all ? true : key > T)) || (eq && carry_eq + oeq < need_eq);
-        uint32_t tt;
-        const uint32_t o = block_exscan(take, tmp, &tt);
-        if (take && carry + o < (uint32_t)kSelMax)
-            sk[carry + o] = ((unsigned long long)(~key) << 32) | (unsigned long long)(uint32_t)i;
-        carry += tt;
-        carry_eq += teq;
-    }
-    const uint32_t ns = carry < (uint32_t)kSelMax ? carry : (uint32_t)kSelMax;
-    // bitonic sort ascending on (~|E| bits, index): |E| descending, index ascending
+}
+
+// ---------------------------------------------------------------- block sorts
+// Sort the list (hi, lo) of s pairs ascending by (hi, lo), by one block of
+// kGatherThreads threads.  Small lists: bitonic network in shared memory.
+__device__ void sort_small(uint32_t *hi, uint32_t *lo, uint32_t s, unsigned long long *sk) {
     uint32_t P = 1;
-    while (P < ns) P <<= 1;
-    for (uint32_t q = ns + threadIdx.x; q < P; q += blockDim.x) sk[q] = ~0ull;
+    while (P < s) P <<= 1;
+    for (uint32_t q = threadIdx.x; q < P; q += blockDim.x)
+        sk[q] = q < s ? (((unsigned long long)hi[q] << 32) | lo[q]) : ~0ull;
     __syncthreads();
     for (uint32_t size = 2; size <= P; size <<= 1) {
         for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
             for (uint32_t q = threadIdx.x; q < P / 2; q += blockDim.x) {
-                const uint32_t lo = 2 * stride * (q / stride) + (q % stride), hi = lo + stride;
-                const bool asc = (lo & size) == 0;
-                const unsigned long long a = sk[lo], b = sk[hi];
-                if ((a > b) == asc) {
-                    sk[lo] = b;
-                    sk[hi] = a;
+                const uint32_t a = 2 * stride * (q / stride) + (q % stride), b = a + stride;
+                const bool asc = (a & size) == 0;
+                const unsigned long long x = sk[a], y = sk[b];
+                if ((x > y) == asc) {
+                    sk[a] = y;
+                    sk[b] = x;
                 }
             }
             __syncthreads();
         }
     }
-    for (uint32_t q = threadIdx.x; q < ns; q += blockDim.x) sel[q] = sk[q];
-    if (threadIdx.x == 0) info[1] = (int32_t)ns;
+    for (uint32_t q = threadIdx.x; q < s; q += blockDim.x) {
+        hi[q] = (uint32_t)(sk[q] >> 32);
+        lo[q] = (uint32_t)sk[q];
+    }
+    __syncthreads();
+}
+
+struct RadixSmem {
+    uint32_t base[256];       // running output position of each digit
+    uint32_t tile_tot[256];   // digit counts of the current tile
+    uint32_t wcnt[32][256];   // per warp and digit: count, then exclusive prefix over warps
+    uint32_t tmp[33];
+    int skip;
+};
+
+__device__ __forceinline__ uint32_t digit_of(const uint32_t *hi, const uint32_t *lo, uint32_t i, int word,
+                                              int shift) {
+    return ((word ? hi[i] : lo[i]) >> shift) & 255u;
+}
+
+// One stable counting pass on an 8-bit digit (word 0: lo, 1: hi) from (shi,
+// slo) to (dhi, dlo).  Returns false (and moves nothing) when every element
+// has the same digit.  Stability: tiles of blockDim elements in order; within
+// a tile, elements of one digit are ranked by warp, then by lane.
+__device__ bool radix_pass(const uint32_t *shi, const uint32_t *slo, uint32_t *dhi, uint32_t *dlo, uint32_t s,
+                           int word, int shift, RadixSmem &R) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) R.base[d] = 0u;
+    if (threadIdx.x == 0) R.skip = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < s; i += blockDim.x) atomicAdd(&R.base[digit_of(shi, slo, i, word, shift)], 1u);
+    __syncthreads();
+    const uint32_t c = threadIdx.x < 256 ? R.base[threadIdx.x] : 0u;
+    if (c == s) R.skip = 1;
+    uint32_t tot;
+    const uint32_t off = block_exscan(c, R.tmp, &tot);
+    const int skip = R.skip;
+    __syncthreads();  // every thread has read the flag before the next pass resets it
+    if (skip) return false;
+    if (threadIdx.x < 256) R.base[threadIdx.x] = off;
+    __syncthreads();
+    for (uint32_t t0 = 0; t0 < s; t0 += blockDim.x) {
+        for (int q = threadIdx.x; q < 32 * 256; q += blockDim.x) (&R.wcnt[0][0])[q] = 0u;
+        __syncthreads();
+        const uint32_t i = t0 + threadIdx.x;
+        const bool valid = i < s;
+        const uint32_t d = valid ? digit_of(shi, slo, i, word, shift) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && lane == __ffs(peers) - 1) R.wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            uint32_t run = 0;
+            for (int w = 0; w < 32; ++w) {
+                const uint32_t v = R.wcnt[w][threadIdx.x];
+                R.wcnt[w][threadIdx.x] = run;
+                run += v;
+            }
+            R.tile_tot[threadIdx.x] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = R.base[d] + R.wcnt[warp][d] + rank;
+            dhi[pos] = shi[i];
+            dlo[pos] = slo[i];
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) R.base[threadIdx.x] += R.tile_tot[threadIdx.x];
+        __syncthreads();
+    }
+    return true;
+}
+
+// Larger lists: LSD radix on the 64-bit (hi, lo) in 8-bit digits, ping-pong
+// between (hi, lo) and (hi2, lo2); passes whose digit is the same for every
+// element are skipped.  The first `keep` sorted pairs end in (hi, lo).
+__device__ void sort_large(uint32_t *hi, uint32_t *lo, uint32_t *hi2, uint32_t *lo2, uint32_t s, uint32_t keep,
+                           RadixSmem &R) {
+    uint32_t *ah = hi, *al = lo, *bh = hi2, *bl = lo2;
+    for (int pass = 0; pass < 8; ++pass) {
+        if (radix_pass(ah, al, bh, bl, s, pass >= 4, 8 * (pass & 3), R)) {
+            uint32_t *t = ah;
+            ah = bh;
+            bh = t;
+            t = al;
+            al = bl;
+            bl = t;
+        }
+    }
+    if (ah != hi) {
+        for (uint32_t q = threadIdx.x; q < keep; q += blockDim.x) {
+            hi[q] = ah[q];
+            lo[q] = al[q];
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kGatherThreads) k_add_gather(const float *E, const uint8_t *mask, int64_t n,
+                                                              double thresh, uint32_t *ctl, int32_t *info,
+                                                              uint32_t *hi, uint32_t *lo, uint32_t *hi2,
+                                                              uint32_t *lo2) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ bool s_last;
+    if (!info[0]) return;
+    const uint32_t B = ctl[CTL_BIN];
+    const int lane = threadIdx.x & 31;
+    if (B < (uint32_t)kSelBins) {
+        // grid-stride in whole warps, so every lane of a warp takes part in the ballot
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+            const int64_t i = i0 + lane;
+            const uint32_t key = i < n ? cand_key(E, mask, i, thresh) : 0u;
+            const bool take = key != 0u && (key >> 20) >= B;
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            if (!bal) continue;
+            uint32_t base = 0;
+            const int leader = __ffs(bal) - 1;
+            if (lane == leader) base = atomicAdd(&ctl[CTL_SLOT], (uint32_t)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (take) {
+                const uint32_t o = base + __popc(bal & ((1u << lane) - 1u));
+                hi[o] = ~key;
+                lo[o] = (uint32_t)i;
+            }
+        }
+    }
+    if (!last_block(&ctl[CTL_GATHER_DONE], &s_last)) return;
+    const uint32_t s = __ldcg(&ctl[CTL_SLOT]), k = min(ctl[CTL_K], s);
+    if (s <= (uint32_t)kBitonicMax)
+        sort_small(hi, lo, s, reinterpret_cast<unsigned long long *>(smem));
+    else
+        sort_large(hi, lo, hi2, lo2, s, k, *reinterpret_cast<RadixSmem *>(smem));
+    if (threadIdx.x == 0) {
+        info[1] = (int32_t)k;
+        ctl[CTL_SLOT] = 0u;
+        ctl[CTL_GATHER_DONE] = 0u;
+    }
 }
 
 // One selected point s (a warp): keep[s] = 0 if an id_all point within the
 // radius has a larger |E|.
 __device__ __forceinline__ void localmax_one(const float *x, const float *y, const float *z, const float *E,
                                              const uint8_t *mask, const uint32_t *cell_start, serbf_grid g, int sf,
-                                             int nsx, int nsy, float r2, int reach, const unsigned long long *sel,
+                                             int nsx, int nsy, float r2, int reach, const uint32_t *sel_idx,
                                              uint32_t *keep, int s, int lane) {
-    const uint32_t i = (uint32_t)(sel[s] & 0xffffffffull);
+    const uint32_t i = sel_idx[s];
     const float xi = x[i], yi = y[i], zi = z[i], ei = fabsf(E[i]);
     const int kx = cell_axis(xi, g.origin[0], g.h, g.n[0]);
     const int ky = cell_axis(yi, g.origin[1], g.h, g.n[1]);
@@ -153,57 +319,47 @@ __device__ __forceinline__ void localmax_one(const float *x, const float *y, con
     if (lane == 0) keep[s] = !bad;
 }
 
-// Warps over the selected points (grid-stride): reject a point if an id_all
-// point within the radius has a larger |E| (distance in float, same operation
-// order as the support test, <= r2).  One block per SM, so a step without an
-// addition retires few blocks.
-__global__ void k_add_localmax(const float *x, const float *y, const float *z, const float *E,
-                               const uint8_t *mask, const uint32_t *cell_start, serbf_grid g, int sf, int nsx,
-                               int nsy, float r2, int reach, const unsigned long long *sel, const int32_t *info,
-                               uint32_t *keep) {
-    pdl_wait();
-    pdl_trigger();
-    if (!info[0]) return;
-    const int lane = threadIdx.x & 31, nsel = info[1];
-    for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nsel; s += (gridDim.x * blockDim.x) >> 5)
-        localmax_one(x, y, z, E, mask, cell_start, g, sf, nsx, nsy, r2, reach, sel, keep, s, lane);
-}
+struct AppendArgs {
+    const float *x, *y, *z, *E, *S;
+    double dbar_min, eps;
+    float *p, *am, *av;
+    int32_t *m_dev;
+    int cap;
+    serbf_state *st;
+    int32_t *status;
+    long long *needed;
+};
 
-__global__ void __launch_bounds__(kAddThreads) k_add_append(const float *x, const float *y, const float *z,
-                                                           const float *E, const float *S, double dbar_min,
-                                                           double eps, const unsigned long long *sel,
-                                                           const uint32_t *keep, int32_t *info, float *p,
-                                                           float *am, float *av, int32_t *m_dev, int cap,
-                                                           serbf_state *st, int32_t *status, long long *needed) {
-    pdl_wait();
-    pdl_trigger();
+// Eq. 3-24 / 3-25: the kept points become kernels, appended in selection
+// order up to the capacity (a flag and the size needed otherwise); Adam
+// restarts from zero moments.  Run by one block.
+__device__ void append_kept(const AppendArgs &a, const uint32_t *sel_idx, const uint32_t *keep, int ns, int32_t *info) {
     __shared__ uint32_t tmp[33];
-    if (!info[0]) return;
-    const int ns = info[1];
-    const int m = *m_dev;
-    const int room = cap - m;
+    const int m = *a.m_dev;
+    const int room = a.cap - m;
+    const int cap = a.cap;
     uint32_t carry = 0;
     for (int s0 = 0; s0 < ns; s0 += blockDim.x) {
         const int s = s0 + threadIdx.x;
-        const uint32_t k = s < ns ? keep[s] : 0u;
+        const uint32_t k = s < ns ? __ldcg(&keep[s]) : 0u;
         uint32_t tot;
         const uint32_t o = block_exscan(k, tmp, &tot);
         if (k && (int)(carry + o) < room) {
-            const uint32_t i = (uint32_t)(sel[s] & 0xffffffffull);
+            const uint32_t i = sel_idx[s];
             const int j = m + (int)(carry + o);
-            const double ae = fabs((double)E[i]);
-            const double dbar = fmax(fabs((double)S[i]), dbar_min);
-            const double d = sqrt(-log(eps / ae) / (dbar * dbar));
-            p[PCX * cap + j] = x[i];
-            p[PCY * cap + j] = y[i];
-            p[PCZ * cap + j] = z[i];
-            p[PD1 * cap + j] = (float)d;
-            p[PD2 * cap + j] = (float)d;
-            p[PD3 * cap + j] = (float)d;
-            p[PTX * cap + j] = 0.f;
-            p[PTY * cap + j] = 0.f;
-            p[PTZ * cap + j] = 0.f;
-            p[PW * cap + j] = -E[i];
+            const double ae = fabs((double)a.E[i]);
+            const double dbar = fmax(fabs((double)a.S[i]), a.dbar_min);
+            const double d = sqrt(-log(a.eps / ae) / (dbar * dbar));
+            a.p[PCX * cap + j] = a.x[i];
+            a.p[PCY * cap + j] = a.y[i];
+            a.p[PCZ * cap + j] = a.z[i];
+            a.p[PD1 * cap + j] = (float)d;
+            a.p[PD2 * cap + j] = (float)d;
+            a.p[PD3 * cap + j] = (float)d;
+            a.p[PTX * cap + j] = 0.f;
+            a.p[PTY * cap + j] = 0.f;
+            a.p[PTZ * cap + j] = 0.f;
+            a.p[PW * cap + j] = -a.E[i];
         }
         carry += tot;
     }
@@ -212,21 +368,42 @@ __global__ void __launch_bounds__(kAddThreads) k_add_append(const float *x, cons
     const int mn = m + added;
     for (int64_t q = threadIdx.x; q < 10ll * mn; q += blockDim.x) {
         const int r = (int)(q / mn), j = (int)(q - (int64_t)r * mn);
-        am[r * cap + j] = 0.f;
-        av[r * cap + j] = 0.f;
+        a.am[r * cap + j] = 0.f;
+        a.av[r * cap + j] = 0.f;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         if ((int)carry > room) {
-            atomicOr(status, SERBF_FLAG_ADD_CAPACITY);
-            atomicMax(needed + 3, (long long)(m + (int)carry));
+            atomicOr(a.status, SERBF_FLAG_ADD_CAPACITY);
+            atomicMax(a.needed + 3, (long long)(m + (int)carry));
         }
         info[2] = (int)carry;
-        *m_dev = mn;
-        st->m_added = added;
-        st->adam_t = 0;
-        st->do_add = 0;
+        *a.m_dev = mn;
+        a.st->m_added = added;
+        a.st->adam_t = 0;
+        a.st->do_add = 0;
         info[0] = 0;
     }
+}
+
+// Warps over the selected points (grid-stride): reject a point if an id_all
+// point within the radius has a larger |E| (distance in float, same operation
+// order as the support test, <= r2).  One block per SM, so a step without an
+// addition retires few blocks.  The last block appends the survivors.
+__global__ void __launch_bounds__(kLmThreads) k_add_localmax(const uint8_t *mask, const uint32_t *cell_start,
+                                                            serbf_grid g, int sf, int nsx, int nsy, float r2,
+                                                            int reach, const uint32_t *sel_idx, uint32_t *keep,
+                                                            int32_t *info, uint32_t *ctl, AppendArgs ap) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ bool s_last;
+    if (!info[0]) return;
+    const int lane = threadIdx.x & 31, nsel = info[1];
+    for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nsel; s += (gridDim.x * blockDim.x) >> 5)
+        localmax_one(ap.x, ap.y, ap.z, ap.E, mask, cell_start, g, sf, nsx, nsy, r2, reach, sel_idx, keep, s, lane);
+    if (!last_block(&ctl[CTL_LM_DONE], &s_last)) return;
+    append_kept(ap, sel_idx, keep, nsel, info);
+    if (threadIdx.x == 0) ctl[CTL_LM_DONE] = 0u;
 }
 
 }  // namespace
@@ -244,24 +421,27 @@ extern "C" int serbf_add_kernels(const serbf_points *pts, const float *S_raw, co
     if (!(cfg->add_radius >= 0.0) || !(cfg->eps > 0.0)) return SERBF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     static bool attr = false;
-    const int smem = kSelMax * (int)sizeof(unsigned long long);
+    const int smem = (int)(sizeof(RadixSmem) > kBitonicMax * sizeof(unsigned long long)
+                               ? sizeof(RadixSmem)
+                               : kBitonicMax * sizeof(unsigned long long));
     if (!attr) {
-        if (cudaFuncSetAttribute(k_add_select, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(k_add_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
             return SERBF_ECUDA;
         attr = true;
     }
-    launch_pdl(k_add_select, dim3(1), dim3(kAddThreads), smem, s, err, mask, pts->n, stats, st_dev, cfg->tau_m * 0.5, cfg->topk_frac,
-                                               force, ws->sel_key, ws->add_info);
+    const unsigned nsm = (unsigned)(ws->sm_count > 0 ? ws->sm_count : 1);
+    const double thresh = cfg->tau_m * 0.5;
+    launch_pdl(k_add_hist, dim3(2 * nsm), dim3(kHistThreads), 0, s, err, mask, pts->n, stats, st_dev, thresh,
+               cfg->topk_frac, force, ws->sel_hist, ws->sel_ctl, ws->add_info);
+    launch_pdl(k_add_gather, dim3(nsm), dim3(kGatherThreads), (size_t)smem, s, err, mask, pts->n, thresh, ws->sel_ctl,
+               ws->add_info, ws->keys0, ws->vals0, ws->keys1, ws->vals1);
     const float r2 = (float)(cfg->add_radius * cfg->add_radius);
     int reach = (int)ceil(cfg->add_radius / ws->grid.h) + 1;
     if (reach > 1 << 20) reach = 1 << 20;
-    const unsigned lm_blocks = (unsigned)(ws->sm_count > 0 ? ws->sm_count : 1);
-    launch_pdl(k_add_localmax, dim3(lm_blocks), dim3(256), 0, s, pts->x, pts->y, pts->z, err, mask, ws->cell_start, ws->grid, ws->sf,
-                                            ws->ns[0], ws->ns[1], r2, reach, ws->sel_key, ws->add_info,
-                                            ws->sel_keep);
-    launch_pdl(k_add_append, dim3(1), dim3(kAddThreads), 0, s, pts->x, pts->y, pts->z, err, S_raw, cfg->dbar_min, cfg->eps, ws->sel_key,
-                                           ws->sel_keep, ws->add_info, prm->p, adam_m, adam_v, prm->m, prm->cap,
-                                           st_dev, ws->status, ws->needed);
+    AppendArgs ap{pts->x, pts->y, pts->z, err, S_raw, cfg->dbar_min, cfg->eps, prm->p, adam_m, adam_v,
+                  prm->m, prm->cap, st_dev, ws->status, ws->needed};
+    launch_pdl(k_add_localmax, dim3(nsm), dim3(kLmThreads), 0, s, mask, ws->cell_start, ws->grid, ws->sf, ws->ns[0],
+               ws->ns[1], r2, reach, ws->vals0, ws->keys1, ws->add_info, ws->sel_ctl, ap);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;
 }

@@ -43,7 +43,6 @@ void carve(Carver &c, serbf_workspace *w, const serbf_ws_sizes *s) {
     int64_t T = N / kTile + S + 1;
     int64_t SB = (N + kSortTile - 1) / kSortTile;
     if (SB < 1) SB = 1;
-    int64_t K8 = K > 8192 ? K : 8192;
     w->max_tiles = T;
     w->max_supers = S;
     w->sort_blocks = SB;
@@ -89,13 +88,14 @@ void carve(Carver &c, serbf_workspace *w, const serbf_ws_sizes *s) {
     w->nz = c.take<float4>(T * kTile);
     w->step_part = c.take<float>(6 * (SERBF_NPARAM * (K / 256 + 1) + 1));
     w->step_scal = c.take<double>(8);
-    w->sel_key = c.take<unsigned long long>(K8);
-    w->sel_keep = c.take<uint32_t>(K8);
+    w->sel_hist = c.take<uint32_t>(kSelBins);
+    w->sel_ctl = c.take<uint32_t>(16);
     w->add_info = c.take<int32_t>(16);
     w->status = c.take<int32_t>(16);
     w->needed = c.take<long long>(4);
     w->counters = c.take<uint32_t>(16);
     w->dtmp = c.take<double>(16);
+    w->cell_max = c.take<uint32_t>(4);
 }
 
 __global__ void k_exscan_u32(uint32_t *a, int64_t n) {
@@ -219,7 +219,7 @@ int launch_exscan_i64(int64_t *a, int64_t n, cudaStream_t s) {
 
 extern "C" {
 
-const char *serbf_version(void) { return "serbf 0.1 (sm_103a)"; }
+const char *serbf_version(void) { return "serbf 0.2.0 (sm_103a)"; }
 
 const char *serbf_status_string(int code) {
     switch (code) {
@@ -296,6 +296,9 @@ int serbf_workspace_init(serbf_workspace *ws, void *dev, size_t bytes, const ser
             return SERBF_ECUDA;
     }
     if (cudaMemset(ws->add_info, 0, 16 * sizeof(int32_t)) != cudaSuccess) return SERBF_ECUDA;
+    if (cudaMemset(ws->sel_hist, 0, kSelBins * sizeof(uint32_t)) != cudaSuccess) return SERBF_ECUDA;
+    if (cudaMemset(ws->cell_max, 0, 4 * sizeof(uint32_t)) != cudaSuccess) return SERBF_ECUDA;
+    if (cudaMemset(ws->sel_ctl, 0, 16 * sizeof(uint32_t)) != cudaSuccess) return SERBF_ECUDA;
     if (cudaMemset(ws->adj_fix, 0, sizeof(unsigned long long) * 10 * (size_t)sz->max_kernels) != cudaSuccess)
         return SERBF_ECUDA;
     if (cudaMemset(ws->adj_pairs, 0, sizeof(unsigned long long) * 8) != cudaSuccess) return SERBF_ECUDA;

@@ -108,13 +108,21 @@ __global__ void k_count_cells(const uint32_t *keys, int64_t n, uint32_t *cnt) {
 
 // tiles and forward work items per super cell (for the scans that number them)
 __global__ void k_super_tiles(const uint32_t *cell_start, int nsuper, int cps, uint32_t *stile, uint32_t *sitem,
-                              uint32_t *maxt) {
+                              uint32_t *maxt, uint32_t *maxc) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nsuper; s += gridDim.x * blockDim.x) {
         uint32_t b = cell_start[(int64_t)s * cps], e = cell_start[(int64_t)(s + 1) * cps];
         const uint32_t nt = (e - b + kTile - 1) / kTile;
         stile[s] = nt;
         sitem[s] = (nt + 1) / 2;
         atomicMax(maxt, nt);
+        // most points in one cell of this super cell (bounds the points in a ball)
+        uint32_t mc = 0, prev = b;
+        for (int c = 1; c <= cps; ++c) {
+            const uint32_t q = cell_start[(int64_t)s * cps + c];
+            mc = max(mc, q - prev);
+            prev = q;
+        }
+        atomicMax(maxc, mc);
     }
 }
 
@@ -280,8 +288,9 @@ extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, 
     if (rc) return rc;
     uint32_t *maxt = ws->counters + 8;
     cudaMemsetAsync(maxt, 0, sizeof(uint32_t), s);
+    cudaMemsetAsync(ws->cell_max, 0, sizeof(uint32_t), s);
     k_super_tiles<<<gsz(nsuper, 256), 256, 0, s>>>(ws->cell_start, (int)nsuper, cps, ws->super_tile0,
-                                                   ws->super_item0, maxt);
+                                                   ws->super_item0, maxt, ws->cell_max);
     rc = launch_exscan_u32(ws->super_tile0, nsuper, s);
     if (rc) return rc;
     rc = launch_exscan_u32(ws->super_item0, nsuper, s);

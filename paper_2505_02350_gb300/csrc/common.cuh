@@ -32,6 +32,7 @@ constexpr int kBwdSplit = 16;                     // most blocks per kernel in t
 constexpr int kBwdWarpsPerKernel = kBwdSplit * kBwdThreads / 32;  // == 32, one epilogue lane each
 constexpr int kMaxRowsPerKernel = 1 << 16;        // cell rows a kernel support may span
 constexpr float kLog2e = 1.4426950408889634f;
+constexpr int kSelBins = 2048;                    // addition: histogram bins over bits 30..20 of |E|
 
 // Parameter rows (Sec. 3.2): centre, axis parameters d, angles, weight.
 enum { PCX = 0, PCY, PCZ, PD1, PD2, PD3, PTX, PTY, PTZ, PW };
@@ -120,15 +121,17 @@ struct serbf_workspace {
     // optimiser step scratch
     float *step_part;   // per-block partial sums
     double *step_scal;  // alpha, beta, Adam bias corrections
-    // addition scratch
-    unsigned long long *sel_key;  // max(max_kernels, 8192)
-    uint32_t *sel_keep;           // max(max_kernels, 8192)
+    // addition scratch (the selection itself lives in the binning sort
+    // buffers keys0/vals0 and keys1/vals1, idle outside binning)
+    uint32_t *sel_hist;           // kSelBins: candidate counts by the top bits of |E| (zero between calls)
+    uint32_t *sel_ctl;            // [16]: threshold bin, k, slot and block counters
     int32_t *add_info;            // [0] active, [1] selected, [2] kept
     // status and counters
     int32_t *status;              // [0] flags
     long long *needed;            // [4]
     uint32_t *counters;           // [8] last-block counters
     double *dtmp;                 // [16]
+    uint32_t *cell_max;           // [4]: [0] most points in one binning cell, [1] fixed-point range bound (float bits)
 };
 
 #define SERBF_CHECK_LAUNCH()                                   \
@@ -344,7 +347,11 @@ __device__ __forceinline__ void accumulate(const float4 &pt, const float4 &k0, c
 //     dL2/dc     =  4 a R^T (d^2 . M1)
 //     dL2/dtheta = -4 a sum_kl d_k^2 K_kl (M2)_kl,   K = (dR/dtheta) R^T
 // (theta_x: K is constant and the sum is (d_2^2 - d_1^2) (M2)_12).
-__device__ __forceinline__ void grad_from_moments(const float *p, int cap, int j, const float (&M)[10], float *grad) {
+// WORLD: the moments come in the world frame (W1 = sum s Delta, W2 = sum s
+// Delta Delta^T with Delta = v - c) and are rotated first: M1 = R W1,
+// M2 = R W2 R^T.
+template <bool WORLD = false>
+__device__ __forceinline__ void grad_from_moments(const float *p, int cap, int j, const float (&Min)[10], float *grad) {
     const float w = p[PW * cap + j];
     const float d[3] = {p[PD1 * cap + j], p[PD2 * cap + j], p[PD3 * cap + j]};
     float sx, cx, sy, cy, sz, cz;
@@ -358,6 +365,25 @@ __device__ __forceinline__ void grad_from_moments(const float *p, int cap, int j
     const float Ry[9] = {-cx * sy, -cx * cy * sz, -cx * cy * cz, -sx * sy, -sx * cy * sz,
                          -sx * cy * cz, cy, -sy * sz, -sy * cz};
     const float Rz[9] = {0.f, R[2], -R[1], 0.f, R[5], -R[4], 0.f, R[8], -R[7]};
+    float M[10];
+#pragma unroll
+    for (int r = 0; r < 10; ++r) M[r] = Min[r];
+    if (WORLD) {
+        const float W2[3][3] = {{Min[4], Min[5], Min[6]}, {Min[5], Min[7], Min[8]}, {Min[6], Min[8], Min[9]}};
+        float T[3][3];  // R W2
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            M[1 + k] = R[3 * k] * Min[1] + R[3 * k + 1] * Min[2] + R[3 * k + 2] * Min[3];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) T[k][b] = R[3 * k] * W2[0][b] + R[3 * k + 1] * W2[1][b] + R[3 * k + 2] * W2[2][b];
+        }
+        const int idx[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const int k = idx[q][0], l = idx[q][1];
+            M[4 + q] = T[k][0] * R[3 * l] + T[k][1] * R[3 * l + 1] + T[k][2] * R[3 * l + 2];
+        }
+    }
     const float aw = w * fabsf(w);
     const float M2[3][3] = {{M[4], M[5], M[6]}, {M[5], M[7], M[8]}, {M[6], M[8], M[9]}};
     grad[PW * cap + j] = 4.f * fabsf(w) * M[0];

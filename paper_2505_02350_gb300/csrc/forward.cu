@@ -47,6 +47,7 @@ struct FwdArgs {
     FwdPart *part;        // one partial per tile
     uint32_t *item_next;  // next work item to take (zero between launches)
     uint32_t *exit_count; // blocks that have exited (zero between launches)
+    int32_t *status;      // device status flags
 };
 
 constexpr int kTouch = 256;  // kernels remembered per warp and item for the adjoint (more: re-scan the list)
@@ -182,23 +183,39 @@ __device__ __forceinline__ float redux_max(float v) {
     return r;
 }
 
-// Fixed-order warp reduction of tile partials [b, e) into one partial.
-__device__ __forceinline__ FwdPart reduce_parts(const FwdPart *p, uint32_t b, uint32_t e, int lane) {
-    ff l{0.f, 0.f};
+// Partial of a group of tiles: the loss sum in double (the global loss
+// reduction runs in FP64; a tile's own sum of 32 squares is float-float).
+struct FwdGPart {
+    double l2;
+    float maxe;
+    uint32_t cnt;
+    unsigned long long pairs;
+};
+static_assert(sizeof(FwdGPart) == sizeof(FwdPart), "group partials reuse the tile-partial storage");
+
+__device__ __forceinline__ double part_l2(const FwdPart *p, uint32_t q) {
+    return (double)__ldcg(&p[q].l2hi) + (double)__ldcg(&p[q].l2lo);
+}
+__device__ __forceinline__ double part_l2(const FwdGPart *p, uint32_t q) { return __ldcg(&p[q].l2); }
+
+// Fixed-order warp reduction of partials [b, e) (of tiles or of groups) into one.
+template <typename P>
+__device__ __forceinline__ FwdGPart reduce_parts(const P *p, uint32_t b, uint32_t e, int lane) {
+    double l = 0.0;
     float mx = 0.f;
     unsigned long long c = 0, pr = 0;
 #pragma unroll 4
     for (uint32_t q = b + lane; q < e; q += 32) {
-        l = ff_add(l, ff{__ldcg(&p[q].l2hi), __ldcg(&p[q].l2lo)});
+        l += part_l2(p, q);
         mx = fmaxf(mx, __ldcg(&p[q].maxe));
         c += __ldcg(&p[q].cnt);
         pr += __ldcg(&p[q].pairs);
     }
-    l = warp_sum_ff(l);
+    l = warp_sum(l);
     mx = warp_max(mx);
     c = warp_sum(c);
     pr = warp_sum(pr);
-    return FwdPart{l.hi, l.lo, mx, (uint32_t)c, pr};
+    return FwdGPart{l, mx, (uint32_t)c, pr};
 }
 
 // Loss terms of one tile, stored as the tile's partial (lane order within the
@@ -265,7 +282,7 @@ __device__ __forceinline__ ItemInfo item_info(uint4 r, int lane) {
 // box, staged in pairs and evaluated against the lane's two points.
 // Returns the lane's partial sums and pair counts; *cost gets the warp's
 // measured work.
-template <int G, bool ADJ>
+template <int G, int ADJ>
 __device__ __forceinline__ void forward_share(const FwdArgs &a, const ItemInfo &it, int w, float *ringP, float *ringF,
                                               int lane, f2 (&acc)[2], uint32_t (&n)[2], uint32_t &cost,
                                               uint32_t *touch, int &ntouch, float (&tv)[2]) {
@@ -385,11 +402,16 @@ __device__ __forceinline__ void forward_share(const FwdArgs &a, const ItemInfo &
 // padded to an even count) are taken against the kernels that reached the
 // item box in the forward filter, kept if their support reaches the box of
 // those points: lanes are kernels, each lane loops over the points two at a
-// time (packed f32x2) and accumulates the ten App. A moments of its kernel.
-// The item's float partial moments go to per-kernel 64-bit fixed-point
-// accumulators (unit 2^-36) by integer atomics: integer addition is
-// associative, so the totals do not depend on the order in which items
-// finish.
+// time (packed f32x2) and accumulates the ten moments of its kernel in the
+// world frame, Delta = v - c:
+//     S0 = sum s,  W1 = sum s Delta,  W2 = sum s Delta Delta^T,  s = phi E,
+// with phi = 2^(-Delta^T Q Delta) from the forward's own records (so the
+// adjoint evaluates the same quadratic form as the forward).  The kernel
+// frame moments of App. A are M1 = R W1 and M2 = R W2 R^T, formed once per
+// kernel after the launch.  The item's float partial
+// moments go to per-kernel 64-bit fixed-point accumulators (unit 2^-36) by
+// integer atomics: integer addition is associative, so the totals do not
+// depend on the order in which items finish.
 
 struct NzPoints {
     float x[kNz], y[kNz], z[kNz], e[kNz];
@@ -399,7 +421,8 @@ __device__ __forceinline__ f2 f2_dup(float v) { return f2_pack(v, v); }
 
 // v * 2^36 rounded to the nearest integer (halves away from zero), with
 // integer operations only (a float to 64-bit integer conversion would use
-// the slow double-precision unit).  |v| >= 2^26 saturates at 2^62.
+// the slow double-precision unit).  |v| >= 2^26 saturates at 2^62 (the
+// caller flags such a partial before converting it).
 __device__ __forceinline__ long long to_fix36(float v) {
     const uint32_t b = __float_as_uint(v);
     const int e = (int)((b >> 23) & 0xffu);  // biased exponent; 0: zero or below 2^-126
@@ -416,26 +439,37 @@ __device__ __forceinline__ long long to_fix36(float v) {
     return (b >> 31) ? -r : r;
 }
 
+// Compensated (Kahan) accumulation of packed pairs: s + v with the lost
+// low-order part carried in c.
+__device__ __forceinline__ void f2_kadd(f2 &s, f2 &c, f2 v) {
+    const f2 y = f2_sub(v, c);
+    const f2 t = f2_add(s, y);
+    c = f2_sub(f2_sub(t, s), y);
+    s = t;
+}
+
 // A batch of cnt <= 32 kernels from queue slot head: all nz points of the
 // item against each kernel.  A short batch spreads each kernel over
 // L = 2, 4 or 8 neighbouring lanes (cnt <= 16, 8, 4) that take every L-th
 // point pair; their moments are combined with xor shuffles within the group
 // (a fixed order for a given cnt) before the atomics, so short batches do
-// not leave most lanes idle.
+// not leave most lanes idle.  KAHAN: compensated per-lane sums.
+template <bool KAHAN>
 __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *q, int head, int cnt,
                                               const NzPoints &nz, int nc0, int nc1, int lane, uint32_t &pairs) {
     const int sh = cnt > 16 ? 0 : (cnt > 8 ? 1 : (cnt > 4 ? 2 : 3));
     const int L = 1 << sh, kl = lane >> sh, sub = lane & (L - 1);
     const bool act = kl < cnt;  // whole groups of L lanes are inactive together
     const uint32_t j = q[(head + (act ? kl : 0)) & (kQueue - 1)];
-    const float4 k0 = a.kbwd[4 * j], k1 = a.kbwd[4 * j + 1], k2 = a.kbwd[4 * j + 2], k3 = a.kbwd[4 * j + 3];
+    const float4 k0 = a.kfwd[3 * j], k1 = a.kfwd[3 * j + 1], k2 = a.kfwd[3 * j + 2];
     const f2 cx = f2_dup(k0.x), cy = f2_dup(k0.y), cz = f2_dup(k0.z);
-    const f2 r11 = f2_dup(k1.x), r12 = f2_dup(k1.y), r13 = f2_dup(k1.z), e1 = f2_dup(k1.w);
-    const f2 r21 = f2_dup(k2.x), r22 = f2_dup(k2.y), r23 = f2_dup(k2.z), e2 = f2_dup(k2.w);
-    const f2 r31 = f2_dup(k3.x), r32 = f2_dup(k3.y), r33 = f2_dup(k3.z), e3 = f2_dup(k3.w);
-    f2 acc[10];
+    const f2 q11 = f2_dup(k1.x), q22 = f2_dup(k1.y), q33 = f2_dup(k1.z);
+    const f2 q12 = f2_dup(k2.x), q13 = f2_dup(k2.y), q23 = f2_dup(k2.z);  // 2 Q12, 2 Q13, 2 Q23
+    f2 acc[10], cmp[KAHAN ? 10 : 1];
 #pragma unroll
     for (int r = 0; r < 10; ++r) acc[r] = 0ull;
+#pragma unroll
+    for (int r = 0; r < (KAHAN ? 10 : 1); ++r) cmp[r] = 0ull;
     uint32_t np = 0;
 #pragma unroll 1
     for (int seg = 0; seg < 2; ++seg) {
@@ -446,33 +480,48 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
             const f2 px = *reinterpret_cast<const f2 *>(&nz.x[i]), py = *reinterpret_cast<const f2 *>(&nz.y[i]);
             const f2 pz = *reinterpret_cast<const f2 *>(&nz.z[i]), pe = *reinterpret_cast<const f2 *>(&nz.e[i]);
             const f2 dx = f2_sub(px, cx), dy = f2_sub(py, cy), dz = f2_sub(pz, cz);
-            // Eq. 3-15-1, same float operations as the scalar test
-            const f2 d2 = f2_add(f2_add(f2_mul(dx, dx), f2_mul(dy, dy)), f2_mul(dz, dz));
-            float d0, d1;
-            f2_unpack(d2, d0, d1);
-            const bool i0 = d0 < k0.w, i1 = d1 < k0.w;
-            const f2 u1 = f2_fma(r13, dz, f2_fma(r12, dy, f2_mul(r11, dx)));
-            const f2 u2 = f2_fma(r23, dz, f2_fma(r22, dy, f2_mul(r21, dx)));
-            const f2 u3 = f2_fma(r33, dz, f2_fma(r32, dy, f2_mul(r31, dx)));
-            const f2 qv = f2_fma(f2_mul(e3, u3), u3, f2_fma(f2_mul(e2, u2), u2, f2_mul(f2_mul(e1, u1), u1)));
+            const f2 zz = f2_mul(dz, dz);
+            // q = Delta^T Q Delta (log2 units), the forward's operation order
+            const f2 ra = f2_fma(q13, dz, f2_fma(q12, dy, f2_mul(q11, dx)));
+            const f2 rb = f2_fma(q23, dz, f2_mul(q22, dy));
+            const f2 qv = f2_fma(q33, zz, f2_fma(dy, rb, f2_mul(dx, ra)));
             float q0, q1, pe0, pe1;
             f2_unpack(qv, q0, q1);
             f2_unpack(pe, pe0, pe1);
-            const float s0 = i0 ? ex2_approx(-q0) * pe0 : 0.f;
-            const float s1 = i1 ? ex2_approx(-q1) * pe1 : 0.f;
+            float e0 = ex2_approx(-q0), e1 = ex2_approx(-q1);
+            // Eq. 3-15-1, same float operations as the scalar test
+            const f2 d2 = f2_add(f2_add(f2_mul(dx, dx), f2_mul(dy, dy)), zz);
+            float d0, d1;
+            f2_unpack(d2, d0, d1);
+            const bool i0 = d0 < k0.w, i1 = d1 < k0.w;
+            e0 = i0 ? e0 : 0.f;
+            e1 = i1 ? e1 : 0.f;
             np += (uint32_t)(i0 && pe0 != 0.f) + (uint32_t)(i1 && pe1 != 0.f);  // pads have E = 0
-            const f2 sv = f2_pack(s0, s1);
-            const f2 su1 = f2_mul(sv, u1), su2 = f2_mul(sv, u2), su3 = f2_mul(sv, u3);
-            acc[0] = f2_add(acc[0], sv);
-            acc[1] = f2_add(acc[1], su1);
-            acc[2] = f2_add(acc[2], su2);
-            acc[3] = f2_add(acc[3], su3);
-            acc[4] = f2_fma(su1, u1, acc[4]);
-            acc[5] = f2_fma(su1, u2, acc[5]);
-            acc[6] = f2_fma(su1, u3, acc[6]);
-            acc[7] = f2_fma(su2, u2, acc[7]);
-            acc[8] = f2_fma(su2, u3, acc[8]);
-            acc[9] = f2_fma(su3, u3, acc[9]);
+            const f2 sv = f2_mul(f2_pack(e0, e1), pe);
+            const f2 sx = f2_mul(sv, dx), sy = f2_mul(sv, dy), sz = f2_mul(sv, dz);
+            if (KAHAN) {
+                f2_kadd(acc[0], cmp[0], sv);
+                f2_kadd(acc[1], cmp[1], sx);
+                f2_kadd(acc[2], cmp[2], sy);
+                f2_kadd(acc[3], cmp[3], sz);
+                f2_kadd(acc[4], cmp[4], f2_mul(sx, dx));
+                f2_kadd(acc[5], cmp[5], f2_mul(sx, dy));
+                f2_kadd(acc[6], cmp[6], f2_mul(sx, dz));
+                f2_kadd(acc[7], cmp[7], f2_mul(sy, dy));
+                f2_kadd(acc[8], cmp[8], f2_mul(sy, dz));
+                f2_kadd(acc[9], cmp[9], f2_mul(sz, dz));
+            } else {
+                acc[0] = f2_add(acc[0], sv);
+                acc[1] = f2_add(acc[1], sx);
+                acc[2] = f2_add(acc[2], sy);
+                acc[3] = f2_add(acc[3], sz);
+                acc[4] = f2_fma(sx, dx, acc[4]);
+                acc[5] = f2_fma(sx, dy, acc[5]);
+                acc[6] = f2_fma(sx, dz, acc[6]);
+                acc[7] = f2_fma(sy, dy, acc[7]);
+                acc[8] = f2_fma(sy, dz, acc[8]);
+                acc[9] = f2_fma(sz, dz, acc[9]);
+            }
         }
     }
     float v[10];
@@ -480,13 +529,27 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
     for (int r = 0; r < 10; ++r) {
         float lo, hi;
         f2_unpack(acc[r], lo, hi);
-        v[r] = lo + hi;
+        if (KAHAN) {
+            // the two halves and their compensations, as a float-float sum
+            float clo, chi;
+            f2_unpack(cmp[r], clo, chi);
+            const ff t = ff_add(two_sum(lo, -clo), two_sum(hi, -chi));
+            v[r] = t.hi + t.lo;
+        } else {
+            v[r] = lo + hi;
+        }
     }
     for (int o = 1; o < L; o <<= 1) {
 #pragma unroll
         for (int r = 0; r < 10; ++r) v[r] += __shfl_xor_sync(0xffffffffu, v[r], o);
     }
     if (act && sub == 0) {
+        // a partial at or beyond 2^26 (or not finite) does not fit the
+        // fixed-point range: flag it (never taken in a healthy fit)
+        bool out = false;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) out |= !(fabsf(v[r]) < 67108864.f);
+        if (out) atomicOr(a.status, SERBF_FLAG_FIX_RANGE);
         unsigned long long *o = a.adj_fix + 10 * (size_t)j;
 #pragma unroll
         for (int r = 0; r < 10; ++r)
@@ -498,7 +561,7 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
 // One warp's share of an item's adjoint: the kernels this warp found
 // reaching the item box (or, if it found more than kTouch, its candidate
 // chunks of the super cell's list again), filtered against the nz box.
-template <int G>
+template <int G, bool KAHAN>
 __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &it, int w, const NzPoints &nz,
                                               int nc0, int nc1, float4 lo, float4 hi, const uint32_t *touch,
                                               int ntouch, uint32_t *q, int lane, uint32_t &cost) {
@@ -514,7 +577,7 @@ __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &
         const uint32_t j = live ? (listed ? touch[b + lane] : lst[b + lane]) : 0u;
         bool hit = false;
         if (live) {
-            const float4 k0 = a.kbwd[4 * j];
+            const float4 k0 = a.kfwd[3 * j];
             hit = box_d2(k0.x, k0.y, k0.z, lo, hi) < k0.w;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
@@ -523,13 +586,13 @@ __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &
         nk += __popc(bal);
         __syncwarp();
         if (qn >= 32) {
-            adjoint_batch(a, q, head, 32, nz, nc0, nc1, lane, pairs);
+            adjoint_batch<KAHAN>(a, q, head, 32, nz, nc0, nc1, lane, pairs);
             head = (head + 32) & (kQueue - 1);
             qn -= 32;
             __syncwarp();
         }
     }
-    if (qn > 0) adjoint_batch(a, q, head, qn, nz, nc0, nc1, lane, pairs);
+    if (qn > 0) adjoint_batch<KAHAN>(a, q, head, qn, nz, nc0, nc1, lane, pairs);
     __syncwarp();
     const uint32_t tot = redux_add(pairs);
     if (lane == 0 && tot) atomicAdd(a.adj_pairs, (unsigned long long)tot);
@@ -637,7 +700,9 @@ __device__ __forceinline__ void sched_finish(const FwdArgs &a) {
 // 16 for the fused variants with 1 or 4 warps per item and 20 with 2, 24 for
 // eight warps and for the forward alone (20 with one warp); more resident
 // warps measured slower on every workload.
-template <int G, bool ADJ>
+// ADJ: 0 forward only, 1 with the fused adjoint, 2 with the fused adjoint
+// and compensated (Kahan) per-item moment sums.
+template <int G, int ADJ>
 __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 16) : (G == 1 ? 20 : 24))) / G) k_forward(FwdArgs a) {
     pdl_wait();
     pdl_trigger();
@@ -698,7 +763,7 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
                                         a.z[it.v1 ? it.i1 : 0], e1, lane, lo1, hi1);
                 __syncwarp();
                 if (nc0 + nc1 > 0)
-                    adjoint_share<1>(a, it, 0, nzl[0], nc0, nc1, box_min(lo0, lo1), box_max(hi0, hi1), touch[0],
+                    adjoint_share<1, (ADJ > 1)>(a, it, 0, nzl[0], nc0, nc1, box_min(lo0, lo1), box_max(hi0, hi1), touch[0],
                                      ntouch, adjq[0], lane, cost);
                 __syncwarp();
             }
@@ -763,7 +828,8 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
                 const float4 lo = nc1 ? (nc0 ? box_min(s_box[0][0], s_box[1][0]) : s_box[1][0]) : s_box[0][0];
                 const float4 hi = nc1 ? (nc0 ? box_max(s_box[0][1], s_box[1][1]) : s_box[1][1]) : s_box[0][1];
                 uint32_t c = 0;
-                adjoint_share<G>(a, it, warp, nzl[0], nc0, nc1, lo, hi, touch[warp], ntouch, adjq[warp], lane, c);
+                adjoint_share<G, (ADJ > 1)>(a, it, warp, nzl[0], nc0, nc1, lo, hi, touch[warp], ntouch, adjq[warp],
+                                            lane, c);
                 if (lane == 0) red_cost[warp] += c;
             }
             __syncthreads();
@@ -782,7 +848,7 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
     if (threadIdx.x == 0) sched_finish(a);
 }
 
-template <int G, bool ADJ>
+template <int G, int ADJ>
 int launch_forward(const FwdArgs &a, int64_t nitems, int sm_count, cudaStream_t s) {
     static int per_sm = 0;  // resident blocks per SM (same for every device of one kind)
     if (per_sm == 0) {
@@ -805,7 +871,7 @@ int64_t forward_groups(int sm_count) {
     static int per_sm = 0;
     if (per_sm == 0) {
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forward<G, false>, G * 32, 0) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forward<G, 0>, G * 32, 0) != cudaSuccess ||
             nb < 1)
             nb = 1;
         per_sm = nb;
@@ -823,7 +889,7 @@ constexpr int kFinishThreads = 256;
 
 struct FinishArgs {
     const FwdPart *part;
-    FwdPart *gpart;
+    FwdGPart *gpart;
     int64_t ntiles;
     const float *p;
     const int32_t *m_dev;
@@ -832,7 +898,20 @@ struct FinishArgs {
     float *grad;
     uint32_t *counter;
     double *stats;
+    const float4 *kbwd;      // (c, r2) of each kernel
+    float cell_h;            // binning cell edge
+    uint32_t *cell_max;      // [0] most points in one cell, [1] running range bound (float bits)
+    int32_t *status;
 };
+
+// Upper bound of |moment| / max|E| for kernel j: a pair has phi <= 1 and
+// |u_k| <= |v - c| < r, so every moment of the kernel is at most
+// (points within r of c) * max|E| * max(1, r^2); the points within r are at
+// most (cells a ball of radius r can touch) * (most points in one cell).
+__device__ __forceinline__ float moment_bound(float r2, float h, uint32_t cell_max) {
+    const float nc = ceilf(2.f * sqrtf(r2) / h) + 2.f;
+    return fmaxf(1.f, r2) * nc * nc * nc * (float)cell_max;
+}
 
 template <bool ADJ>
 __global__ void __launch_bounds__(kFinishThreads) k_fwd_finish(FinishArgs f) {
@@ -845,7 +924,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_fwd_finish(FinishArgs f) {
     if (g < ngroups) {
         const uint32_t gb = (uint32_t)(g * kFwdGroup);
         const uint32_t ge = (uint32_t)min((int64_t)gb + kFwdGroup, f.ntiles);
-        const FwdPart gp = reduce_parts(f.part, gb, ge, lane);
+        const FwdGPart gp = reduce_parts(f.part, gb, ge, lane);
         if (lane == 0) f.gpart[g] = gp;
     }
     if (ADJ) {
@@ -863,7 +942,9 @@ __global__ void __launch_bounds__(kFinishThreads) k_fwd_finish(FinishArgs f) {
                 M[r] = fmaf(hi, 4294967296.f, lo) * kFixUnitF;
                 o[r] = 0ull;
             }
-            grad_from_moments(f.p, f.cap, j, M, f.grad);
+            grad_from_moments<true>(f.p, f.cap, j, M, f.grad);
+            // positive floats order like their bits (NaN orders above +inf)
+            atomicMax(&f.cell_max[1], __float_as_uint(moment_bound(f.kbwd[4 * j].w, f.cell_h, f.cell_max[0])));
         }
     }
     __syncthreads();
@@ -874,15 +955,20 @@ __global__ void __launch_bounds__(kFinishThreads) k_fwd_finish(FinishArgs f) {
     __syncthreads();
     if (!s_last || warp != 0) return;
     __threadfence();
-    const FwdPart tot = reduce_parts(f.gpart, 0, (uint32_t)ngroups, lane);
+    const FwdGPart tot = reduce_parts(f.gpart, 0, (uint32_t)ngroups, lane);
     if (lane == 0) {
-        f.stats[SERBF_STAT_L2] = (double)tot.l2hi + (double)tot.l2lo;
+        f.stats[SERBF_STAT_L2] = tot.l2;
         f.stats[SERBF_STAT_MAXE] = tot.maxe;
         f.stats[SERBF_STAT_COUNT] = (double)tot.cnt;
         f.stats[SERBF_STAT_PAIRS_FWD] = (double)tot.pairs;
         if (ADJ) {
             f.stats[SERBF_STAT_PAIRS_BWD] = (double)__ldcg(f.pairs);
             *f.pairs = 0ull;
+            // the int64 sums hold |moment| < 2^27 (unit 2^-36); flag when the
+            // bound reaches 2^26, or is not finite
+            const float bound = __uint_as_float(__ldcg(&f.cell_max[1])) * tot.maxe;
+            if (!(bound < 67108864.f)) atomicOr(f.status, SERBF_FLAG_FIX_RANGE);
+            f.cell_max[1] = 0u;
         }
         *f.counter = 0u;
     }
@@ -938,6 +1024,7 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
     a.part = ws->fwd_part;
     a.item_next = ws->counters + 4;
     a.exit_count = ws->counters + 6;
+    a.status = ws->status;
     int rc = SERBF_OK;
     if (ws->ntiles > 0) {
         // warps per item: the fewest that still leave about four items per
@@ -946,21 +1033,26 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
         int G = ni >= 4 * forward_groups<1>(ws->sm_count) ? 1 : (ni >= 4 * forward_groups<2>(ws->sm_count) ? 2 : 4);
         if (cfg->fwd_warps == 1 || cfg->fwd_warps == 2 || cfg->fwd_warps == 4 || cfg->fwd_warps == 8)
             G = cfg->fwd_warps;
-        switch (G * 2 + (adj ? 1 : 0)) {
-            case 2: rc = launch_forward<1, false>(a, ni, ws->sm_count, s); break;
-            case 3: rc = launch_forward<1, true>(a, ni, ws->sm_count, s); break;
-            case 4: rc = launch_forward<2, false>(a, ni, ws->sm_count, s); break;
-            case 5: rc = launch_forward<2, true>(a, ni, ws->sm_count, s); break;
-            case 8: rc = launch_forward<4, false>(a, ni, ws->sm_count, s); break;
-            case 9: rc = launch_forward<4, true>(a, ni, ws->sm_count, s); break;
-            case 16: rc = launch_forward<8, false>(a, ni, ws->sm_count, s); break;
-            default: rc = launch_forward<8, true>(a, ni, ws->sm_count, s); break;
+        const int mode = adj ? (cfg->kahan ? 2 : 1) : 0;
+        switch (G * 4 + mode) {
+            case 4: rc = launch_forward<1, 0>(a, ni, ws->sm_count, s); break;
+            case 5: rc = launch_forward<1, 1>(a, ni, ws->sm_count, s); break;
+            case 6: rc = launch_forward<1, 2>(a, ni, ws->sm_count, s); break;
+            case 8: rc = launch_forward<2, 0>(a, ni, ws->sm_count, s); break;
+            case 9: rc = launch_forward<2, 1>(a, ni, ws->sm_count, s); break;
+            case 10: rc = launch_forward<2, 2>(a, ni, ws->sm_count, s); break;
+            case 16: rc = launch_forward<4, 0>(a, ni, ws->sm_count, s); break;
+            case 17: rc = launch_forward<4, 1>(a, ni, ws->sm_count, s); break;
+            case 18: rc = launch_forward<4, 2>(a, ni, ws->sm_count, s); break;
+            case 32: rc = launch_forward<8, 0>(a, ni, ws->sm_count, s); break;
+            case 33: rc = launch_forward<8, 1>(a, ni, ws->sm_count, s); break;
+            default: rc = launch_forward<8, 2>(a, ni, ws->sm_count, s); break;
         }
     }
     if (rc) return rc;
     FinishArgs f;
     f.part = ws->fwd_part;
-    f.gpart = ws->fwd_gpart;
+    f.gpart = reinterpret_cast<FwdGPart *>(ws->fwd_gpart);
     f.ntiles = ws->ntiles;
     f.p = prm->p;
     f.m_dev = prm->m;
@@ -970,6 +1062,10 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
     f.grad = grad;
     f.counter = ws->counters + 5;
     f.stats = stats;
+    f.kbwd = ws->kbwd;
+    f.cell_h = ws->grid.h;
+    f.cell_max = ws->cell_max;
+    f.status = ws->status;
     const int64_t ngroups = (ws->ntiles + kFwdGroup - 1) / kFwdGroup;
     int64_t nb = (ngroups + kFinishThreads / 32 - 1) / (kFinishThreads / 32);
     if (adj) nb = max(nb, (int64_t)((prm->cap + kFinishThreads - 1) / kFinishThreads));

@@ -3,7 +3,9 @@
 // serbf_normalize_sdf keeps its reduction scratch in the caller's workspace,
 // which the caller has to allocate on the device first.  This variant keeps the
 // scratch in a fixed array of this library instead, for callers that cannot
-// allocate device memory at the point where they need the normalisation.
+// allocate device memory at the point where they need the normalisation: an
+// application that only hands out buffers from its own pool, or a loop that
+// must not allocate once it runs.
 #include <math.h>
 
 #include <mutex>
@@ -25,10 +27,12 @@ static __device__ __align__(256) int g_na_scratch[kNaMaxBlocks];
 
 std::mutex g_na_mutex;
 int *g_na_ptr[kNaMaxDevices] = {nullptr};
+int g_na_sms[kNaMaxDevices] = {0};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the symbol's host-side name is not a device address).
-int na_scratch(int **out) {
+// Device address of the scratch array on the current device and the device's
+// SM count, looked up once per device (the symbol's host-side name is not a
+// device address).
+int na_setup(int **out, int *sms) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return SERBF_ECUDA;
     if (dev < 0 || dev >= kNaMaxDevices) return SERBF_EINVAL;
@@ -36,9 +40,14 @@ int na_scratch(int **out) {
     if (!g_na_ptr[dev]) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) return SERBF_ECUDA;
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            return SERBF_ECUDA;
+        g_na_sms[dev] = n;
         g_na_ptr[dev] = static_cast<int *>(p);
     }
     *out = g_na_ptr[dev];
+    *sms = g_na_sms[dev];
     return SERBF_OK;
 }
 
@@ -100,14 +109,15 @@ extern "C" int serbf_normalize_sdf_noalloc(const float *S, float *t, int64_t n, 
     if (!S || !t || !mh_dev || n <= 0) return SERBF_EINVAL;
     if (n > kNaMaxPoints) return SERBF_ECAPACITY;
     int *scratch = nullptr;
-    int rc = na_scratch(&scratch);
+    int sms = 0;
+    int rc = na_setup(&scratch, &sms);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const int nblocks = (int)((n + kNaItemsPerBlock - 1) / kNaItemsPerBlock);
     k_na_min<<<nblocks, 256, 0, s>>>(S, n, scratch);
     k_na_finish<<<1, 256, 0, s>>>(scratch, nblocks, mh_dev);
     int64_t ab = (n + 255) / 256;
-    if (ab > 152 * 32) ab = 152 * 32;
+    if (ab > (int64_t)sms * 8) ab = (int64_t)sms * 8;  // grid-stride: 8 blocks of 256 per SM
     k_na_apply<<<(unsigned)ab, 256, 0, s>>>(S, t, n, mh_dev);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;

@@ -38,20 +38,20 @@ __device__ void block_sums_ff(const float (&v)[NV], ff (*sh)[NV], ff (&out)[NV])
     __syncthreads();
 }
 
-// Same for three float-float inputs.
-__device__ void block_sums_ff3(const ff (&v)[3], ff (*sh)[3], ff (&out)[3]) {
+// Block sums of three doubles, in a fixed order.
+__device__ void block_sums_d3(const double (&v)[3], double (*sh)[3], double (&out)[3]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const ff s = warp_sum_ff(v[k]);
+        const double s = warp_sum(v[k]);
         if (lane == 0) sh[warp][k] = s;
     }
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            ff t = lane < nw ? sh[lane][k] : ff{0.f, 0.f};
-            t = warp_sum_ff(t);
+            double t = lane < nw ? sh[lane][k] : 0.0;
+            t = warp_sum(t);
             if (lane == 0) sh[32][k] = t;
         }
     }
@@ -72,7 +72,7 @@ struct StepArgs {
     serbf_state *st;
     double *stats;
     serbf_config c;
-    float *part;      // per block partial sums (float-float pairs)
+    float *part;      // per block partial sums
     double *scal;     // alpha, beta, bias corrections for the update kernel
     uint32_t *counter;
 };
@@ -81,34 +81,34 @@ constexpr int kStateWords = (int)(sizeof(serbf_state) / 4);
 static_assert(sizeof(serbf_state) % 8 == 0, "state is copied as 32-bit words");
 
 // ---------------------------------------------------------------- pieces
-// The three sums of Eq. 3-21 and Eq. 3-14_2 for kernel j: |w|, and with the
-// L1 term on, (g1 - g2) g1 and |g2 - g1|^2 on the weight gradients.
-__device__ __forceinline__ void alpha_terms(const StepArgs &a, int j, bool use_l1, float (&part)[3]) {
-    const float w = a.p[PW * a.cap + j], g2 = a.grad[PW * a.cap + j];
-    part[0] += fabsf(w);
+// The three sums of Eq. 3-21 and Eq. 3-14_2 for kernel j, in double: |w|,
+// and with the L1 term on, (g1 - g2) g1 and |g2 - g1|^2 on the weight
+// gradients (one term per kernel, so FP64 costs nothing here).
+__device__ __forceinline__ void alpha_terms(const StepArgs &a, int j, bool use_l1, double (&part)[3]) {
+    const double w = a.p[PW * a.cap + j], g2 = a.grad[PW * a.cap + j];
+    part[0] += fabs(w);
     if (use_l1) {
-        const float g1 = sgnf(w);
+        const double g1 = (double)((w > 0.0) - (w < 0.0));
         part[1] += (g1 - g2) * g1;
         part[2] += (g2 - g1) * (g2 - g1);
     }
 }
 
-// alpha (clamped to [0, 1]; 1 when the L1 term is off or the two gradients
-// coincide), beta = 1 - alpha, the Adam bias corrections; writes the stats.
-// sc = {alpha, beta, 1 - beta1^t, 1 - beta2^t}.
-__device__ __forceinline__ void alpha_finish(const StepArgs &a, bool use_l1, const ff (&fin)[3], float (&sc)[4]) {
-    // float arithmetic (FP64 is slow on this part): alpha to ~1e-7
-    const float num = fin[1].hi + fin[1].lo, den = fin[2].hi + fin[2].lo;
-    float al = 1.f;
-    if (use_l1 && den > 0.f) al = fminf(1.f, fmaxf(0.f, num / den));
-    const float t = (float)(a.st->adam_t + 1);
+// alpha of Eq. 3-21 in double (clamped to [0, 1]; 1 when the L1 term is off
+// or the two gradients coincide), beta = 1 - alpha, the Adam bias
+// corrections; writes the stats.  sc = {alpha, beta, 1 - beta1^t, 1 - beta2^t}.
+__device__ __forceinline__ void alpha_finish(const StepArgs &a, bool use_l1, const double (&fin)[3], double (&sc)[4]) {
+    const double num = fin[1], den = fin[2];
+    double al = 1.0;
+    if (use_l1 && den > 0.0) al = fmin(1.0, fmax(0.0, num / den));
+    const double t = (double)(a.st->adam_t + 1);
     sc[0] = al;
-    sc[1] = 1.f - al;
-    sc[2] = 1.f - powf((float)a.c.beta1, t);
-    sc[3] = 1.f - powf((float)a.c.beta2, t);
-    a.stats[SERBF_STAT_L1] = (double)fin[0].hi + (double)fin[0].lo;
+    sc[1] = 1.0 - al;
+    sc[2] = 1.0 - pow(a.c.beta1, t);
+    sc[3] = 1.0 - pow(a.c.beta2, t);
+    a.stats[SERBF_STAT_L1] = fin[0];
     a.stats[SERBF_STAT_ALPHA] = al;
-    a.stats[SERBF_STAT_BETA] = 1.f - al;
+    a.stats[SERBF_STAT_BETA] = 1.0 - al;
 }
 
 // tau_d rounded up to float: |w| >= taud decides as in double.
@@ -142,7 +142,7 @@ __device__ __forceinline__ float adam_param(const StepArgs &a, int r, int j, con
 // e < T^e), Eq. l1_activate (population std of the last k^l2 L2 values <
 // tau^l2), Eq. add_activate (range of the last k^l1 values of b_f < tau^l1),
 // the L2-only phase with a cosine learning rate from T^e.
-__device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float alpha, float beta, int lane) {
+__device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, double alpha, double beta, int lane) {
     // per step: Adam counter, alpha/beta, the epoch's L2 sum; the gates only
     // after the epoch's last step (every step when epoch_steps <= 1)
     const int steps = a.c.epoch_steps > 1 ? a.c.epoch_steps : 1;
@@ -157,7 +157,7 @@ __device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float 
             st.beta = beta;
             st.adam_t = st.adam_t + 1;
             a.stats[SERBF_STAT_BF] = bf;
-            a.stats[SERBF_STAT_LOSS] = (float)alpha * (float)l2_step + (float)beta * (float)a.stats[SERBF_STAT_L1];
+            a.stats[SERBF_STAT_LOSS] = alpha * l2_step + beta * a.stats[SERBF_STAT_L1];
         }
         return;
     }
@@ -175,27 +175,18 @@ __device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float 
     const int n_l2 = st.n_l2, n_bf = st.n_bf;
     const int do_prune = (e % kl2 == 0) && l1n && (e < a.c.T_e);
     if (!l1n && !phase2 && e >= kl2 && n_l2 == kl2) {
-        // population std of the last k_l2 values; each double is split into
-        // a float-float pair so the mean and deviations keep ~48 bits
-        ff v{0.f, 0.f};
+        // population std of the last k_l2 values, in double (the convergence
+        // test of Eq. l1_activate; at most 64 values)
+        double v = 0.0;
+        for (int k = lane; k < kl2; k += 32) v += st.l2_hist[k];
+        const double mean = warp_sum(v) / (double)kl2;
+        double var = 0.0;
         for (int k = lane; k < kl2; k += 32) {
-            const double x = st.l2_hist[k];
-            const float xh = (float)x;
-            v = ff_add(v, ff{xh, (float)(x - (double)xh)});
+            const double d = st.l2_hist[k] - mean;
+            var += d * d;
         }
-        v = warp_sum_ff(v);
-        const float inv = 1.f / (float)kl2;
-        const ff mean{v.hi * inv, v.lo * inv};
-        float var = 0.f;
-        for (int k = lane; k < kl2; k += 32) {
-            const double x = st.l2_hist[k];
-            const float xh = (float)x;
-            const ff d = ff_add(ff{xh, (float)(x - (double)xh)}, ff{-mean.hi, -mean.lo});
-            const float dd = d.hi + d.lo;
-            var = fmaf(dd, dd, var);
-        }
-        var = warp_sum(var) * inv;
-        if (sqrtf(var) < (float)a.c.tau_l2) l1n = 1;
+        var = warp_sum(var) / (double)kl2;
+        if (sqrt(var) < a.c.tau_l2) l1n = 1;
     }
     int do_add = 0;
     if (l1n && !phase2 && n_bf == kl1) {
@@ -239,17 +230,17 @@ __device__ void epoch_tail(const StepArgs &a, serbf_state &st, double bf, float 
         st.lr = lr_next;
         st.epoch = e;
         a.stats[SERBF_STAT_BF] = bf;
-        a.stats[SERBF_STAT_LOSS] = (float)alpha * (float)l2_step + (float)beta * (float)a.stats[SERBF_STAT_L1];
+        a.stats[SERBF_STAT_LOSS] = alpha * l2_step + beta * a.stats[SERBF_STAT_L1];
     }
 }
 
 // The epoch tail (warp 0) on a shared-memory copy of the state, written back.
-__device__ void finish_step(const StepArgs &a, double bf, const float (&sc)[4], uint32_t *s_words) {
+__device__ void finish_step(const StepArgs &a, double bf, double alpha, double beta, uint32_t *s_words) {
     const uint32_t *gw = reinterpret_cast<const uint32_t *>(a.st);
     for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) s_words[k] = gw[k];
     __syncthreads();
     serbf_state &st = *reinterpret_cast<serbf_state *>(s_words);
-    if (threadIdx.x < 32) epoch_tail(a, st, bf, sc[0], sc[1], threadIdx.x);
+    if (threadIdx.x < 32) epoch_tail(a, st, bf, alpha, beta, threadIdx.x);
     __syncthreads();
     uint32_t *gwo = reinterpret_cast<uint32_t *>(a.st);
     for (int k = threadIdx.x; k < kStateWords; k += blockDim.x) gwo[k] = s_words[k];
@@ -261,35 +252,31 @@ __device__ void finish_step(const StepArgs &a, double bf, const float (&sc)[4], 
 __global__ void __launch_bounds__(kStepThreads) k_step_alpha(StepArgs a) {
     pdl_wait();
     pdl_trigger();
-    __shared__ ff sh3[33][3];
+    __shared__ double sh3[33][3];
     __shared__ bool s_last;
     const int m = *a.m;
     const bool use_l1 = a.st->l1_optim && (a.stats[SERBF_STAT_MAXE] < a.c.tau_m);
-    float part[3] = {0.f, 0.f, 0.f};
+    double part[3] = {0.0, 0.0, 0.0};
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < m) alpha_terms(a, j, use_l1, part);
-    ff tot[3];
-    block_sums_ff<3>(part, sh3, tot);
+    double tot[3];
+    block_sums_d3(part, sh3, tot);
+    double *bp = reinterpret_cast<double *>(a.part);  // 3 doubles per block
     if (threadIdx.x == 0) {
-        float *o = a.part + 6 * blockIdx.x;
-        for (int k = 0; k < 3; ++k) {
-            o[2 * k] = tot[k].hi;
-            o[2 * k + 1] = tot[k].lo;
-        }
+        for (int k = 0; k < 3; ++k) bp[3 * blockIdx.x + k] = tot[k];
         __threadfence();
         s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    ff acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    double acc[3] = {0.0, 0.0, 0.0};
     for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
-        for (int k = 0; k < 3; ++k)
-            acc[k] = ff_add(acc[k], ff{__ldcg(a.part + 6 * b + 2 * k), __ldcg(a.part + 6 * b + 2 * k + 1)});
-    ff fin[3];
-    block_sums_ff3(acc, sh3, fin);
+        for (int k = 0; k < 3; ++k) acc[k] += __ldcg(bp + 3 * b + k);
+    double fin[3];
+    block_sums_d3(acc, sh3, fin);
     if (threadIdx.x == 0) {
-        float sc[4];
+        double sc[4];
         alpha_finish(a, use_l1, fin, sc);
         for (int k = 0; k < 4; ++k) a.scal[k] = sc[k];
         *a.counter = 0u;
@@ -326,7 +313,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
     for (unsigned b = threadIdx.x; b < nblocks; b += blockDim.x) cnt += __ldcg(a.part + b);
     float cc[1] = {cnt};
     block_sums_ff<1>(cc, sh1, tot);
-    finish_step(a, (double)tot[0].hi + tot[0].lo, sc, s_words);
+    finish_step(a, (double)tot[0].hi + tot[0].lo, a.scal[0], a.scal[1], s_words);
     if (threadIdx.x == 0) a.counter[1] = 0u;
 }
 

@@ -1,0 +1,112 @@
+"""The largest single-GPU field (60 random primitives on a 256^3 band + far
+field, 9.4 M points, M = 16384) through the C ABI in the launch configuration
+the bench times: two-level neighbour rebuild, fused forward + adjoint with one
+warp per work item.  The oracle checks sampled outputs it can compute one by
+one: the binning (bit-exact), Psi and the support pair counts at every point of
+the 64^3 sub-lattice (every 4th grid point per axis), and the App. A gradients
+of 256 kernels around a random location (their residuals from the oracle's own
+forward)."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+FWD_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def c4():
+    torch = torch_cuda()
+    from paper_2505_02350_gb300 import build, field
+    build.build()
+    cfg, lay, P = synth.workload("c4")
+    x, y, z, S = lay[0]
+    m = cfg["m"]
+    pb = field.Problem(x, y, z, S, P, m, synth.spacing(256), cap=2 * m, super_factor=4)
+    pb.cfg.fwd_warps = 1
+    pb.build_neighbors()
+    pb.forward_backward()
+    torch.cuda.synchronize()
+    return torch, pb, (x, y, z, S, np.asarray(P, np.float64)[:, :m], m)
+
+
+def test_c4_binning_and_launch_configuration(c4, orc):
+    torch, pb, (x, y, z, S, P, m) = c4
+    assert pb.n == x.size > 9_000_000
+    assert pb.launches_per_epoch() == 12  # the two-level rebuild
+    assert pb.status()[0] == 0
+    g = pb.grid
+    orc.set_threads(os.cpu_count() or 1)
+    perm = orc.bin_points(x, y, z, tuple(g.origin), g.h, tuple(g.n), pb.sizes.super_factor)
+    np.testing.assert_array_equal(pb.perm[:pb.n].cpu().numpy().astype(np.uint32), perm)
+
+
+def test_c4_forward_on_the_64_sublattice(c4, orc):
+    torch, pb, (x, y, z, S, P, m) = c4
+    from paper_2505_02350_gb300 import _native as N
+    n = pb.n
+    orc.set_threads(os.cpu_count() or 1)
+    sp = synth.spacing(256)
+    ix, iy, iz = (np.rint((v.astype(np.float64) + 1.0) / sp).astype(np.int64) for v in (x, y, z))
+    sel = np.flatnonzero((ix % 4 == 0) & (iy % 4 == 0) & (iz % 4 == 0))
+    assert sel.size > 50_000
+    perm = pb.perm[:n].cpu().numpy().astype(np.int64)
+    inv = np.empty(n, np.int64)
+    inv[perm] = np.arange(n)
+    pos = inv[sel]
+    t_or = orc.normalize(S)[0].astype(np.float32)
+    psi_o, _E, _mask, st = orc.forward(x[sel], y[sel], z[sel], t_or[sel], P, m)
+    psi = pb.psi[:n].cpu().numpy()[pos]
+    assert np.abs(psi - psi_o).max() <= FWD_TOL * float(np.abs(t_or).max())
+    # support pair counts per point: the point-major CSR row pointers (the
+    # column capacity is left too small on purpose; the row pointers are
+    # still written and the call reports the capacity)
+    rowptr = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    col = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc, npairs = N.serbf_build_neighbors(pb.pts, pb.prm, pb.cfg, pb.ws, None, N.csr(rowptr, col))
+    assert rc == N.SERBF_ECAPACITY and npairs == pb.stats[4].item()
+    cnt = np.diff(rowptr.cpu().numpy())[pos]
+    _kr, _kc, prow, _pc = orc.neighbors(x[sel], y[sel], z[sel], P, m, cols=False)
+    np.testing.assert_array_equal(cnt, np.diff(prow))
+    assert st[4] == cnt.sum()
+
+
+def test_c4_gradients_of_256_kernels(c4, orc):
+    torch, pb, (x, y, z, S, P, m) = c4
+    n = pb.n
+    orc.set_threads(os.cpu_count() or 1)
+    g = np.random.default_rng(4)
+    centre = P[0:3, g.integers(m)]
+    d2c = np.sum((P[0:3] - centre[:, None]) ** 2, axis=0)
+    ks = np.sort(np.argsort(d2c, kind="stable")[:256])
+    perm = pb.perm[:n].cpu().numpy().astype(np.int64)
+    xb, yb, zb = x[perm], y[perm], z[perm]
+    t_or = orc.normalize(S)[0].astype(np.float32)[perm]
+    # the oracle's residuals at every point the sampled kernels may reach
+    near = np.zeros(n, bool)
+    for j in ks:
+        d = P[3:6, j]
+        r2 = 16.118095650958319 / np.min(d * d)
+        near |= (xb - P[0, j]) ** 2 + (yb - P[1, j]) ** 2 + (zb - P[2, j]) ** 2 < 1.01 * r2
+    sub = np.flatnonzero(near)
+    E = np.zeros(n)
+    _psi, E_sub, mask_sub, _st = orc.forward(xb[sub], yb[sub], zb[sub], t_or[sub], P, m)
+    E[sub] = E_sub
+    # Eq. 3-18 decisions at borderline points may differ between float and
+    # double Psi: bounded, and only where they agree are the residuals compared
+    mask_gpu = pb.mask[:n].cpu().numpy()[sub].astype(bool)
+    flips = np.count_nonzero(mask_gpu != mask_sub.astype(bool))
+    assert flips <= max(3, sub.size // 10_000)
+    both = mask_gpu & mask_sub.astype(bool)
+    err_gpu = pb.err[:n].cpu().numpy()[sub]
+    assert np.abs(err_gpu[both] - E_sub[both]).max() <= FWD_TOL * float(np.abs(t_or).max())
+    g_o, _ = orc.backward(xb, yb, zb, E, P[:, ks].copy(), len(ks))
+    gk = pb.grad[:, ks].cpu().numpy()
+    for sl in (slice(0, 3), slice(3, 6), slice(6, 9), slice(9, 10)):
+        assert rel_l2(gk[sl], g_o[sl]) <= GRAD_TOL

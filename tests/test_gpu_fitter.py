@@ -100,3 +100,45 @@ def test_octree_layers_fit():
     assert pb.n == total
     msq = [h["l2"] / max(h["count"], 1) for h in hist]
     assert np.isfinite(msq).all() and min(msq[-5:]) < msq[0]
+
+
+def test_octree_layers_match_oracle_after_each_append(orc):
+    """Each octree layer appended to the training set (Sec. 3.4.2): the
+    binning of the grown set, its targets and the first forward after the
+    append against the oracle -- its own binning, its own Eq. 3-10 map over
+    all layers, its own forward with the GPU's current parameters."""
+    torch = torch_cuda()
+    from paper_2505_02350_gb300 import build, field
+    build.build()
+    sphere = lambda x, y, z: np.sqrt(x * x + y * y + z * z) - 0.5
+    layers = synth.octree_layers(sphere, 4, 6)
+    ts = field.normalize_layers([l[3] for l in layers])
+    t_or_all, _, _ = orc.normalize(np.concatenate([l[3] for l in layers]))
+    t_or_all = t_or_all.astype(np.float32)
+    np.testing.assert_allclose(np.concatenate(ts), t_or_all, rtol=2 ** -23, atol=0)
+    total = sum(l[0].size for l in layers)
+    finest = layers[-1][4]
+    g = field.grid_for(finest)
+    x, y, z, S, _ = layers[0]
+    pb = field.Problem(x, y, z, S, np.zeros((10, 2048), np.float32), 0, finest, max_points=total, t=ts[0],
+                       cap=2048, max_cells=g.n[0] * g.n[1] * g.n[2])
+    pb.init_kernels()
+    for k in range(1, len(layers)):
+        for _ in range(10):
+            pb.epoch()
+        l = layers[k]
+        pb.refine(l[0], l[1], l[2], l[3], ts[k], spacing=finest)
+        pb.build_neighbors()
+        pb.forward()
+        torch.cuda.synchronize()
+        n, m = pb.n, pb.m()
+        xs, ys, zs = (np.concatenate([layers[q][c] for q in range(k + 1)]) for c in range(3))
+        perm = orc.bin_points(xs, ys, zs, tuple(pb.grid.origin), pb.grid.h, tuple(pb.grid.n),
+                              pb.sizes.super_factor).astype(np.int64)
+        np.testing.assert_array_equal(pb.perm[:n].cpu().numpy().astype(np.int64), perm)
+        t_or = t_or_all[:n][perm]
+        np.testing.assert_allclose(pb.tb[:n].cpu().numpy(), t_or, rtol=2 ** -23, atol=0)
+        P = pb.p[:, :m].cpu().numpy().astype(np.float64)
+        psi_o, _E, _mask, st = orc.forward(xs[perm], ys[perm], zs[perm], t_or, P, m)
+        assert pb.stats[4].item() == st[4]
+        assert np.abs(pb.psi[:n].cpu().numpy() - psi_o).max() <= 1e-5 * np.abs(t_or).max()
