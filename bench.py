@@ -39,7 +39,7 @@ ADJ_INSTR_PER_PAIR = 32  # minimum FP32-pipe instructions of one adjoint pair (r
 # split, valid only for the library version it was taken with (any other
 # version, workload or split reports null)
 TRAFFIC_BYTES = {}  # (library version, workload, warps per item) -> bytes
-DEFAULT_STEPS = {"c1": 3000, "c2": 3000, "c3": 500, "c4": 200, "c5": 100}
+DEFAULT_STEPS = {"c1": 3000, "c2": 3000, "c3": 500, "c4": 200, "c5": 2000}
 WORKLOADS = {
     "c1": ("sphere |x|-0.5 on 32^3, M=64 isotropic", None),
     "c2": ("torus R=0.5 r=0.2 on 32^3+64^3 union (after 32^3->64^3 refinement), M=512 anisotropic", [32, 64]),
@@ -321,70 +321,101 @@ def run_native(args, ws, rank, local):
 
 
 def run_batched(args, ws, rank, local):
-    """Time-to-fit of the batched solve: E epochs of all c5 shapes as one
-    graph launch per epoch, against the plain loop that launches each
-    shape's epoch graph in turn.  Both start from the same snapshot and run
-    the same arithmetic, so each shape ends at the same RMSE (checked)."""
+    """Time-to-fit of the batched solve (c5): 64 fields of uneven sizes fitted
+    for E epochs (the Algorithm 3 schedule to M^e) by the plain per-field loop
+    -- each field's epoch graph launched in turn -- which fixes every field's
+    target RMSE, then by the batched solve -- one graph per epoch around
+    serbf_epoch_batched, one persistent forward + adjoint launch for all
+    fields -- from the same snapshot, run until every field reaches its
+    target.  Both use the same warps per item, so the trajectories are the
+    same bits and the batch reaches the targets at epoch E (checked)."""
     import torch
     from paper_2505_02350_gb300 import batch, field
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     shapes = synth.batch_workload(64, device=dev)
-    pbs = [field.Problem(sh["x"], sh["y"], sh["z"], sh["S"], sh["P"], sh["m"], sh["spacing"], cap=2 * sh["m"],
+    pbs = [field.Problem(sh["x"], sh["y"], sh["z"], sh["S"], sh["P"], sh["m"], sh["spacing"], cap=4 * sh["m"],
                          device=dev) for sh in shapes]
     for pb in pbs:
         for _ in range(args.warmup):
             pb.epoch()
-        pb.capture(split=False)
+    torch.cuda.synchronize()
     bt = batch.Batch(pbs)
+    tune = bt.autotune() if not args.fwd_warps else {}
+    if args.fwd_warps:
+        bt._init(args.fwd_warps)
+    for pb in pbs:
+        pb.cfg.fwd_warps = bt.fwd_warps  # the loop takes the batch's split: the same bits
+        pb.capture(split=False)
     bt.capture()
     torch.cuda.synchronize()
     snap = bt.snapshot()
-    E = min(args.steps, 200)
+    E = args.steps
+    chunk = 100
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
-    def timed(step):
-        flush.fill_(1)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+    def run_loop():
         for _ in range(E):
-            step()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / 1e3
-
-    def loop_step():
-        for pb in pbs:
-            pb.epoch_graph()
+            for pb in pbs:
+                pb.epoch_graph()
 
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.2)
-    t0 = time.time()
-    t_loop = timed(loop_step)
-    r_loop = bt.rmse()
+    t0w = time.time()
+    flush.fill_(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    run_loop()
+    e1.record()
+    torch.cuda.synchronize()
+    t_loop = e0.elapsed_time(e1) / 1e3
+    target = bt.rmse()
     bt.restore(snap)
-    t_batch = timed(bt.epoch_graph)
-    r_batch = bt.rmse()
-    sampler.mark(t0, time.time())
+    flush.fill_(2)
+    torch.cuda.synchronize()
+    # the batched solve to the targets: graph replays in chunks, every
+    # field's RMSE read after each chunk (host reads inside the timed span)
+    tb = time.perf_counter()
+    e0.record()
+    done = 0
+    while True:
+        for _ in range(min(chunk, 10 * E - done)):
+            bt.epoch_graph()
+        done += min(chunk, 10 * E - done)
+        r = bt.rmse()
+        if all(a <= b for a, b in zip(r, target)) or done >= 10 * E:
+            break
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    wall_batch = time.perf_counter() - tb
+    sampler.mark(t0w, time.time())
     clocks = sampler.stop()
+    from paper_2505_02350_gb300 import _native as N
     flags = [pb.status()[0] for pb in pbs]
-    if any(flags):
-        raise RuntimeError("capacity flags %s" % flags)
-    same = r_loop == r_batch
+    if any(f & ~N.FLAG_ADD_CAPACITY for f in flags):
+        raise RuntimeError("status flags %s" % flags)
     return {
-        "metric": "time-to-fit at fixed RMSE (%d epochs of 64 shapes)" % E, "value": t_batch, "unit": "s",
-        "n_gpus": ws, "steps": E, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / E, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": "time-to-fit at fixed RMSE (64 fields, batched vs per-field loop)", "value": t_batch, "unit": "s",
+        "n_gpus": ws, "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / max(done, 1),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOADS["c5"][0], "config": "c5", "shapes": len(pbs),
-                   "points": int(sum(pb.n for pb in pbs)), "kernels": int(sum(pb.m() for pb in pbs)),
-                   "batched": "one CUDA graph per epoch, one stream per shape",
-                   "loop": "one CUDA graph launch per shape per epoch, in turn",
-                   "l2_flush": "256 MiB buffer written before each timed run"},
-        "loop_s": t_loop, "speedup_vs_loop": t_loop / t_batch,
-        "rmse": {"mean": float(np.mean(r_batch)), "max": float(np.max(r_batch)), "identical_to_loop": bool(same)},
-        "clocks": clocks,
+                   "points": int(sum(pb.n for pb in pbs)), "kernels_start": int(sum(sh["m"] for sh in shapes)),
+                   "kernels_end": int(sum(pb.m() for pb in pbs)), "fwd_warps": bt.fwd_warps,
+                   "autotune_ms": {str(k): round(v, 4) for k, v in tune.items()},
+                   "batched": "serbf_epoch_batched in one CUDA graph per epoch: one persistent forward + adjoint "
+                              "launch over every field's work items, one launch per other stage",
+                   "loop": "each field's epoch graph (11 launches) in turn",
+                   "target": "each field's RMSE after the loop's %d epochs (Algorithm 3 to M^e)" % E,
+                   "check_every": chunk, "l2_flush": "256 MiB buffer written before each timed run"},
+        "loop_s": t_loop, "speedup_vs_loop": t_loop / t_batch, "epochs_to_target": done,
+        "fields_additions_truncated": int(sum(1 for f in flags if f & N.FLAG_ADD_CAPACITY)),
+        "rmse": {"mean": float(np.mean(r)), "max": float(np.max(r)), "identical_to_loop": bool(r == target),
+                 "target_mean": float(np.mean(target))},
+        "gpu_launches": done * (11 + 1), "gpu_launches_basis": "at most 12 kernels per batched epoch",
+        "wall_batch_s": wall_batch, "clocks": clocks,
     }
 
 

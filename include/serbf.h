@@ -344,7 +344,8 @@ int serbf_backward(const serbf_points *pts, const serbf_params *prm, const serbf
  * and order-independent, each item's partial rounded to 2^-36; it equals
  * serbf_backward's up to float rounding.  The fixed-point range is
  * |moment| < 2^27: a partial beyond 2^26, or a bound of max|E| x (points
- * within a kernel's support radius) x max(1, r^2) reaching 2^26, sets
+ * within a kernel's support radius) x max(1, min(r^2, far^2)) reaching 2^26
+ * (far = distance from the centre to the farthest corner of the points' box), sets
  * SERBF_FLAG_FIX_RANGE (read with serbf_status; the call itself does not
  * wait for the device).  Two launches.  EINVAL as serbf_forward, or when
  * grad is NULL. */
@@ -397,6 +398,56 @@ int serbf_refine(float *x_all, float *y_all, float *z_all, float *t_all, float *
                  const float *x_new, const float *y_new, const float *z_new, const float *t_new,
                  const float *s_new, int64_t n_new, const serbf_grid *grid, uint32_t *perm, float *xb,
                  float *yb, float *zb, float *tb, float *sb, serbf_workspace *ws, void *stream);
+
+/* ------------------------------------------------------------------ batches of fields */
+/* One field of a batch: the arguments of its single-field epoch calls
+ * (serbf_build_neighbors, serbf_forward_backward, serbf_step, serbf_prune,
+ * serbf_add_kernels), all device buffers owned by the caller, and its binned
+ * workspace (serbf_bin_points done).  cfg->fwd_warps is ignored (the batch
+ * uses one split for every field); cfg->kahan must be the same for all. */
+typedef struct {
+    serbf_points pts;
+    const float *S_raw;          /* raw signed distances, binned order */
+    float *psi, *err;            /* n */
+    uint8_t *mask;               /* n */
+    serbf_params prm;
+    float *grad, *adam_m, *adam_v; /* 10 x cap */
+    serbf_state *st;
+    double *stats;
+    const serbf_config *cfg;
+    serbf_workspace *ws;
+} serbf_field;
+
+typedef struct serbf_batch serbf_batch; /* opaque, host memory of serbf_batch_struct_size() bytes */
+
+size_t serbf_batch_struct_size(void);
+
+/* Device bytes of the batch tables for nfields (1..1024) fields. */
+int serbf_batch_bytes(int32_t nfields, size_t *bytes);
+
+/* Records every field's arguments in the caller's device buffer `dev`
+ * (>= serbf_batch_bytes, 256-byte aligned) and sizes the batch's grids.
+ * fwd_warps: warps per forward work item for all fields (1, 2, 4, 8; 0 =
+ * chosen from the total item count).  Re-initialise after any field is
+ * re-binned (refinement).  SYNCHRONISES the stream.  EINVAL on bad fields
+ * (not binned, mismatched kahan, NULL buffers), ENOMEM when bytes is too
+ * small, ECAPACITY beyond 2^32 work items. */
+int serbf_batch_init(serbf_batch *b, const serbf_field *fields, int32_t nfields, int32_t fwd_warps, void *dev,
+                     size_t bytes, void *stream);
+
+/* The warps per forward work item the batch uses. */
+int serbf_batch_warps(const serbf_batch *b);
+
+/* One Algorithm 3 epoch of every field (full batch): neighbour rebuild
+ * (Eq. 3-15-1), fused forward + adjoint (Eq. 3-26, 3-18, 3-19, App. A) as
+ * ONE persistent launch over the work items of all fields, the finishing
+ * reductions, the Eq. 3-21 / Adam step with the Algorithm 3 gates, Eq. 3-27
+ * deletion and Algorithm 2 addition -- twelve launches or fewer whatever
+ * the number of fields, asynchronous, capturable into a CUDA graph.  Each
+ * field's results are bit-identical to its single-field epoch with the same
+ * warps per item (no floating-point atomics; every reduction has a fixed
+ * order).  Status flags go to each field's workspace. */
+int serbf_epoch_batched(serbf_batch *b, void *stream);
 
 #ifdef __cplusplus
 }

@@ -53,12 +53,16 @@ float oracle_support_r2(float d1, float d2, float d3, float neg_ln_eps) {
     return neg_ln_eps / lam;
 }
 
+/* The canonical float squared distance of the membership test: the three
+ * differences, then fl(dx dx) and two fused multiply-adds (fmaf rounds once,
+ * C99), fmaf(dz, dz, fmaf(dy, dy, dx * dx)).  Reading: the paper states the
+ * test in real arithmetic; the float form is fixed so that every
+ * implementation takes the same integer decision. */
+static float support_d2(float dx, float dy, float dz) { return fmaf(dz, dz, fmaf(dy, dy, dx * dx)); }
+
 int oracle_in_support(float px, float py, float pz, float cx, float cy, float cz, float r2) {
     float dx = px - cx, dy = py - cy, dz = pz - cz;
-    float xx = dx * dx, yy = dy * dy, zz = dz * dz;
-    float s = xx + yy;
-    float d2 = s + zz;
-    return d2 < r2;
+    return support_d2(dx, dy, dz) < r2;
 }
 
 /* ---------------------------------------------------------------------------
@@ -578,9 +582,7 @@ int32_t oracle_local_max(const float *x, const float *y, const float *z, const f
         for (int64_t q = 0; q < n && ok; ++q) {
             if (!mask[q]) continue;
             float dx = x[q] - x[i], dy = y[q] - y[i], dz = z[q] - z[i];
-            float xx = dx * dx, yy = dy * dy, zz = dz * dz;
-            float s = xx + yy;
-            float d2 = s + zz;
+            float d2 = support_d2(dx, dy, dz);
             if (d2 <= r2 && fabsf(E[q]) > ei) ok = 0;
         }
         if (ok) out[o++] = i;
@@ -642,7 +644,7 @@ int32_t oracle_inscribed(const float *x, const float *y, const float *z, const f
         for (int64_t k = 0; k < n; ++k) {
             if (!alive[k]) continue;
             const float dx = x[k] - x[best], dy = y[k] - y[best], dz = z[k] - z[best];
-            const float d2 = (dx * dx + dy * dy) + dz * dz;
+            const float d2 = support_d2(dx, dy, dz);
             if (!(d2 > r2)) {
                 alive[k] = 0;
                 --left;

@@ -69,6 +69,13 @@ class WsSizes(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class Field(C.Structure):
+    _fields_ = [("pts", Points), ("S_raw", C.c_void_p), ("psi", C.c_void_p), ("err", C.c_void_p),
+                ("mask", C.c_void_p), ("prm", Params), ("grad", C.c_void_p), ("adam_m", C.c_void_p),
+                ("adam_v", C.c_void_p), ("st", C.c_void_p), ("stats", C.c_void_p), ("cfg", C.POINTER(Config)),
+                ("ws", C.c_void_p)]
+
+
 VP = C.c_void_p
 _SIGS = {
     "serbf_version": (C.c_char_p, []),
@@ -106,6 +113,11 @@ _SIGS = {
                                     C.POINTER(Config), C.c_int, VP, VP]),
     "serbf_refine": (C.c_int, [VP, VP, VP, VP, VP, C.c_int64, VP, VP, VP, VP, VP, C.c_int64, C.POINTER(Grid),
                                VP, VP, VP, VP, VP, VP, VP, VP]),
+    "serbf_batch_struct_size": (C.c_size_t, []),
+    "serbf_batch_bytes": (C.c_int, [C.c_int32, C.POINTER(C.c_size_t)]),
+    "serbf_batch_init": (C.c_int, [VP, C.POINTER(Field), C.c_int32, C.c_int32, VP, C.c_size_t, VP]),
+    "serbf_batch_warps": (C.c_int, [VP]),
+    "serbf_epoch_batched": (C.c_int, [VP, VP]),
 }
 
 
@@ -320,6 +332,32 @@ def serbf_refine(x_all, y_all, z_all, t_all, s_all, n_old, x_new, y_new, z_new, 
 def workspace_struct():
     """Host storage for one serbf_workspace (opaque)."""
     return C.create_string_buffer(_lib.serbf_workspace_struct_size())
+
+
+def batch_struct():
+    """Host storage for one serbf_batch (opaque)."""
+    return C.create_string_buffer(_lib.serbf_batch_struct_size())
+
+
+def serbf_batch_bytes(nfields):
+    b = C.c_size_t()
+    _check("serbf_batch_bytes", _lib.serbf_batch_bytes(int(nfields), C.byref(b)))
+    return b.value
+
+
+def serbf_batch_init(b_host, fields, fwd_warps, dev, stream=None):
+    arr = (Field * len(fields))(*fields)
+    return _check("serbf_batch_init", _lib.serbf_batch_init(C.addressof(b_host), arr, len(fields), int(fwd_warps),
+                                                            _p(dev), dev.numel() * dev.element_size(),
+                                                            _stream(stream)))
+
+
+def serbf_batch_warps(b_host):
+    return _lib.serbf_batch_warps(C.addressof(b_host))
+
+
+def serbf_epoch_batched(b_host, stream=None):
+    return _check("serbf_epoch_batched", _lib.serbf_epoch_batched(C.addressof(b_host), _stream(stream)))
 
 
 STATE_BYTES = C.sizeof(State)

@@ -20,6 +20,7 @@
 //                   the last block appends the survivors in order.
 // The selection lists use the binning sort buffers (idle outside binning).
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 
@@ -35,6 +36,36 @@ constexpr int kLmThreads = 256;
 // sel_ctl slots
 enum { CTL_BIN = 0, CTL_K, CTL_SUPER, CTL_SLOT, CTL_HIST_DONE, CTL_GATHER_DONE, CTL_LM_DONE };
 
+struct AppendArgs {
+    const float *x, *y, *z, *E, *S;
+    double dbar_min, eps;
+    float *p, *am, *av;
+    int32_t *m_dev;
+    int cap;
+    serbf_state *st;
+    int32_t *status;
+    long long *needed;
+};
+
+// Everything the three launches of one addition read.
+struct AddArgs {
+    const float *E;
+    const uint8_t *mask;
+    int64_t n;
+    const double *stats;
+    double thresh, frac;
+    int force;
+    uint32_t *hist, *ctl;
+    int32_t *info;
+    uint32_t *hi, *lo, *hi2, *lo2;  // selection lists (binning sort buffers)
+    const uint32_t *cell_start;
+    serbf_grid g;
+    int sf, nsx, nsy;
+    float r2;
+    int reach;
+    AppendArgs ap;
+};
+
 __device__ __forceinline__ uint32_t cand_key(const float *E, const uint8_t *mask, int64_t i, double thresh) {
     const float a = fabsf(E[i]);
     return (mask[i] && (double)a > thresh) ? __float_as_uint(a) : 0u;
@@ -42,41 +73,43 @@ __device__ __forceinline__ uint32_t cand_key(const float *E, const uint8_t *mask
 
 // Last block of a grid to reach this point (after its own writes): true in
 // exactly one block.  No block waits for another.
-__device__ __forceinline__ bool last_block(uint32_t *counter, bool *s_flag) {
+__device__ __forceinline__ bool last_block(uint32_t *counter, bool *s_flag, int nbx) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        *s_flag = atomicAdd(counter, 1u) == gridDim.x - 1;
+        *s_flag = atomicAdd(counter, 1u) == (unsigned)nbx - 1;
     }
     __syncthreads();
     if (*s_flag) __threadfence();
     return *s_flag;
 }
 
-__global__ void __launch_bounds__(kHistThreads) k_add_hist(const float *E, const uint8_t *mask, int64_t n,
-                                                          const double *stats, const serbf_state *st,
-                                                          double thresh, double frac, int force, uint32_t *hist,
-                                                          uint32_t *ctl, int32_t *info) {
-    pdl_wait();
-    pdl_trigger();
+// Block bx of nbx.
+__device__ __forceinline__ void add_hist_body(const AddArgs &A, int bx, int nbx) {
+    const float *E = A.E;
+    const uint8_t *mask = A.mask;
+    const int64_t n = A.n;
+    const double thresh = A.thresh, frac = A.frac;
+    uint32_t *hist = A.hist, *ctl = A.ctl;
+    int32_t *info = A.info;
     __shared__ uint32_t sh[kSelBins];
     __shared__ uint32_t tmp[33];
     __shared__ bool s_last;
-    const bool go = force || st->do_add;
+    const bool go = A.force || A.ap.st->do_add;
     if (!go) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) info[0] = 0;
+        if (bx == 0 && threadIdx.x == 0) info[0] = 0;
         return;
     }
     for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) sh[d] = 0u;
     __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)nbx * blockDim.x) {
         const uint32_t key = cand_key(E, mask, i, thresh);
         if (key) atomicAdd(&sh[key >> 20], 1u);
     }
     __syncthreads();
     for (int d = threadIdx.x; d < kSelBins; d += blockDim.x)
         if (sh[d]) atomicAdd(&hist[d], sh[d]);
-    if (!last_block(&ctl[CTL_HIST_DONE], &s_last)) return;
+    if (!last_block(&ctl[CTL_HIST_DONE], &s_last, nbx)) return;
     // the last block: bin counts (cleared for the next call), their total C,
     // k and the bin B holding the k-th largest key
     for (int d = threadIdx.x; d < kSelBins; d += blockDim.x) {
@@ -94,7 +127,7 @@ __global__ void __launch_bounds__(kHistThreads) k_add_hist(const float *E, const
     const uint32_t above = block_exscan(own, tmp, &total);  // keys in larger bins than this thread's
     int64_t k = total;
     if (frac > 0.0) {
-        const double kk = ceil(frac * stats[SERBF_STAT_COUNT]);
+        const double kk = ceil(frac * A.stats[SERBF_STAT_COUNT]);
         if (kk < (double)k) k = (int64_t)kk;
     }
     if (k < 0) k = 0;
@@ -243,21 +276,22 @@ __device__ void sort_large(uint32_t *hi, uint32_t *lo, uint32_t *hi2, uint32_t *
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kGatherThreads) k_add_gather(const float *E, const uint8_t *mask, int64_t n,
-                                                              double thresh, uint32_t *ctl, int32_t *info,
-                                                              uint32_t *hi, uint32_t *lo, uint32_t *hi2,
-                                                              uint32_t *lo2) {
-    pdl_wait();
-    pdl_trigger();
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void add_gather_body(const AddArgs &A, int bx, int nbx, unsigned char *smem) {
+    const float *E = A.E;
+    const uint8_t *mask = A.mask;
+    const int64_t n = A.n;
+    const double thresh = A.thresh;
+    uint32_t *ctl = A.ctl;
+    int32_t *info = A.info;
+    uint32_t *hi = A.hi, *lo = A.lo, *hi2 = A.hi2, *lo2 = A.lo2;
     __shared__ bool s_last;
     if (!info[0]) return;
     const uint32_t B = ctl[CTL_BIN];
     const int lane = threadIdx.x & 31;
     if (B < (uint32_t)kSelBins) {
         // grid-stride in whole warps, so every lane of a warp takes part in the ballot
-        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+        const int64_t stride = (int64_t)nbx * blockDim.x;
+        for (int64_t i0 = bx * (int64_t)blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
             const int64_t i = i0 + lane;
             const uint32_t key = i < n ? cand_key(E, mask, i, thresh) : 0u;
             const bool take = key != 0u && (key >> 20) >= B;
@@ -274,7 +308,7 @@ __global__ void __launch_bounds__(kGatherThreads) k_add_gather(const float *E, c
             }
         }
     }
-    if (!last_block(&ctl[CTL_GATHER_DONE], &s_last)) return;
+    if (!last_block(&ctl[CTL_GATHER_DONE], &s_last, nbx)) return;
     const uint32_t s = __ldcg(&ctl[CTL_SLOT]), k = min(ctl[CTL_K], s);
     if (s <= (uint32_t)kBitonicMax)
         sort_small(hi, lo, s, reinterpret_cast<unsigned long long *>(smem));
@@ -309,8 +343,7 @@ __device__ __forceinline__ void localmax_one(const float *x, const float *y, con
                     bool v = false;
                     if (q < e && mask[q]) {
                         const float dx = __fsub_rn(x[q], xi), dy = __fsub_rn(y[q], yi), dz = __fsub_rn(z[q], zi);
-                        const float d2 =
-                            __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                        const float d2 = support_d2(dx, dy, dz);
                         v = d2 <= r2 && fabsf(E[q]) > ei;
                     }
                     bad = __any_sync(0xffffffffu, v);
@@ -318,17 +351,6 @@ __device__ __forceinline__ void localmax_one(const float *x, const float *y, con
             }
     if (lane == 0) keep[s] = !bad;
 }
-
-struct AppendArgs {
-    const float *x, *y, *z, *E, *S;
-    double dbar_min, eps;
-    float *p, *am, *av;
-    int32_t *m_dev;
-    int cap;
-    serbf_state *st;
-    int32_t *status;
-    long long *needed;
-};
 
 // Eq. 3-24 / 3-25: the kept points become kernels, appended in selection
 // order up to the capacity (a flag and the size needed otherwise); Adam
@@ -390,58 +412,160 @@ __device__ void append_kept(const AppendArgs &a, const uint32_t *sel_idx, const 
 // point within the radius has a larger |E| (distance in float, same operation
 // order as the support test, <= r2).  One block per SM, so a step without an
 // addition retires few blocks.  The last block appends the survivors.
-__global__ void __launch_bounds__(kLmThreads) k_add_localmax(const uint8_t *mask, const uint32_t *cell_start,
-                                                            serbf_grid g, int sf, int nsx, int nsy, float r2,
-                                                            int reach, const uint32_t *sel_idx, uint32_t *keep,
-                                                            int32_t *info, uint32_t *ctl, AppendArgs ap) {
+__device__ __forceinline__ void add_localmax_body(const AddArgs &A, int bx, int nbx) {
+    const AppendArgs &ap = A.ap;
+    const uint32_t *sel_idx = A.lo;  // the sorted selection's indices
+    uint32_t *keep = A.hi2;          // scratch once the selection is sorted
+    __shared__ bool s_last;
+    if (!A.info[0]) return;
+    const int lane = threadIdx.x & 31, nsel = A.info[1];
+    for (int s = (bx * blockDim.x + threadIdx.x) >> 5; s < nsel; s += (nbx * blockDim.x) >> 5)
+        localmax_one(ap.x, ap.y, ap.z, ap.E, A.mask, A.cell_start, A.g, A.sf, A.nsx, A.nsy, A.r2, A.reach, sel_idx,
+                     keep, s, lane);
+    if (!last_block(&A.ctl[CTL_LM_DONE], &s_last, nbx)) return;
+    append_kept(ap, sel_idx, keep, nsel, A.info);
+    if (threadIdx.x == 0) A.ctl[CTL_LM_DONE] = 0u;
+}
+
+__global__ void __launch_bounds__(kHistThreads) k_add_hist(AddArgs A) {
     pdl_wait();
     pdl_trigger();
-    __shared__ bool s_last;
-    if (!info[0]) return;
-    const int lane = threadIdx.x & 31, nsel = info[1];
-    for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nsel; s += (gridDim.x * blockDim.x) >> 5)
-        localmax_one(ap.x, ap.y, ap.z, ap.E, mask, cell_start, g, sf, nsx, nsy, r2, reach, sel_idx, keep, s, lane);
-    if (!last_block(&ctl[CTL_LM_DONE], &s_last)) return;
-    append_kept(ap, sel_idx, keep, nsel, info);
-    if (threadIdx.x == 0) ctl[CTL_LM_DONE] = 0u;
+    add_hist_body(A, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kGatherThreads) k_add_gather(AddArgs A) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smem[];
+    add_gather_body(A, blockIdx.x, gridDim.x, smem);
+}
+
+__global__ void __launch_bounds__(kLmThreads) k_add_localmax(AddArgs A) {
+    pdl_wait();
+    pdl_trigger();
+    add_localmax_body(A, blockIdx.x, gridDim.x);
+}
+
+// Batches of fields: field blockIdx.y.
+__global__ void __launch_bounds__(kHistThreads) k_add_hist_batch(const AddArgs *aa) {
+    pdl_wait();
+    pdl_trigger();
+    add_hist_body(aa[blockIdx.y], blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kGatherThreads) k_add_gather_batch(const AddArgs *aa) {
+    pdl_wait();
+    pdl_trigger();
+    extern __shared__ __align__(16) unsigned char smem[];
+    add_gather_body(aa[blockIdx.y], blockIdx.x, gridDim.x, smem);
+}
+
+__global__ void __launch_bounds__(kLmThreads) k_add_localmax_batch(const AddArgs *aa) {
+    pdl_wait();
+    pdl_trigger();
+    add_localmax_body(aa[blockIdx.y], blockIdx.x, gridDim.x);
+}
+
+int gather_smem() {
+    return (int)(sizeof(RadixSmem) > kBitonicMax * sizeof(unsigned long long) ? sizeof(RadixSmem)
+                                                                                : kBitonicMax * sizeof(unsigned long long));
+}
+
+// Dynamic shared memory of the gather kernels (once per process).
+int gather_attr() {
+    static bool done = false;
+    if (!done) {
+        if (cudaFuncSetAttribute(k_add_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, gather_smem()) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_add_gather_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, gather_smem()) !=
+                cudaSuccess)
+            return SERBF_ECUDA;
+        done = true;
+    }
+    return SERBF_OK;
+}
+
+bool make_add_args(const serbf_points *pts, const float *S_raw, const float *err, const uint8_t *mask,
+                   serbf_params *prm, float *adam_m, float *adam_v, serbf_state *st_dev, const double *stats,
+                   const serbf_config *cfg, int force, serbf_workspace *ws, AddArgs &A) {
+    if (!pts || !prm || !cfg || !ws || ws->magic != kMagic || !ws->binned) return false;
+    if (pts->n != ws->npoints || !prm->p || !prm->m || prm->cap < 1 || prm->cap > ws->sz.max_kernels) return false;
+    if (!st_dev || !stats || !adam_m || !adam_v) return false;
+    if (pts->n > 0 && (!S_raw || !err || !mask || !pts->x || !pts->y || !pts->z)) return false;
+    if (!(cfg->add_radius >= 0.0) || !(cfg->eps > 0.0)) return false;
+    A.E = err;
+    A.mask = mask;
+    A.n = pts->n;
+    A.stats = stats;
+    A.thresh = cfg->tau_m * 0.5;
+    A.frac = cfg->topk_frac;
+    A.force = force;
+    A.hist = ws->sel_hist;
+    A.ctl = ws->sel_ctl;
+    A.info = ws->add_info;
+    A.hi = ws->keys0;
+    A.lo = ws->vals0;
+    A.hi2 = ws->keys1;
+    A.lo2 = ws->vals1;
+    A.cell_start = ws->cell_start;
+    A.g = ws->grid;
+    A.sf = ws->sf;
+    A.nsx = ws->ns[0];
+    A.nsy = ws->ns[1];
+    A.r2 = (float)(cfg->add_radius * cfg->add_radius);
+    int reach = (int)ceil(cfg->add_radius / ws->grid.h) + 1;
+    if (reach > 1 << 20) reach = 1 << 20;
+    A.reach = reach;
+    A.ap = AppendArgs{pts->x, pts->y, pts->z, err, S_raw, cfg->dbar_min, cfg->eps, prm->p, adam_m, adam_v,
+                      prm->m, prm->cap, st_dev, ws->status, ws->needed};
+    return true;
 }
 
 }  // namespace
+
+namespace serbf {
+
+size_t add_args_size() { return sizeof(AddArgs); }
+
+// Host record of one field's addition for a batch (out: sizeof(AddArgs) bytes).
+int batch_add_args(const serbf_points *pts, const float *S_raw, const float *err, const uint8_t *mask,
+                   serbf_params *prm, float *adam_m, float *adam_v, serbf_state *st_dev, const double *stats,
+                   const serbf_config *cfg, serbf_workspace *ws, void *out) {
+    AddArgs A;
+    if (!make_add_args(pts, S_raw, err, mask, prm, adam_m, adam_v, st_dev, stats, cfg, 0, ws, A)) return SERBF_EINVAL;
+    memcpy(out, &A, sizeof(A));
+    return SERBF_OK;
+}
+
+// The batched addition: three launches, each a no-op for fields whose
+// addition is not due.
+int batch_add_launch(const void *args, int nfields, int sm_count, cudaStream_t s) {
+    if (gather_attr()) return SERBF_ECUDA;
+    const AddArgs *aa = static_cast<const AddArgs *>(args);
+    const unsigned nsm = (unsigned)(sm_count > 0 ? sm_count : 1);
+    launch_pdl(k_add_hist_batch, dim3(2 * nsm, (unsigned)nfields), dim3(kHistThreads), 0, s, aa);
+    launch_pdl(k_add_gather_batch, dim3(nsm, (unsigned)nfields), dim3(kGatherThreads), (size_t)gather_smem(), s, aa);
+    launch_pdl(k_add_localmax_batch, dim3(nsm, (unsigned)nfields), dim3(kLmThreads), 0, s, aa);
+    SERBF_CHECK_LAUNCH();
+    return SERBF_OK;
+}
+
+}  // namespace serbf
 
 extern "C" int serbf_add_kernels(const serbf_points *pts, const float *S_raw, const float *err, const uint8_t *mask,
                                  serbf_params *prm, float *adam_m, float *adam_v, serbf_state *st_dev,
                                  const double *stats, const serbf_config *cfg, int force, serbf_workspace *ws,
                                  void *stream) {
     SERBF_TRACE();
-    if (!pts || !prm || !cfg || !ws || ws->magic != kMagic || !ws->binned) return SERBF_EINVAL;
-    if (pts->n != ws->npoints || !prm->p || !prm->m || prm->cap < 1 || prm->cap > ws->sz.max_kernels)
+    AddArgs A;
+    if (!make_add_args(pts, S_raw, err, mask, prm, adam_m, adam_v, st_dev, stats, cfg, force, ws, A))
         return SERBF_EINVAL;
-    if (!st_dev || !stats || !adam_m || !adam_v) return SERBF_EINVAL;
-    if (pts->n > 0 && (!S_raw || !err || !mask || !pts->x || !pts->y || !pts->z)) return SERBF_EINVAL;
-    if (!(cfg->add_radius >= 0.0) || !(cfg->eps > 0.0)) return SERBF_EINVAL;
+    if (gather_attr()) return SERBF_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    static bool attr = false;
-    const int smem = (int)(sizeof(RadixSmem) > kBitonicMax * sizeof(unsigned long long)
-                               ? sizeof(RadixSmem)
-                               : kBitonicMax * sizeof(unsigned long long));
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_add_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-            return SERBF_ECUDA;
-        attr = true;
-    }
     const unsigned nsm = (unsigned)(ws->sm_count > 0 ? ws->sm_count : 1);
-    const double thresh = cfg->tau_m * 0.5;
-    launch_pdl(k_add_hist, dim3(2 * nsm), dim3(kHistThreads), 0, s, err, mask, pts->n, stats, st_dev, thresh,
-               cfg->topk_frac, force, ws->sel_hist, ws->sel_ctl, ws->add_info);
-    launch_pdl(k_add_gather, dim3(nsm), dim3(kGatherThreads), (size_t)smem, s, err, mask, pts->n, thresh, ws->sel_ctl,
-               ws->add_info, ws->keys0, ws->vals0, ws->keys1, ws->vals1);
-    const float r2 = (float)(cfg->add_radius * cfg->add_radius);
-    int reach = (int)ceil(cfg->add_radius / ws->grid.h) + 1;
-    if (reach > 1 << 20) reach = 1 << 20;
-    AppendArgs ap{pts->x, pts->y, pts->z, err, S_raw, cfg->dbar_min, cfg->eps, prm->p, adam_m, adam_v,
-                  prm->m, prm->cap, st_dev, ws->status, ws->needed};
-    launch_pdl(k_add_localmax, dim3(nsm), dim3(kLmThreads), 0, s, mask, ws->cell_start, ws->grid, ws->sf, ws->ns[0],
-               ws->ns[1], r2, reach, ws->vals0, ws->keys1, ws->add_info, ws->sel_ctl, ap);
+    launch_pdl(k_add_hist, dim3(2 * nsm), dim3(kHistThreads), 0, s, A);
+    launch_pdl(k_add_gather, dim3(nsm), dim3(kGatherThreads), (size_t)gather_smem(), s, A);
+    launch_pdl(k_add_localmax, dim3(nsm), dim3(kLmThreads), 0, s, A);
     SERBF_CHECK_LAUNCH();
     return SERBF_OK;
 }

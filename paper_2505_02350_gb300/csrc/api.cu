@@ -96,6 +96,7 @@ void carve(Carver &c, serbf_workspace *w, const serbf_ws_sizes *s) {
     w->counters = c.take<uint32_t>(16);
     w->dtmp = c.take<double>(16);
     w->cell_max = c.take<uint32_t>(4);
+    w->field_box = c.take<float4>(2);
 }
 
 __global__ void k_exscan_u32(uint32_t *a, int64_t n) {
@@ -219,7 +220,7 @@ int launch_exscan_i64(int64_t *a, int64_t n, cudaStream_t s) {
 
 extern "C" {
 
-const char *serbf_version(void) { return "serbf 0.2.0 (sm_103a)"; }
+const char *serbf_version(void) { return "serbf 0.3.0 (sm_103a)"; }
 
 const char *serbf_status_string(int code) {
     switch (code) {

@@ -185,6 +185,37 @@ __global__ void k_tile_boxes(const uint32_t *tile_super, const uint32_t *tile_st
     }
 }
 
+// One block: the union of the super-cell boxes (the box of every binned point).
+__global__ void k_field_box(const float4 *slo, const float4 *shi, int nsuper, float4 *box) {
+    __shared__ float red[6][32];
+    float v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int s = threadIdx.x; s < nsuper; s += blockDim.x) {
+        const float4 a = slo[s], b = shi[s];
+        v[0] = fminf(v[0], a.x);
+        v[1] = fminf(v[1], a.y);
+        v[2] = fminf(v[2], a.z);
+        v[3] = fmaxf(v[3], b.x);
+        v[4] = fmaxf(v[4], b.y);
+        v[5] = fmaxf(v[5], b.z);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const float w = __shfl_xor_sync(0xffffffffu, v[k], o);
+            v[k] = k < 3 ? fminf(v[k], w) : fmaxf(v[k], w);
+        }
+        if (lane == 0) red[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            for (int k = 0; k < 6; ++k) v[k] = k < 3 ? fminf(v[k], red[k][w]) : fmaxf(v[k], red[k][w]);
+        box[0] = make_float4(v[0], v[1], v[2], 0.f);
+        box[1] = make_float4(v[3], v[4], v[5], 0.f);
+    }
+}
+
 // One warp per super cell: union of its tile boxes (empty: +inf / -inf).
 __global__ void k_super_boxes(const uint32_t *stile0, int nsuper, const float4 *tlo, const float4 *thi, float4 *slo,
                               float4 *shi) {
@@ -320,6 +351,7 @@ extern "C" int serbf_bin_points(const float *x, const float *y, const float *z, 
                                                                         cps, nt, xb, yb, zb, ws->tile_lo, ws->tile_hi);
     k_super_boxes<<<(unsigned)((nsuper * 32 + 255) / 256), 256, 0, s>>>(ws->super_tile0, (int)nsuper, ws->tile_lo,
                                                                         ws->tile_hi, ws->sup_lo, ws->sup_hi);
+    k_field_box<<<1, 256, 0, s>>>(ws->sup_lo, ws->sup_hi, (int)nsuper, ws->field_box);
     SERBF_CHECK_LAUNCH();
     ws->binned = 1;
     return SERBF_OK;

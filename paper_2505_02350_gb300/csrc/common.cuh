@@ -132,6 +132,7 @@ struct serbf_workspace {
     uint32_t *counters;           // [8] last-block counters
     double *dtmp;                 // [16]
     uint32_t *cell_max;           // [4]: [0] most points in one binning cell, [1] fixed-point range bound (float bits)
+    float4 *field_box;            // [2]: lower and upper corner of all binned points
 };
 
 #define SERBF_CHECK_LAUNCH()                                   \
@@ -175,23 +176,32 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-// Eq. 3-15-1 membership, float, fixed operation order, never contracted.
+// Squared distance of the support test (Eq. 3-15-1) in its canonical float
+// form: dx = fl(px - cx) and likewise for y, z, then
+// d2 = fma(dz, dz, fma(dy, dy, fl(dx * dx))), each fma rounded once.  Every
+// implementation (the scalar and packed kernels, the oracle) spells out the
+// same three operations, so no compiler contraction can change the value.
+__device__ __forceinline__ float support_d2(float dx, float dy, float dz) {
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+// Eq. 3-15-1 membership, float, fixed operation order.
 __device__ __forceinline__ bool in_support(float px, float py, float pz, float cx, float cy, float cz,
                                            float r2) {
-    float dx = __fsub_rn(px, cx), dy = __fsub_rn(py, cy), dz = __fsub_rn(pz, cz);
-    float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    return d2 < r2;
+    const float dx = __fsub_rn(px, cx), dy = __fsub_rn(py, cy), dz = __fsub_rn(pz, cz);
+    return support_d2(dx, dy, dz) < r2;
 }
 
 // Squared distance from c to a box, rounded so that it never exceeds the
-// float squared distance of any point inside the box (every step is a
-// monotone rounding of a smaller exact value), hence box_d2 < r2 is a superset
-// of the membership test for points in the box.
+// support_d2 of any point inside the box (every step is a monotone rounding
+// of a smaller exact value, and fma with non-negative terms is monotone in
+// each argument), hence box_d2 < r2 is a superset of the membership test for
+// points in the box.
 __device__ __forceinline__ float box_d2(float cx, float cy, float cz, float4 lo, float4 hi) {
     float ax = cx < lo.x ? __fsub_rn(lo.x, cx) : (cx > hi.x ? __fsub_rn(cx, hi.x) : 0.f);
     float ay = cy < lo.y ? __fsub_rn(lo.y, cy) : (cy > hi.y ? __fsub_rn(cy, hi.y) : 0.f);
     float az = cz < lo.z ? __fsub_rn(lo.z, cz) : (cz > hi.z ? __fsub_rn(cz, hi.z) : 0.f);
-    return __fadd_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)), __fmul_rn(az, az));
+    return support_d2(ax, ay, az);
 }
 
 __device__ __forceinline__ float support_r2(float d1, float d2, float d3, float nle) {
@@ -308,7 +318,7 @@ template <bool KAHAN>
 __device__ __forceinline__ void accumulate(const float4 &pt, const float4 &k0, const float4 &k1, const float4 &k2,
                                            const float4 &k3, float (&acc)[10], float (&cmp)[10], uint32_t &pairs) {
     const float dx = __fsub_rn(pt.x, k0.x), dy = __fsub_rn(pt.y, k0.y), dz = __fsub_rn(pt.z, k0.z);
-    const bool in = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)) < k0.w;
+    const bool in = support_d2(dx, dy, dz) < k0.w;
     const float u1 = fmaf(k1.z, dz, fmaf(k1.y, dy, k1.x * dx));
     const float u2 = fmaf(k2.z, dz, fmaf(k2.y, dy, k2.x * dx));
     const float u3 = fmaf(k3.z, dz, fmaf(k3.y, dy, k3.x * dx));

@@ -17,6 +17,7 @@
 // by the previous launch) to keep the tail short; the warps of a block split
 // an item's candidate list and combine their sums in a fixed order.
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 
@@ -118,19 +119,19 @@ __device__ __forceinline__ void stage_empty(float *ring, int slot) {
 }
 
 // Squared distance from c to the farthest corner of a box, rounded so that
-// it is never below the float squared distance of any point inside the box:
+// it is never below the support_d2 of any point inside the box:
 // box_far_d2 < r2 means every point of the box is in the support.
 __device__ __forceinline__ float box_far_d2(float cx, float cy, float cz, float4 lo, float4 hi) {
     const float ax = fmaxf(__fsub_rn(cx, lo.x), __fsub_rn(hi.x, cx));
     const float ay = fmaxf(__fsub_rn(cy, lo.y), __fsub_rn(hi.y, cy));
     const float az = fmaxf(__fsub_rn(cz, lo.z), __fsub_rn(hi.z, cz));
-    return __fadd_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)), __fmul_rn(az, az));
+    return support_d2(ax, ay, az);
 }
 
 // npairs staged kernel pairs from pair index pb against the lane's two
 // points.  PARTIAL: the support only partly covers the item box, so each
-// pair takes the exact Eq. 3-15-1 predicate (same float operations as the
-// scalar test: fl(fl(fl(dx^2) + fl(dy^2)) + fl(dz^2)) < r2).
+// pair takes the exact Eq. 3-15-1 predicate (the operations of support_d2,
+// packed: fma(dz, dz, fma(dy, dy, fl(dx dx))) < r2).
 template <bool PARTIAL, int UNROLL>
 __device__ __forceinline__ void eval_pairs(const float *ring, int pb, int npairs, const f2 (&P)[2][3], f2 (&acc)[2],
                                            uint32_t (&n)[2]) {
@@ -150,7 +151,7 @@ __device__ __forceinline__ void eval_pairs(const float *ring, int pb, int npairs
             f2_unpack(qv, q0, q1);
             float e0 = ex2_approx(-q0), e1 = ex2_approx(-q1);
             if (PARTIAL) {
-                const f2 d2 = f2_add(f2_add(f2_mul(dx, dx), f2_mul(dy, dy)), zz);
+                const f2 d2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
                 float d0, d1, r0, r1;
                 f2_unpack(d2, d0, d1);
                 f2_unpack(F1.y, r0, r1);
@@ -474,7 +475,7 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
 #pragma unroll 1
     for (int seg = 0; seg < 2; ++seg) {
         const int base = seg ? kTile : 0, cntp = act ? ((seg ? nc1 : nc0) + 1) >> 1 : 0;
-#pragma unroll 2
+#pragma unroll 4
         for (int pp = sub; pp < cntp; pp += L) {
             const int i = base + 2 * pp;
             const f2 px = *reinterpret_cast<const f2 *>(&nz.x[i]), py = *reinterpret_cast<const f2 *>(&nz.y[i]);
@@ -489,8 +490,8 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
             f2_unpack(qv, q0, q1);
             f2_unpack(pe, pe0, pe1);
             float e0 = ex2_approx(-q0), e1 = ex2_approx(-q1);
-            // Eq. 3-15-1, same float operations as the scalar test
-            const f2 d2 = f2_add(f2_add(f2_mul(dx, dx), f2_mul(dy, dy)), zz);
+            // Eq. 3-15-1, the operations of support_d2, packed
+            const f2 d2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
             float d0, d1;
             f2_unpack(d2, d0, d1);
             const bool i0 = d0 < k0.w, i1 = d1 < k0.w;
@@ -692,20 +693,58 @@ __device__ __forceinline__ void sched_finish(const FwdArgs &a) {
     *a.exit_count = 0u;
 }
 
+// A batch of fields advanced by one launch: the fields' arguments in device
+// memory and their work items concatenated in field order (item_off: prefix
+// sums of the item counts).  Blocks claim from one counter over all items.
+struct FwdBatch {
+    const FwdArgs *args;
+    const uint32_t *item_off;  // nfields + 1
+    int nfields;
+    uint32_t *next, *exit;     // claim and exit counters (zero between launches)
+};
+constexpr int kMaxBatchFields = 1024;
+
+// Item k of the batch: its field (binary search of the offsets in shared
+// memory) and record; w = 0 when none is left.
+__device__ __forceinline__ uint4 resolve_batch(const FwdBatch &b, const uint32_t *off, uint32_t k, uint32_t &field) {
+    field = 0;
+    if (k >= off[b.nfields]) return make_uint4(0u, 0u, 0u, 0u);
+    int lo = 0, hi = b.nfields - 1;  // largest f with off[f] <= k
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= k) lo = mid; else hi = mid - 1;
+    }
+    field = (uint32_t)lo;
+    return b.args[lo].order_rec[k - off[lo]];
+}
+
+// Last block out of a batch launch: every field's mean cost, and the batch
+// counters reset.
+__device__ __forceinline__ void sched_finish_batch(const FwdBatch &b) {
+    __threadfence();
+    if (atomicAdd(b.exit, 1u) != gridDim.x - 1) return;
+    __threadfence();
+    for (int f = 0; f < b.nfields; ++f) {
+        const FwdArgs &a = b.args[f];
+        const unsigned long long tot = __ldcg(a.sched_total);
+        const unsigned long long mean = a.nitems > 0 ? tot / (unsigned long long)a.nitems : 0ull;
+        a.sched[0] = (uint32_t)min(mean, 0xffffffffull);
+        *a.sched_total = 0ull;
+    }
+    *b.next = 0u;
+    *b.exit = 0u;
+}
+
 // Persistent blocks take work items, heaviest first, from a global counter.
 // The G warps of a block share an item (its candidate list split by 32-entry
 // chunks); their partial sums are combined in warp order, so Psi does not
 // depend on timing.  G = 1 when there are enough items to balance the warps,
-// 2 or 4 for small problems.  Resident warps per SM (the register budget):
-// 16 for the fused variants with 1 or 4 warps per item and 20 with 2, 24 for
-// eight warps and for the forward alone (20 with one warp); more resident
-// warps measured slower on every workload.
+// 2 or 4 for small problems.
 // ADJ: 0 forward only, 1 with the fused adjoint, 2 with the fused adjoint
 // and compensated (Kahan) per-item moment sums.
-template <int G, int ADJ>
-__global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 16) : (G == 1 ? 20 : 24))) / G) k_forward(FwdArgs a) {
-    pdl_wait();
-    pdl_trigger();
+// BATCH: the items of a batch of fields (b); otherwise of one field (a1).
+template <int G, int ADJ, bool BATCH>
+__device__ __forceinline__ void forward_loop(const FwdArgs &a1, const FwdBatch &b) {
     // two rings per warp (kernels partly / fully covering the item box); a
     // ring holds 64 staged kernels (32 pairs), consumed 32 at a time from
     // slot 0 or 32
@@ -722,17 +761,46 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
     __shared__ float4 s_box[2][2];
     __shared__ uint32_t adjq[ADJ ? G : 1][ADJ ? kQueue : 1];
     __shared__ uint32_t touch[ADJ ? G : 1][ADJ ? kTouch : 1];
+    // batch: the arguments of the current item's field, the item offsets
+    __shared__ __align__(16) FwdArgs s_args[BATCH ? 1 : 1];
+    __shared__ uint32_t s_off[BATCH ? kMaxBatchFields + 1 : 1];
+    __shared__ uint32_t s_field;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t mean = a.sched[0];
-    if (threadIdx.x == 0) s_rec = resolve(a, atomicAdd(a.item_next, 1u));
+    if (BATCH) {
+        for (int f = threadIdx.x; f <= b.nfields; f += blockDim.x) s_off[f] = b.item_off[f];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (BATCH) {
+            uint32_t f;
+            s_rec = resolve_batch(b, s_off, atomicAdd(b.next, 1u), f);
+            s_field = f;
+        } else {
+            s_rec = resolve(a1, atomicAdd(a1.item_next, 1u));
+        }
+    }
     __syncthreads();
     uint4 rec = s_rec;  // the item's record; no points (w = 0) when done
+    uint32_t field = BATCH ? s_field : 0u, loaded = ~0u;
+    uint32_t mean = BATCH ? 0u : a1.sched[0];
+    const FwdArgs &a = BATCH ? s_args[0] : a1;
     while (rec.w != 0u) {
+        if (BATCH && field != loaded) {
+            // the block's threads copy the field's arguments (block-uniform
+            // branch: every thread holds the same record and field)
+            if (G == 1) __syncwarp(); else __syncthreads();
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(b.args + field);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(s_args);
+            for (int k = threadIdx.x; k < (int)(sizeof(FwdArgs) / 4); k += blockDim.x) dst[k] = src[k];
+            if (G == 1) __syncwarp(); else __syncthreads();
+            loaded = field;
+            mean = a.sched[0];
+        }
         const ItemInfo it = item_info(rec, lane);
         // the next claim is made now, its record is fetched after the sums
         // and used at the end, so neither round trip is on the item's path
-        uint32_t knext = 0;
-        if (threadIdx.x == 0) knext = atomicAdd(a.item_next, 1u);
+        uint32_t knext = 0, fnext = 0;
+        if (threadIdx.x == 0) knext = atomicAdd(BATCH ? b.next : a.item_next, 1u);
         f2 acc[2];
         uint32_t n[2], cost;
         int ntouch = 0;
@@ -740,7 +808,7 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
         forward_share<G, ADJ>(a, it, warp, ringP[warp], ringF[warp], lane, acc, n, cost, touch[ADJ ? warp : 0],
                               ntouch, tv);
         uint4 rn = make_uint4(0u, 0u, 0u, 0u);
-        if (threadIdx.x == 0) rn = resolve(a, knext);
+        if (threadIdx.x == 0) rn = BATCH ? resolve_batch(b, s_off, knext, fnext) : resolve(a, knext);
         if (G == 1) {
             // one warp: finish both tiles directly
             float l0, h0, l1, h1;
@@ -772,6 +840,7 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
             rec.y = __shfl_sync(0xffffffffu, rn.y, 0);
             rec.z = __shfl_sync(0xffffffffu, rn.z, 0);
             rec.w = __shfl_sync(0xffffffffu, rn.w, 0);
+            if (BATCH) field = __shfl_sync(0xffffffffu, fnext, 0);
             continue;
         }
         {
@@ -819,6 +888,7 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
                     note_cost(a, mean, rec, c);
                 }
                 s_rec = rn;
+                if (BATCH) s_field = fnext;
             }
         }
         if (ADJ) {
@@ -842,10 +912,37 @@ __global__ void __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 2 ? 20 : 1
         }
         __syncthreads();
         rec = s_rec;
+        if (BATCH) field = s_field;
     }
     // the last block out prepares the next launch: every block has made its
     // last claim and recorded its costs before it counts itself out
-    if (threadIdx.x == 0) sched_finish(a);
+    if (threadIdx.x == 0) {
+        if (BATCH)
+            sched_finish_batch(b);
+        else
+            sched_finish(a1);
+    }
+}
+
+// Resident warps per SM (the register budget): 20 for the fused variants
+// with 1 or 2 warps per item and 16 with 4, 24 for eight warps and for the
+// forward alone (20 with one warp); measured on the 128^3 and 256^3 fields,
+// other bounds were slower.
+#define SERBF_FWD_BOUNDS(G, ADJ) __launch_bounds__(G * 32, (G == 8 ? 24 : (ADJ ? (G == 4 ? 16 : 20) : (G == 1 ? 20 : 24))) / G)
+
+template <int G, int ADJ>
+__global__ void SERBF_FWD_BOUNDS(G, ADJ) k_forward(FwdArgs a) {
+    pdl_wait();
+    pdl_trigger();
+    forward_loop<G, ADJ, false>(a, FwdBatch{});
+}
+
+// One launch over the work items of every field of a batch.
+template <int G, int ADJ>
+__global__ void SERBF_FWD_BOUNDS(G, ADJ) k_forward_batch(FwdBatch b) {
+    pdl_wait();
+    pdl_trigger();
+    forward_loop<G, ADJ, true>(FwdArgs{}, b);
 }
 
 template <int G, int ADJ>
@@ -901,26 +998,31 @@ struct FinishArgs {
     const float4 *kbwd;      // (c, r2) of each kernel
     float cell_h;            // binning cell edge
     uint32_t *cell_max;      // [0] most points in one cell, [1] running range bound (float bits)
+    const float4 *field_box; // box of all binned points
+    float npoints;
     int32_t *status;
 };
 
-// Upper bound of |moment| / max|E| for kernel j: a pair has phi <= 1 and
-// |u_k| <= |v - c| < r, so every moment of the kernel is at most
-// (points within r of c) * max|E| * max(1, r^2); the points within r are at
-// most (cells a ball of radius r can touch) * (most points in one cell).
-__device__ __forceinline__ float moment_bound(float r2, float h, uint32_t cell_max) {
-    const float nc = ceilf(2.f * sqrtf(r2) / h) + 2.f;
-    return fmaxf(1.f, r2) * nc * nc * nc * (float)cell_max;
+// Upper bound of |moment| / max|E| for kernel j (centre c, support radius
+// r): a pair has phi <= 1 and every component of v - c is at most the
+// distance from c to the farthest corner of the points' box, and below r,
+// so every moment of the kernel is at most (points within r of c) * max|E| *
+// max(1, min(r^2, far^2)); the points within r are at most the points of
+// the field and at most (cells a ball of radius r can touch) * (most points
+// in one cell).
+__device__ __forceinline__ float moment_bound(float4 k0, float h, uint32_t cell_max, const float4 *box, float npts) {
+    const float nc = ceilf(2.f * sqrtf(k0.w) / h) + 2.f;
+    const float far2 = box_far_d2(k0.x, k0.y, k0.z, box[0], box[1]);
+    return fmaxf(1.f, fminf(k0.w, far2)) * fminf(npts, nc * nc * nc * (float)cell_max);
 }
 
+// Block bx of nbx.
 template <bool ADJ>
-__global__ void __launch_bounds__(kFinishThreads) k_fwd_finish(FinishArgs f) {
-    pdl_wait();
-    pdl_trigger();
+__device__ __forceinline__ void fwd_finish_body(const FinishArgs &f, int bx, int nbx) {
     __shared__ bool s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t ngroups = (f.ntiles + kFwdGroup - 1) / kFwdGroup;
-    const int64_t g = (int64_t)blockIdx.x * (kFinishThreads / 32) + warp;
+    const int64_t g = (int64_t)bx * (kFinishThreads / 32) + warp;
     if (g < ngroups) {
         const uint32_t gb = (uint32_t)(g * kFwdGroup);
         const uint32_t ge = (uint32_t)min((int64_t)gb + kFwdGroup, f.ntiles);
@@ -929,7 +1031,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_fwd_finish(FinishArgs f) {
     }
     if (ADJ) {
         const int m = *f.m_dev;
-        const int j = blockIdx.x * blockDim.x + threadIdx.x;
+        const int j = bx * blockDim.x + threadIdx.x;
         if (j < m) {
             unsigned long long *o = f.fix + 10 * (size_t)j;
             float M[10];
@@ -944,13 +1046,14 @@ __global__ void __launch_bounds__(kFinishThreads) k_fwd_finish(FinishArgs f) {
             }
             grad_from_moments<true>(f.p, f.cap, j, M, f.grad);
             // positive floats order like their bits (NaN orders above +inf)
-            atomicMax(&f.cell_max[1], __float_as_uint(moment_bound(f.kbwd[4 * j].w, f.cell_h, f.cell_max[0])));
+            atomicMax(&f.cell_max[1], __float_as_uint(moment_bound(f.kbwd[4 * j], f.cell_h, f.cell_max[0],
+                                                                   f.field_box, f.npoints)));
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        s_last = atomicAdd(f.counter, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(f.counter, 1u) == (unsigned)nbx - 1;
     }
     __syncthreads();
     if (!s_last || warp != 0) return;
@@ -974,18 +1077,34 @@ __global__ void __launch_bounds__(kFinishThreads) k_fwd_finish(FinishArgs f) {
     }
 }
 
-int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi, float *err,
-                 uint8_t *mask, float *grad, double *stats, serbf_workspace *ws, void *stream) {
-    if (!pts || !prm || !cfg || !ws || ws->magic != kMagic || !ws->binned) return SERBF_EINVAL;
-    if (pts->n != ws->npoints || !prm->m || !prm->p) return SERBF_EINVAL;
-    if (pts->n > 0 && (!pts->x || !pts->y || !pts->z || !pts->t || !psi || !err || !mask)) return SERBF_EINVAL;
-    if (!stats) return SERBF_EINVAL;
+template <bool ADJ>
+__global__ void __launch_bounds__(kFinishThreads) k_fwd_finish(FinishArgs f) {
+    pdl_wait();
+    pdl_trigger();
+    fwd_finish_body<ADJ>(f, blockIdx.x, gridDim.x);
+}
+
+// Batch: field blockIdx.y.
+template <bool ADJ>
+__global__ void __launch_bounds__(kFinishThreads) k_fwd_finish_batch(const FinishArgs *fa) {
+    pdl_wait();
+    pdl_trigger();
+    const FinishArgs f = fa[blockIdx.y];
+    fwd_finish_body<ADJ>(f, blockIdx.x, gridDim.x);
+}
+
+// The arguments of one forward (+ adjoint) call; false on bad arguments.
+bool make_args(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi, float *err,
+               uint8_t *mask, float *grad, double *stats, serbf_workspace *ws, FwdArgs &a, FinishArgs &f,
+               int64_t &finish_blocks) {
+    if (!pts || !prm || !cfg || !ws || ws->magic != kMagic || !ws->binned) return false;
+    if (pts->n != ws->npoints || !prm->m || !prm->p) return false;
+    if (pts->n > 0 && (!pts->x || !pts->y || !pts->z || !pts->t || !psi || !err || !mask)) return false;
+    if (!stats) return false;
     const bool adj = grad != nullptr;
     if (cfg->fwd_warps != 0 && cfg->fwd_warps != 1 && cfg->fwd_warps != 2 && cfg->fwd_warps != 4 && cfg->fwd_warps != 8)
-        return SERBF_EINVAL;
-    if (adj && (prm->cap < 1 || prm->cap > ws->sz.max_kernels)) return SERBF_EINVAL;
-    cudaStream_t s = (cudaStream_t)stream;
-    FwdArgs a;
+        return false;
+    if (adj && (prm->cap < 1 || prm->cap > ws->sz.max_kernels)) return false;
     a.x = pts->x;
     a.y = pts->y;
     a.z = pts->z;
@@ -1025,14 +1144,49 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
     a.item_next = ws->counters + 4;
     a.exit_count = ws->counters + 6;
     a.status = ws->status;
+    f.part = ws->fwd_part;
+    f.gpart = reinterpret_cast<FwdGPart *>(ws->fwd_gpart);
+    f.ntiles = ws->ntiles;
+    f.p = prm->p;
+    f.m_dev = prm->m;
+    f.cap = prm->cap;
+    f.fix = ws->adj_fix;
+    f.pairs = ws->adj_pairs;
+    f.grad = grad;
+    f.counter = ws->counters + 5;
+    f.stats = stats;
+    f.kbwd = ws->kbwd;
+    f.cell_h = ws->grid.h;
+    f.cell_max = ws->cell_max;
+    f.field_box = ws->field_box;
+    f.npoints = (float)ws->npoints;
+    f.status = ws->status;
+    const int64_t ngroups = (ws->ntiles + kFwdGroup - 1) / kFwdGroup;
+    int64_t nb = (ngroups + kFinishThreads / 32 - 1) / (kFinishThreads / 32);
+    if (adj) nb = max(nb, (int64_t)((prm->cap + kFinishThreads - 1) / kFinishThreads));
+    finish_blocks = nb < 1 ? 1 : nb;
+    return true;
+}
+
+// Warps per item: the fewest that still leave about four items per group of
+// warps for the heavy-first balancing, unless the configuration fixes it.
+int pick_warps(int64_t nitems, int sm_count, int fixed) {
+    if (fixed == 1 || fixed == 2 || fixed == 4 || fixed == 8) return fixed;
+    return nitems >= 4 * forward_groups<1>(sm_count) ? 1 : (nitems >= 4 * forward_groups<2>(sm_count) ? 2 : 4);
+}
+
+int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi, float *err,
+                 uint8_t *mask, float *grad, double *stats, serbf_workspace *ws, void *stream) {
+    FwdArgs a;
+    FinishArgs f;
+    int64_t nb = 1;
+    if (!make_args(pts, prm, cfg, psi, err, mask, grad, stats, ws, a, f, nb)) return SERBF_EINVAL;
+    const bool adj = grad != nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
     int rc = SERBF_OK;
     if (ws->ntiles > 0) {
-        // warps per item: the fewest that still leave about four items per
-        // group of warps for the heavy-first balancing
         const int64_t ni = ws->nitems;
-        int G = ni >= 4 * forward_groups<1>(ws->sm_count) ? 1 : (ni >= 4 * forward_groups<2>(ws->sm_count) ? 2 : 4);
-        if (cfg->fwd_warps == 1 || cfg->fwd_warps == 2 || cfg->fwd_warps == 4 || cfg->fwd_warps == 8)
-            G = cfg->fwd_warps;
+        const int G = pick_warps(ni, ws->sm_count, cfg->fwd_warps);
         const int mode = adj ? (cfg->kahan ? 2 : 1) : 0;
         switch (G * 4 + mode) {
             case 4: rc = launch_forward<1, 0>(a, ni, ws->sm_count, s); break;
@@ -1050,26 +1204,6 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
         }
     }
     if (rc) return rc;
-    FinishArgs f;
-    f.part = ws->fwd_part;
-    f.gpart = reinterpret_cast<FwdGPart *>(ws->fwd_gpart);
-    f.ntiles = ws->ntiles;
-    f.p = prm->p;
-    f.m_dev = prm->m;
-    f.cap = prm->cap;
-    f.fix = ws->adj_fix;
-    f.pairs = ws->adj_pairs;
-    f.grad = grad;
-    f.counter = ws->counters + 5;
-    f.stats = stats;
-    f.kbwd = ws->kbwd;
-    f.cell_h = ws->grid.h;
-    f.cell_max = ws->cell_max;
-    f.status = ws->status;
-    const int64_t ngroups = (ws->ntiles + kFwdGroup - 1) / kFwdGroup;
-    int64_t nb = (ngroups + kFinishThreads / 32 - 1) / (kFinishThreads / 32);
-    if (adj) nb = max(nb, (int64_t)((prm->cap + kFinishThreads - 1) / kFinishThreads));
-    if (nb < 1) nb = 1;
     if (adj)
         launch_pdl(k_fwd_finish<true>, dim3((unsigned)nb), dim3(kFinishThreads), 0, s, f);
     else
@@ -1078,7 +1212,76 @@ int forward_impl(const serbf_points *pts, const serbf_params *prm, const serbf_c
     return SERBF_OK;
 }
 
+template <int G, int ADJ>
+int launch_forward_batch(const FwdBatch &b, int64_t nitems, int sm_count, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_forward_batch<G, ADJ>, G * 32, 0) != cudaSuccess ||
+            nb < 1)
+            return SERBF_ECUDA;
+        per_sm = nb;
+    }
+    int64_t blocks = nitems;
+    const int64_t resident = (int64_t)sm_count * per_sm;
+    if (blocks > resident) blocks = resident;
+    if (blocks < 1) blocks = 1;
+    launch_pdl(k_forward_batch<G, ADJ>, dim3((unsigned)blocks), dim3(G * 32), 0, s, b);
+    SERBF_CHECK_LAUNCH();
+    return SERBF_OK;
+}
+
 }  // namespace
+
+namespace serbf {
+
+size_t fwd_args_size() { return sizeof(FwdArgs); }
+size_t finish_args_size() { return sizeof(FinishArgs); }
+
+// Host records of one field's fused forward + adjoint (out: sizeof(FwdArgs)
+// and sizeof(FinishArgs) bytes) and the finishing kernel's block count.
+int batch_forward_args(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi,
+                       float *err, uint8_t *mask, float *grad, double *stats, serbf_workspace *ws, void *fwd_out,
+                       void *fin_out, int64_t *finish_blocks) {
+    FwdArgs a;
+    FinishArgs f;
+    if (!make_args(pts, prm, cfg, psi, err, mask, grad, stats, ws, a, f, *finish_blocks)) return SERBF_EINVAL;
+    memcpy(fwd_out, &a, sizeof(a));
+    memcpy(fin_out, &f, sizeof(f));
+    return SERBF_OK;
+}
+
+int batch_pick_warps(int64_t nitems, int sm_count, int fixed) { return pick_warps(nitems, sm_count, fixed); }
+
+// One persistent launch over the items of every field, then the finishing
+// kernel of every field (grid.y = field).  args / fin / item_off / counters
+// are device arrays written by the batch set-up.
+int batch_forward_launch(const void *args, const void *fin, const uint32_t *item_off, int nfields, uint32_t *counters,
+                         int64_t total_items, int64_t finish_blocks, int G, int kahan, int sm_count, cudaStream_t s) {
+    if (nfields < 1 || nfields > kMaxBatchFields) return SERBF_EINVAL;
+    FwdBatch b{static_cast<const FwdArgs *>(args), item_off, nfields, counters, counters + 1};
+    int rc = SERBF_OK;
+    if (total_items > 0) {
+        switch (G * 2 + (kahan ? 1 : 0)) {
+            case 2: rc = launch_forward_batch<1, 1>(b, total_items, sm_count, s); break;
+            case 3: rc = launch_forward_batch<1, 2>(b, total_items, sm_count, s); break;
+            case 4: rc = launch_forward_batch<2, 1>(b, total_items, sm_count, s); break;
+            case 5: rc = launch_forward_batch<2, 2>(b, total_items, sm_count, s); break;
+            case 8: rc = launch_forward_batch<4, 1>(b, total_items, sm_count, s); break;
+            case 9: rc = launch_forward_batch<4, 2>(b, total_items, sm_count, s); break;
+            case 16: rc = launch_forward_batch<8, 1>(b, total_items, sm_count, s); break;
+            case 17: rc = launch_forward_batch<8, 2>(b, total_items, sm_count, s); break;
+            default: return SERBF_EINVAL;
+        }
+    }
+    if (rc) return rc;
+    launch_pdl(k_fwd_finish_batch<true>, dim3((unsigned)finish_blocks, (unsigned)nfields), dim3(kFinishThreads), 0, s,
+               static_cast<const FinishArgs *>(fin));
+    SERBF_CHECK_LAUNCH();
+    return SERBF_OK;
+}
+
+}  // namespace serbf
 
 extern "C" int serbf_forward(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg, float *psi,
                              float *err, uint8_t *mask, double *stats, serbf_workspace *ws, void *stream) {

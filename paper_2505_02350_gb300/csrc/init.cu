@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kInitThreads) k_inscribed(InitArgs a) {
                 const uint32_t rk = a.rank[k];
                 if (rk == 0xffffffffu || a.removed[rk]) continue;
                 const float dx = __fsub_rn(a.x[k], cx), dy = __fsub_rn(a.y[k], cy), dz = __fsub_rn(a.z[k], cz);
-                const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+                const float d2 = support_d2(dx, dy, dz);
                 if (!(d2 > r2)) a.removed[rk] = 1;
             }
         }

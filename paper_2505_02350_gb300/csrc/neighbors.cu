@@ -5,6 +5,7 @@
 // support predicate per pair.  On request the explicit kernel-major and
 // point-major CSR lists are produced from the same structure.
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 
@@ -60,12 +61,11 @@ __device__ __forceinline__ void prep_kernels(const float *p, int cap, int m, flo
 // (b + 1) kOrderChunk).  k_order_items: block b places the same items; a
 // class starts after all heavier classes and after this class in earlier
 // chunks, and the rank inside the chunk comes from ballots in item order.
-__global__ void __launch_bounds__(kOrderChunk) k_class_count(const uint8_t *item_class, int64_t nitems,
-                                                             uint32_t *hist) {
+__device__ __forceinline__ void class_count_body(const uint8_t *item_class, int64_t nitems, uint32_t *hist, int bx) {
     constexpr int NW = kOrderChunk / 32;
     __shared__ uint32_t s_wcnt[NW][kCostClasses];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * kOrderChunk + threadIdx.x;
+    const int64_t i = (int64_t)bx * kOrderChunk + threadIdx.x;
     const int cls = i < nitems ? (int)item_class[i] : -1;
 #pragma unroll
     for (int c = 0; c < kCostClasses; ++c) {
@@ -76,18 +76,23 @@ __global__ void __launch_bounds__(kOrderChunk) k_class_count(const uint8_t *item
     if (threadIdx.x < kCostClasses) {
         uint32_t t = 0;
         for (int w = 0; w < NW; ++w) t += s_wcnt[w][threadIdx.x];
-        hist[(size_t)blockIdx.x * kCostClasses + threadIdx.x] = t;
+        hist[(size_t)bx * kCostClasses + threadIdx.x] = t;
     }
 }
 
-__global__ void __launch_bounds__(kOrderChunk) k_order_items(const uint8_t *item_class, const uint32_t *hist,
-                                                             const uint4 *item_rec, uint4 *order_rec, int64_t nitems) {
+__global__ void __launch_bounds__(kOrderChunk) k_class_count(const uint8_t *item_class, int64_t nitems,
+                                                             uint32_t *hist) {
+    class_count_body(item_class, nitems, hist, blockIdx.x);
+}
+
+__device__ __forceinline__ void order_items_body(const uint8_t *item_class, const uint32_t *hist,
+                                                 const uint4 *item_rec, uint4 *order_rec, int64_t nitems, int bx) {
     constexpr int NW = kOrderChunk / 32;
     __shared__ uint32_t s_base[kCostClasses];      // first position of each class for this chunk
     __shared__ uint32_t s_tot[kCostClasses];
     __shared__ uint32_t s_wcnt[NW][kCostClasses];  // per warp: class counts, then offsets
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nchunks = (int)((nitems + kOrderChunk - 1) / kOrderChunk), b = blockIdx.x;
+    const int nchunks = (int)((nitems + kOrderChunk - 1) / kOrderChunk), b = bx;
     // class totals and this class's count in earlier chunks: warp c handles class c
     if (warp < kCostClasses) {
         uint32_t tot = 0, before = 0;
@@ -129,22 +134,25 @@ __global__ void __launch_bounds__(kOrderChunk) k_order_items(const uint8_t *item
     if (cls >= 0) order_rec[s_wcnt[warp][cls] + rank] = r;
 }
 
+__global__ void __launch_bounds__(kOrderChunk) k_order_items(const uint8_t *item_class, const uint32_t *hist,
+                                                             const uint4 *item_rec, uint4 *order_rec, int64_t nitems) {
+    order_items_body(item_class, hist, item_rec, order_rec, nitems, blockIdx.x);
+}
+
 // The per-step rebuild in one launch: blocks [0, nsuper) list, per super
 // cell, every kernel whose support may reach its box (centre and r2 taken
 // from the parameters with the same float operations as the records); the
 // remaining blocks write the per-kernel records.
-__global__ void __launch_bounds__(256) k_rebuild(const float *p, int cap, const int32_t *m_dev, float nle,
-                                                 float4 *kfwd, float4 *kbwd, const float4 *slo, const float4 *shi,
-                                                 int nsuper, uint32_t *list, uint32_t *cnt, int scap, int32_t *status,
-                                                 long long *needed) {
-    pdl_wait();
-    pdl_trigger();
+__device__ __forceinline__ void rebuild_body(const float *p, int cap, const int32_t *m_dev, float nle, float4 *kfwd,
+                                             float4 *kbwd, const float4 *slo, const float4 *shi, int nsuper,
+                                             uint32_t *list, uint32_t *cnt, int scap, int32_t *status,
+                                             long long *needed, int bx, int nbx) {
     __shared__ uint32_t tmp[33];
     const int m = *m_dev;
-    const int s = blockIdx.x;
+    const int s = bx;
     if (s >= nsuper) {
         prep_kernels(p, cap, m, nle, kfwd, kbwd, (s - nsuper) * blockDim.x + threadIdx.x,
-                     (gridDim.x - nsuper) * blockDim.x);
+                     (nbx - nsuper) * blockDim.x);
         return;
     }
     const float4 lo = slo[s], hi = shi[s];
@@ -175,23 +183,31 @@ __global__ void __launch_bounds__(256) k_rebuild(const float *p, int cap, const 
     }
 }
 
+__global__ void __launch_bounds__(256) k_rebuild(const float *p, int cap, const int32_t *m_dev, float nle,
+                                                 float4 *kfwd, float4 *kbwd, const float4 *slo, const float4 *shi,
+                                                 int nsuper, uint32_t *list, uint32_t *cnt, int scap, int32_t *status,
+                                                 long long *needed) {
+    pdl_wait();
+    pdl_trigger();
+    rebuild_body(p, cap, m_dev, nle, kfwd, kbwd, slo, shi, nsuper, list, cnt, scap, status, needed, blockIdx.x,
+                 gridDim.x);
+}
+
 // Two-level rebuild, for many super cells and kernels.  First launch: blocks
 // [0, ncoarse) list, per block of 2 x 2 x 2 super cells, every kernel whose
 // support may reach the union of their boxes (as k_rebuild does per super
 // cell); the remaining blocks write the per-kernel records.
-__global__ void __launch_bounds__(256) k_coarse_lists(const float *p, int cap, const int32_t *m_dev, float nle,
-                                                      float4 *kfwd, float4 *kbwd, const float4 *slo,
-                                                      const float4 *shi, int nsx, int nsy, int nsz, int ncoarse,
-                                                      uint32_t *list, uint32_t *cnt, int scap) {
-    pdl_wait();
-    pdl_trigger();
+__device__ __forceinline__ void coarse_lists_body(const float *p, int cap, const int32_t *m_dev, float nle,
+                                                  float4 *kfwd, float4 *kbwd, const float4 *slo, const float4 *shi,
+                                                  int nsx, int nsy, int nsz, int ncoarse, uint32_t *list,
+                                                  uint32_t *cnt, int scap, int bx, int nbx) {
     __shared__ uint32_t tmp[33];
     __shared__ float4 s_lo, s_hi;
     const int m = *m_dev;
-    const int c = blockIdx.x;
+    const int c = bx;
     if (c >= ncoarse) {
         prep_kernels(p, cap, m, nle, kfwd, kbwd, (c - ncoarse) * blockDim.x + threadIdx.x,
-                     (gridDim.x - ncoarse) * blockDim.x);
+                     (nbx - ncoarse) * blockDim.x);
         return;
     }
     if (threadIdx.x == 0) {
@@ -234,19 +250,27 @@ __global__ void __launch_bounds__(256) k_coarse_lists(const float *p, int cap, c
     if (threadIdx.x == 0) cnt[c] = count;
 }
 
+__global__ void __launch_bounds__(256) k_coarse_lists(const float *p, int cap, const int32_t *m_dev, float nle,
+                                                      float4 *kfwd, float4 *kbwd, const float4 *slo,
+                                                      const float4 *shi, int nsx, int nsy, int nsz, int ncoarse,
+                                                      uint32_t *list, uint32_t *cnt, int scap) {
+    pdl_wait();
+    pdl_trigger();
+    coarse_lists_body(p, cap, m_dev, nle, kfwd, kbwd, slo, shi, nsx, nsy, nsz, ncoarse, list, cnt, scap, blockIdx.x,
+                      gridDim.x);
+}
+
 // Second launch: each super cell keeps the kernels of its block's list that
 // reach its own box, with the centre and r2 of the records (the values
 // k_rebuild computes), so the lists equal the one-level ones: a kernel that
 // reaches a super cell's box reaches the block's box, which contains it.  A
 // block list that overflowed is not used: its super cells test every kernel.
-__global__ void __launch_bounds__(256) k_fine_lists(const int32_t *m_dev, const float4 *kfwd, const float4 *slo,
-                                                    const float4 *shi, int nsx, int nsy, int nsuper,
-                                                    const uint32_t *clist, const uint32_t *ccnt, uint32_t *list,
-                                                    uint32_t *cnt, int scap, int32_t *status, long long *needed) {
-    pdl_wait();
-    pdl_trigger();
+__device__ __forceinline__ void fine_lists_body(const int32_t *m_dev, const float4 *kfwd, const float4 *slo,
+                                                const float4 *shi, int nsx, int nsy, int nsuper, const uint32_t *clist,
+                                                const uint32_t *ccnt, uint32_t *list, uint32_t *cnt, int scap,
+                                                int32_t *status, long long *needed, int bx) {
     __shared__ uint32_t tmp[33];
-    const int s = blockIdx.x;
+    const int s = bx;
     if (s >= nsuper) return;
     const float4 lo = slo[s], hi = shi[s];
     if (!(lo.x <= hi.x)) {
@@ -282,6 +306,78 @@ __global__ void __launch_bounds__(256) k_fine_lists(const int32_t *m_dev, const 
             atomicMax(needed + 0, (long long)count);
         }
     }
+}
+
+__global__ void __launch_bounds__(256) k_fine_lists(const int32_t *m_dev, const float4 *kfwd, const float4 *slo,
+                                                    const float4 *shi, int nsx, int nsy, int nsuper,
+                                                    const uint32_t *clist, const uint32_t *ccnt, uint32_t *list,
+                                                    uint32_t *cnt, int scap, int32_t *status, long long *needed) {
+    pdl_wait();
+    pdl_trigger();
+    fine_lists_body(m_dev, kfwd, slo, shi, nsx, nsy, nsuper, clist, ccnt, list, cnt, scap, status, needed,
+                    blockIdx.x);
+}
+
+// ---------------------------------------------------------------- batches of fields
+// One field's neighbour rebuild for the batched epoch: the arguments of the
+// single-field launches, and which form (one or two levels) it takes.
+struct RebuildArgs {
+    const float *p;
+    int cap;
+    const int32_t *m_dev;
+    float nle;
+    float4 *kfwd, *kbwd;
+    const float4 *slo, *shi;
+    int nsx, nsy, nsz, nsuper, ncoarse;
+    uint32_t *list, *cnt, *clist, *ccnt;
+    int scap;
+    int two_level;
+    int32_t *status;
+    long long *needed;
+    int level1_blocks;                 // blocks this field uses in the first launch
+    const uint8_t *item_class;         // heavy-first order of the forward's items
+    uint32_t *class_hist;
+    const uint4 *item_rec;
+    uint4 *order_rec;
+    int64_t nitems;
+};
+
+// Field blockIdx.y: the item order for the next forward (two launches).
+__global__ void __launch_bounds__(kOrderChunk) k_class_count_batch(const RebuildArgs *ra) {
+    const RebuildArgs &r = ra[blockIdx.y];
+    if ((int64_t)blockIdx.x * kOrderChunk >= r.nitems) return;
+    class_count_body(r.item_class, r.nitems, r.class_hist, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kOrderChunk) k_order_items_batch(const RebuildArgs *ra) {
+    const RebuildArgs &r = ra[blockIdx.y];
+    if ((int64_t)blockIdx.x * kOrderChunk >= r.nitems) return;
+    order_items_body(r.item_class, r.class_hist, r.item_rec, r.order_rec, r.nitems, blockIdx.x);
+}
+
+// First rebuild launch: one-level fields rebuild, two-level fields list the
+// kernels of their blocks of 2 x 2 x 2 super cells; both write the records.
+__global__ void __launch_bounds__(256) k_rebuild_batch(const RebuildArgs *ra) {
+    pdl_wait();
+    pdl_trigger();
+    const RebuildArgs &r = ra[blockIdx.y];
+    if ((int)blockIdx.x >= r.level1_blocks) return;
+    if (r.two_level)
+        coarse_lists_body(r.p, r.cap, r.m_dev, r.nle, r.kfwd, r.kbwd, r.slo, r.shi, r.nsx, r.nsy, r.nsz, r.ncoarse,
+                          r.clist, r.ccnt, r.scap, blockIdx.x, r.level1_blocks);
+    else
+        rebuild_body(r.p, r.cap, r.m_dev, r.nle, r.kfwd, r.kbwd, r.slo, r.shi, r.nsuper, r.list, r.cnt, r.scap,
+                     r.status, r.needed, blockIdx.x, r.level1_blocks);
+}
+
+// Second rebuild launch: the super-cell lists of two-level fields.
+__global__ void __launch_bounds__(256) k_fine_lists_batch(const RebuildArgs *ra) {
+    pdl_wait();
+    pdl_trigger();
+    const RebuildArgs &r = ra[blockIdx.y];
+    if (!r.two_level || (int)blockIdx.x >= r.nsuper) return;
+    fine_lists_body(r.m_dev, r.kfwd, r.slo, r.shi, r.nsx, r.nsy, r.nsuper, r.clist, r.ccnt, r.list, r.cnt, r.scap,
+                    r.status, r.needed, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- point-major CSR
@@ -369,6 +465,77 @@ bool rebuild_two_level(int levels, int64_t nsuper, int cap) {
 }  // namespace
 
 namespace serbf {
+}  // namespace serbf
+
+namespace serbf {
+
+size_t rebuild_args_size() { return sizeof(RebuildArgs); }
+
+// Host record of one field's neighbour rebuild for a batch (out:
+// sizeof(RebuildArgs) bytes); *level1_blocks, *chunks and *nsuper size the
+// batch's grids, *two_level says which form the field takes.
+int batch_rebuild_args(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg,
+                       serbf_workspace *ws, void *out, int *level1_blocks, int64_t *chunks, int *nsuper,
+                       int *two_level) {
+    if (!pts || !prm || !cfg || !ws_ok(ws)) return SERBF_EINVAL;
+    if (!prm->p || !prm->m || prm->cap < 1 || prm->cap > ws->sz.max_kernels) return SERBF_EINVAL;
+    if (pts->n != ws->npoints) return SERBF_EINVAL;
+    if (!(cfg->eps > 0.0 && cfg->eps < 1.0) || cfg->rebuild_levels < 0 || cfg->rebuild_levels > 2) return SERBF_EINVAL;
+    RebuildArgs r;
+    memset(&r, 0, sizeof(r));
+    const int nsx = ws->ns[0], nsy = ws->ns[1], nsz = ws->ns[2];
+    const int64_t ncoarse = (int64_t)((nsx + 1) / 2) * ((nsy + 1) / 2) * ((nsz + 1) / 2);
+    const int prep_blocks = (prm->cap + 255) / 256;
+    r.p = prm->p;
+    r.cap = prm->cap;
+    r.m_dev = prm->m;
+    r.nle = (float)(-log(cfg->eps));
+    r.kfwd = ws->kfwd;
+    r.kbwd = ws->kbwd;
+    r.slo = ws->sup_lo;
+    r.shi = ws->sup_hi;
+    r.nsx = nsx;
+    r.nsy = nsy;
+    r.nsz = nsz;
+    r.nsuper = ws->nsuper;
+    r.ncoarse = (int)ncoarse;
+    r.list = ws->sup_list;
+    r.cnt = ws->sup_cnt;
+    r.clist = ws->crs_list;
+    r.ccnt = ws->crs_cnt;
+    r.scap = ws->sz.super_cap;
+    r.two_level = rebuild_two_level(cfg->rebuild_levels, ws->nsuper, prm->cap) && ncoarse <= ws->max_coarse;
+    r.status = ws->status;
+    r.needed = ws->needed;
+    r.level1_blocks = (r.two_level ? (int)ncoarse : ws->nsuper) + prep_blocks;
+    r.item_class = ws->item_class;
+    r.class_hist = ws->class_hist;
+    r.item_rec = ws->item_rec;
+    r.order_rec = ws->order_rec;
+    r.nitems = ws->nitems;
+    memcpy(out, &r, sizeof(r));
+    *level1_blocks = r.level1_blocks;
+    *chunks = (ws->nitems + kOrderChunk - 1) / kOrderChunk;
+    *nsuper = ws->nsuper;
+    *two_level = r.two_level;
+    return SERBF_OK;
+}
+
+// The batched rebuild: item order (two launches), then the lists and
+// records (one launch, two when some field takes two levels).
+int batch_rebuild_launch(const void *args, int nfields, int level1_blocks, int64_t chunks, int nsuper, int two_level,
+                         cudaStream_t s) {
+    const RebuildArgs *ra = static_cast<const RebuildArgs *>(args);
+    if (chunks > 0) {
+        k_class_count_batch<<<dim3((unsigned)chunks, (unsigned)nfields), kOrderChunk, 0, s>>>(ra);
+        k_order_items_batch<<<dim3((unsigned)chunks, (unsigned)nfields), kOrderChunk, 0, s>>>(ra);
+    }
+    launch_pdl(k_rebuild_batch, dim3((unsigned)level1_blocks, (unsigned)nfields), dim3(256), 0, s, ra);
+    if (two_level) launch_pdl(k_fine_lists_batch, dim3((unsigned)nsuper, (unsigned)nfields), dim3(256), 0, s, ra);
+    SERBF_CHECK_LAUNCH();
+    return SERBF_OK;
+}
+
 }  // namespace serbf
 
 extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params *prm, const serbf_config *cfg,

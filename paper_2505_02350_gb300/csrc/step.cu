@@ -5,6 +5,7 @@
 // Two grid-wide launches whose last blocks finish the reductions.  Also the
 // Eq. 3-27 compaction.
 #include <math.h>
+#include <string.h>
 
 #include "common.cuh"
 
@@ -249,29 +250,28 @@ __device__ void finish_step(const StepArgs &a, double bf, double alpha, double b
 // ---------------------------------------------------------------- grid path
 // Stage 1 (one thread per kernel, many blocks): the sums of alpha_terms; the
 // last block turns them into alpha, beta and the Adam bias corrections.
-__global__ void __launch_bounds__(kStepThreads) k_step_alpha(StepArgs a) {
-    pdl_wait();
-    pdl_trigger();
+// Block bx of nbx.
+__device__ __forceinline__ void step_alpha_body(const StepArgs &a, int bx, int nbx) {
     __shared__ double sh3[33][3];
     __shared__ bool s_last;
     const int m = *a.m;
     const bool use_l1 = a.st->l1_optim && (a.stats[SERBF_STAT_MAXE] < a.c.tau_m);
     double part[3] = {0.0, 0.0, 0.0};
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = bx * blockDim.x + threadIdx.x;
     if (j < m) alpha_terms(a, j, use_l1, part);
     double tot[3];
     block_sums_d3(part, sh3, tot);
     double *bp = reinterpret_cast<double *>(a.part);  // 3 doubles per block
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 3; ++k) bp[3 * blockIdx.x + k] = tot[k];
+        for (int k = 0; k < 3; ++k) bp[3 * bx + k] = tot[k];
         __threadfence();
-        s_last = atomicAdd(a.counter, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(a.counter, 1u) == (unsigned)nbx - 1;
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     double acc[3] = {0.0, 0.0, 0.0};
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+    for (unsigned b = threadIdx.x; b < (unsigned)nbx; b += blockDim.x)
         for (int k = 0; k < 3; ++k) acc[k] += __ldcg(bp + 3 * b + k);
     double fin[3];
     block_sums_d3(acc, sh3, fin);
@@ -283,23 +283,27 @@ __global__ void __launch_bounds__(kStepThreads) k_step_alpha(StepArgs a) {
     }
 }
 
-// Stage 2 (one thread per parameter, many blocks): adam_param; then the last
-// block runs the epoch tail.
-__global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
+__global__ void __launch_bounds__(kStepThreads) k_step_alpha(StepArgs a) {
     pdl_wait();
     pdl_trigger();
+    step_alpha_body(a, blockIdx.x, gridDim.x);
+}
+
+// Stage 2 (one thread per parameter, many blocks): adam_param; then the last
+// block runs the epoch tail.  Block (bx, r) of nbx x 10.
+__device__ __forceinline__ void step_adam_body(const StepArgs &a, int bx, int r, int nbx) {
     __shared__ ff sh1[33][1];
     __shared__ bool s_last;
     __shared__ __align__(8) uint32_t s_words[kStateWords];
     const int m = *a.m;
-    const int r = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = bx * blockDim.x + threadIdx.x;
     const float sc[4] = {(float)a.scal[0], (float)a.scal[1], (float)a.scal[2], (float)a.scal[3]};
     const float lr = (float)a.st->lr, taud = tau_d_float(a.c.tau_d);
     float bfc[1] = {0.f};
     if (j < m) bfc[0] = adam_param(a, r, j, sc, lr, taud);
     ff tot[1];
     block_sums_ff<1>(bfc, sh1, tot);
-    const unsigned nblocks = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
+    const unsigned nblocks = (unsigned)nbx * SERBF_NPARAM, bid = (unsigned)r * nbx + bx;
     if (threadIdx.x == 0) {
         a.part[bid] = tot[0].hi;
         __threadfence();
@@ -317,11 +321,15 @@ __global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
     if (threadIdx.x == 0) a.counter[1] = 0u;
 }
 
-// Eq. 3-27: stable compaction of the kernels with |w| >= tau_d.
-__global__ void __launch_bounds__(kStepThreads) k_prune(float *p, float *am, float *av, int32_t *m_dev, int cap,
-                                                        serbf_state *st, double tau_d, int force) {
+__global__ void __launch_bounds__(kStepThreads) k_step_adam(StepArgs a) {
     pdl_wait();
     pdl_trigger();
+    step_adam_body(a, blockIdx.x, blockIdx.y, gridDim.x);
+}
+
+// Eq. 3-27: stable compaction of the kernels with |w| >= tau_d.
+__device__ __forceinline__ void prune_body(float *p, float *am, float *av, int32_t *m_dev, int cap, serbf_state *st,
+                                           double tau_d, int force) {
     __shared__ uint32_t tmp[33];
     __shared__ int s_go;
     if (threadIdx.x == 0) s_go = force || st->do_prune;
@@ -367,7 +375,81 @@ __global__ void __launch_bounds__(kStepThreads) k_prune(float *p, float *am, flo
     }
 }
 
+__global__ void __launch_bounds__(kStepThreads) k_prune(float *p, float *am, float *av, int32_t *m_dev, int cap,
+                                                        serbf_state *st, double tau_d, int force) {
+    pdl_wait();
+    pdl_trigger();
+    prune_body(p, am, av, m_dev, cap, st, tau_d, force);
+}
+
+// ---------------------------------------------------------------- batches of fields
+// One field's step for the batched epoch: its arguments and its own block
+// count (blocks of the batch grid beyond it leave at once, so each field's
+// last-block hand-offs count only its own blocks).
+struct StepBatch {
+    StepArgs a;
+    int nb;
+};
+
+__global__ void __launch_bounds__(kStepThreads) k_step_alpha_batch(const StepBatch *sb) {
+    pdl_wait();
+    pdl_trigger();
+    const StepBatch &b = sb[blockIdx.y];
+    if ((int)blockIdx.x >= b.nb) return;
+    step_alpha_body(b.a, blockIdx.x, b.nb);
+}
+
+__global__ void __launch_bounds__(kStepThreads) k_step_adam_batch(const StepBatch *sb) {
+    pdl_wait();
+    pdl_trigger();
+    const StepBatch &b = sb[blockIdx.z];
+    if ((int)blockIdx.x >= b.nb) return;
+    step_adam_body(b.a, blockIdx.x, blockIdx.y, b.nb);
+}
+
+// Eq. 3-27 of field blockIdx.x.
+__global__ void __launch_bounds__(kStepThreads) k_prune_batch(const StepBatch *sb) {
+    pdl_wait();
+    pdl_trigger();
+    const StepArgs &a = sb[blockIdx.x].a;
+    prune_body(a.p, a.am, a.av, const_cast<int32_t *>(a.m), a.cap, a.st, a.c.tau_d, 0);
+}
+
 }  // namespace
+
+namespace serbf {
+
+size_t step_args_size() { return sizeof(StepBatch); }
+
+// Host record of one field's step for a batch (out: sizeof(StepBatch) bytes).
+int batch_step_args(serbf_params *prm, const float *grad, float *adam_m, float *adam_v, serbf_state *st_dev,
+                    double *stats, const serbf_config *cfg, serbf_workspace *ws, void *out, int *nb) {
+    if (!prm || !prm->p || !prm->m || prm->cap < 1 || !grad || !adam_m || !adam_v || !st_dev || !stats || !cfg)
+        return SERBF_EINVAL;
+    if (!ws || ws->magic != kMagic || prm->cap > ws->sz.max_kernels) return SERBF_EINVAL;
+    if (cfg->k_l2 < 1 || cfg->k_l2 > 64 || cfg->k_l1 < 1 || cfg->k_l1 > 256) return SERBF_EINVAL;
+    if (!(cfg->lr >= 0.0) || !(cfg->beta1 >= 0.0 && cfg->beta1 < 1.0) || !(cfg->beta2 >= 0.0 && cfg->beta2 < 1.0))
+        return SERBF_EINVAL;
+    StepBatch b{StepArgs{prm->p, prm->m, prm->cap, grad, adam_m, adam_v, st_dev, stats, *cfg, ws->step_part,
+                         ws->step_scal, ws->counters + 2},
+                (prm->cap + kStepThreads - 1) / kStepThreads};
+    memcpy(out, &b, sizeof(b));
+    *nb = b.nb;
+    return SERBF_OK;
+}
+
+// The batched step (two launches) and deletion (one).
+int batch_step_launch(const void *args, int nfields, int max_nb, cudaStream_t s) {
+    const StepBatch *sb = static_cast<const StepBatch *>(args);
+    launch_pdl(k_step_alpha_batch, dim3((unsigned)max_nb, (unsigned)nfields), dim3(kStepThreads), 0, s, sb);
+    launch_pdl(k_step_adam_batch, dim3((unsigned)max_nb, SERBF_NPARAM, (unsigned)nfields), dim3(kStepThreads), 0, s,
+               sb);
+    launch_pdl(k_prune_batch, dim3((unsigned)nfields), dim3(kStepThreads), 0, s, sb);
+    SERBF_CHECK_LAUNCH();
+    return SERBF_OK;
+}
+
+}  // namespace serbf
 
 extern "C" int serbf_step(serbf_params *prm, const float *grad, float *adam_m, float *adam_v, serbf_state *st_dev,
                           double *stats, const serbf_config *cfg, serbf_workspace *ws, void *stream) {

@@ -93,3 +93,23 @@ def test_uninitialised_workspace_is_rejected(native):
     cfg = native.config_default()
     assert native.lib.serbf_forward(C.byref(pts), C.byref(prm), C.byref(cfg), None, None, None, None,
                                     C.addressof(ws), None) == native.SERBF_EINVAL
+
+
+def test_batch_entry_points_check_arguments_on_the_host(native):
+    L = native.lib
+    E = native.SERBF_EINVAL
+    b = C.c_size_t()
+    assert L.serbf_batch_bytes(0, C.byref(b)) == E
+    assert L.serbf_batch_bytes(1025, C.byref(b)) == E
+    assert L.serbf_batch_bytes(64, C.byref(b)) == native.SERBF_OK and b.value > 0
+    bb = native.batch_struct()
+    assert L.serbf_epoch_batched(C.addressof(bb), None) == E  # not initialised
+    assert L.serbf_batch_warps(C.addressof(bb)) == E
+    assert L.serbf_batch_init(C.addressof(bb), None, 1, 0, None, 0, None) == E
+    # a field without a workspace is rejected before anything touches the device
+    f = (native.Field * 1)()
+    cfg = native.config_default()
+    f[0].cfg = C.pointer(cfg)
+    assert L.serbf_batch_init(C.addressof(bb), f, 1, 0, C.c_void_p(256), 1 << 20, None) == E
+    assert L.serbf_batch_init(C.addressof(bb), f, 1, 3, C.c_void_p(256), 1 << 20, None) == E  # bad split
+

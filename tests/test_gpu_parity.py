@@ -405,7 +405,7 @@ def test_prune_parity(torch, orc):
 @pytest.mark.parametrize("layers,frac,radius,cap,tau_m", [
     ([32], 0.01, None, 2048, None),           # the paper's 1 %: a few hundred candidates, sorted in shared memory
     ([32], 0.0, None, 16384, None),           # no limit: every candidate is selected
-    ([32, 64], 0.25, 0.0, 131072, 2e-6),      # k > 8192: the block radix sort.  A candidate threshold of
+    ([32, 64], 0.75, 0.0, 131072, 2e-6),      # k > 8192: the block radix sort.  A candidate threshold of
                                               # 1e-6 (> eps) lets most of id_all compete; radius 0 keeps every
                                               # selected point, so the appended kernels give the whole
                                               # selection in order
@@ -432,7 +432,7 @@ def test_add_parity(torch, orc, layers, frac, radius, cap, tau_m):
     pb.stats[3] = float(cnt)
     k = math.ceil(frac * cnt) if frac > 0 else -1
     cand = orc.select_topk(E, mask, thresh, k)
-    if frac == 0.25:
+    if frac == 0.75:
         assert len(cand) > 8192
     r2 = np.float32(pb.cfg.add_radius * pb.cfg.add_radius)
     if radius == 0.0:

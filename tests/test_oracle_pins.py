@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import synth
+from fp32 import fmaf, support_d2
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -209,7 +210,41 @@ def test_support_predicate_is_strict(orc):
 def _np_member(px, py, pz, cx, cy, cz, r2):
     f = np.float32
     dx, dy, dz = f(px) - f(cx), f(py) - f(cy), f(pz) - f(cz)
-    return ((dx * dx + dy * dy) + dz * dz) < f(r2)
+    return support_d2(dx, dy, dz) < f(r2)
+
+
+def test_fmaf_helper_rounds_once():
+    """The float32 fma of the pins against exact rational arithmetic."""
+    from fractions import Fraction
+    g = np.random.default_rng(30)
+    a, b, c = (g.normal(0, 1, 400).astype(np.float32) for _ in range(3))
+    # a case whose float64 sum lies exactly halfway between two float32 values
+    a = np.append(a, np.float32(1.0)); b = np.append(b, np.float32(1.0))
+    c = np.append(c, np.float32(2.0 ** -24) + np.float32(2.0 ** -60))
+    got = fmaf(a, b, c)
+    for k in range(a.size):
+        exact = Fraction(float(a[k])) * Fraction(float(b[k])) + Fraction(float(c[k]))
+        lo = np.float32(float(exact))
+        cands = [np.nextafter(lo, np.float32(-np.inf)), lo, np.nextafter(lo, np.float32(np.inf))]
+        dist = [abs(Fraction(float(v)) - exact) for v in cands]
+        best = min(dist)
+        assert abs(Fraction(float(got[k])) - exact) == best, k
+
+
+def test_support_predicate_uses_the_fma_form(orc):
+    """Where the canonical form fma(dz, dz, fma(dy, dy, fl(dx dx))) and the
+    unfused sum of rounded squares give different floats, the oracle's test
+    follows the canonical form (r2 set between the two values)."""
+    g = np.random.default_rng(31)
+    d = g.uniform(-0.3, 0.3, (3, 400000)).astype(np.float32)
+    canon = support_d2(d[0], d[1], d[2])
+    plain = ((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]).astype(np.float32)
+    diff = np.flatnonzero(canon != plain)
+    assert diff.size >= 20
+    for k in diff[:40]:
+        r2 = max(canon[k], plain[k])  # strictly above the smaller one only
+        p = (float(d[0, k]), float(d[1, k]), float(d[2, k]))
+        assert orc.in_support(p, (0.0, 0.0, 0.0), float(r2)) == bool(canon[k] < r2)
 
 
 def test_neighbors_match_numpy_bruteforce(orc):
@@ -580,7 +615,7 @@ def test_local_max_bruteforce(orc):
     got = orc.local_max(x, y, z, E, mask, cand, r2)
     ref = []
     for i in cand:
-        d2 = ((x - x[i]) * (x - x[i]) + (y - y[i]) * (y - y[i])) + (z - z[i]) * (z - z[i])
+        d2 = support_d2(x - x[i], y - y[i], z - z[i])
         nb = (d2 <= r2) & mask.astype(bool)
         if np.all(np.abs(E[nb]) <= abs(E[i])):
             ref.append(i)
@@ -639,7 +674,7 @@ def test_inscribed_properties_on_sphere(orc):
     # the first centre is the deepest interior point; radii never grow
     assert idx[0] == interior[np.argmax(np.abs(S[interior]))]
     assert np.all(np.diff(r) <= 0)
-    d2 = lambda i, j: (np.float32(x[i] - x[j]) ** 2 + np.float32(y[i] - y[j]) ** 2) + np.float32(z[i] - z[j]) ** 2
+    d2 = lambda i, j: support_d2(np.float32(x[i] - x[j]), np.float32(y[i] - y[j]), np.float32(z[i] - z[j]))
     # every interior point lies in some selected sphere; no centre lies in an earlier one
     cover = np.zeros(interior.size, bool)
     for c, rc in zip(idx, r):
