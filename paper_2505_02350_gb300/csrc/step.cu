@@ -102,11 +102,13 @@ __device__ __forceinline__ void alpha_finish(const StepArgs &a, bool use_l1, con
     const double num = fin[1], den = fin[2];
     double al = 1.0;
     if (use_l1 && den > 0.0) al = fmin(1.0, fmax(0.0, num / den));
-    const double t = (double)(a.st->adam_t + 1);
+    // the Adam bias corrections feed a float update: float powers (a double
+    // pow costs microseconds on this part's FP64 unit)
+    const float t = (float)(a.st->adam_t + 1);
     sc[0] = al;
     sc[1] = 1.0 - al;
-    sc[2] = 1.0 - pow(a.c.beta1, t);
-    sc[3] = 1.0 - pow(a.c.beta2, t);
+    sc[2] = 1.0f - powf((float)a.c.beta1, t);
+    sc[3] = 1.0f - powf((float)a.c.beta2, t);
     a.stats[SERBF_STAT_L1] = fin[0];
     a.stats[SERBF_STAT_ALPHA] = al;
     a.stats[SERBF_STAT_BETA] = 1.0 - al;
