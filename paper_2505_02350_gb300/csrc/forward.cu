@@ -414,8 +414,17 @@ __device__ __forceinline__ void forward_share(const FwdArgs &a, const ItemInfo &
 // integer atomics: integer addition is associative, so the totals do not
 // depend on the order in which items finish.
 
+// The nz points in pairs: pair k holds points 2k and 2k + 1 as two 16-byte
+// words (x0, x1, y0, y1) and (z0, z1, e0, e1), so one pair of points is two
+// 16-byte loads that give the packed operands directly.
 struct NzPoints {
-    float x[kNz], y[kNz], z[kNz], e[kNz];
+    float4 v[kNz];  // kNz / 2 pairs, two words each
+    __device__ __forceinline__ float &at(int field, int i) {
+        // field 0..3 = x, y, z, e of point i
+        float4 &w = v[2 * (i >> 1) + (field >> 1)];
+        const int k = 2 * (field & 1) + (i & 1);
+        return k == 0 ? w.x : (k == 1 ? w.y : (k == 2 ? w.z : w.w));
+    }
 };
 
 __device__ __forceinline__ f2 f2_dup(float v) { return f2_pack(v, v); }
@@ -478,8 +487,9 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
 #pragma unroll 4
         for (int pp = sub; pp < cntp; pp += L) {
             const int i = base + 2 * pp;
-            const f2 px = *reinterpret_cast<const f2 *>(&nz.x[i]), py = *reinterpret_cast<const f2 *>(&nz.y[i]);
-            const f2 pz = *reinterpret_cast<const f2 *>(&nz.z[i]), pe = *reinterpret_cast<const f2 *>(&nz.e[i]);
+            const ulonglong2 wa = *reinterpret_cast<const ulonglong2 *>(&nz.v[i]);
+            const ulonglong2 wb = *reinterpret_cast<const ulonglong2 *>(&nz.v[i + 1]);
+            const f2 px = wa.x, py = wa.y, pz = wb.x, pe = wb.y;
             const f2 dx = f2_sub(px, cx), dy = f2_sub(py, cy), dz = f2_sub(pz, cz);
             const f2 zz = f2_mul(dz, dz);
             // q = Delta^T Q Delta (log2 units), the forward's operation order
@@ -610,18 +620,18 @@ __device__ __forceinline__ int nz_tile(NzPoints &nzp, int base, bool nz, float x
     const int cnt = __popc(bal);
     if (nz) {
         const int i = base + __popc(bal & ((1u << lane) - 1u));
-        nzp.x[i] = x;
-        nzp.y[i] = y;
-        nzp.z[i] = z;
-        nzp.e[i] = e;
+        nzp.at(0, i) = x;
+        nzp.at(1, i) = y;
+        nzp.at(2, i) = z;
+        nzp.at(3, i) = e;
     }
     __syncwarp();
     if ((cnt & 1) && lane == 0) {
         // pad: a copy of the last point with E = 0 (finite, adds nothing)
-        nzp.x[base + cnt] = nzp.x[base + cnt - 1];
-        nzp.y[base + cnt] = nzp.y[base + cnt - 1];
-        nzp.z[base + cnt] = nzp.z[base + cnt - 1];
-        nzp.e[base + cnt] = 0.f;
+        nzp.at(0, base + cnt) = nzp.at(0, base + cnt - 1);
+        nzp.at(1, base + cnt) = nzp.at(1, base + cnt - 1);
+        nzp.at(2, base + cnt) = nzp.at(2, base + cnt - 1);
+        nzp.at(3, base + cnt) = 0.f;
     }
     float mnx = nz ? x : INFINITY, mny = nz ? y : INFINITY, mnz = nz ? z : INFINITY;
     float mxx = nz ? x : -INFINITY, mxy = nz ? y : -INFINITY, mxz = nz ? z : -INFINITY;

@@ -54,3 +54,25 @@ def rel_l2(a, b):
     b = np.asarray(b, np.float64)
     den = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def per_kernel_errors(g, g_o, groups=((0, 3), (3, 6), (6, 9), (9, 10)), rel=1e-3, abs_frac=1e-5, floor=0.0):
+    """Kernel-by-kernel gradient check, one number per parameter group; each
+    must be <= 1.  Kernel j passes when ||g_j - g_o,j|| <= rel * ||g_o,j||
+    + abs_frac * scale, the scale being the group's largest kernel norm (or
+    `floor`, for a group that is all rounding, e.g. the rotation gradient of
+    isotropic kernels).  The absolute term covers the fused adjoint's
+    fixed-point accumulation: each work item's partial is rounded to 2^-36,
+    which leaves an absolute error (about 1e-9 of the largest kernel on the
+    torus field) on kernels at the fringe of the band whose gradient nearly
+    vanishes.  A wrong kernel whose gradient is above abs_frac of the largest
+    cannot hide under a group norm."""
+    g = np.asarray(g, np.float64)
+    g_o = np.asarray(g_o, np.float64)
+    out = []
+    for a, b in groups:
+        num = np.linalg.norm(g[a:b] - g_o[a:b], axis=0)
+        den = np.linalg.norm(g_o[a:b], axis=0)
+        scale = max(den.max(), floor, 1e-300)
+        out.append(float((num / (rel * den + abs_frac * scale)).max()))
+    return out

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import rel_l2, torch_cuda
+from gpu_util import per_kernel_errors, rel_l2, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -110,3 +110,4 @@ def test_c4_gradients_of_256_kernels(c4, orc):
     gk = pb.grad[:, ks].cpu().numpy()
     for sl in (slice(0, 3), slice(3, 6), slice(6, 9), slice(9, 10)):
         assert rel_l2(gk[sl], g_o[sl]) <= GRAD_TOL
+    assert max(per_kernel_errors(gk, g_o)) <= 1.0  # kernel by kernel

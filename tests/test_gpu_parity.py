@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import host_params, oracle_view, problem, rel_l2, torch_cuda
+from gpu_util import host_params, oracle_view, per_kernel_errors, problem, rel_l2, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -240,6 +240,8 @@ def _fused_check(torch, orc, pb):
     for sl in (slice(0, 3), slice(3, 6), slice(6, 9), slice(9, 10)):
         e = np.linalg.norm(g[sl] - g_o[sl]) / max(np.linalg.norm(g_o[sl]), floor, 1e-300)
         assert e <= GRAD_TOL, (sl, e)
+    # and kernel by kernel
+    assert max(per_kernel_errors(g, g_o, floor=floor)) <= 1.0
     assert rel_l2(g, g_sep[:, :m].cpu().numpy()) <= 1e-5
     # a second call gives the same bits (integer accumulation, cleared by the epilogue)
     g1 = pb.grad.clone()
@@ -577,6 +579,7 @@ def test_full_size_c3_sampled(torch, orc):
     gk = pb.grad[:, ks].cpu().numpy()
     for sl in (slice(0, 3), slice(3, 6), slice(6, 9), slice(9, 10)):
         assert rel_l2(gk[sl], g_o[sl]) <= GRAD_TOL
+    assert max(per_kernel_errors(gk, g_o)) <= 1.0
 
 
 def test_graph_captured_epochs_match_eager(torch):
