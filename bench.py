@@ -38,9 +38,10 @@ ADJ_INSTR_PER_PAIR = 32  # minimum FP32-pipe instructions of one adjoint pair (r
 # kernel plus its finishing kernel, from one ncu capture per workload and warp
 # split, valid only for the library version it was taken with (any other
 # version, workload or split reports null)
-_TRAFFIC_030 = {("c4", 1): 170_680_000 + 64_230_000 + 9_930_000, ("c3", 2): 37_330_000 + 116_740 + 2_310_000}
-# 0.3.1 changes only the optimiser step, not the two kernels captured
-TRAFFIC_BYTES = {(v,) + k: b for v in ("serbf 0.3.0 (sm_103a)", "serbf 0.3.1 (sm_103a)") for k, b in _TRAFFIC_030.items()}
+TRAFFIC_BYTES = {
+    ("serbf 0.3.2 (sm_103a)", "c4", 1): 170_590_000 + 63_920_000 + 9_920_000,
+    ("serbf 0.3.2 (sm_103a)", "c3", 2): 37_330_000 + 114_180 + 2_320_000,
+}
 DEFAULT_STEPS = {"c1": 3000, "c2": 3000, "c3": 500, "c4": 200, "c5": 2000}
 WORKLOADS = {
     "c1": ("sphere |x|-0.5 on 32^3, M=64 isotropic", None),
