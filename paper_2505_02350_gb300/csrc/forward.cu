@@ -286,7 +286,7 @@ __device__ __forceinline__ ItemInfo item_info(uint4 r, int lane) {
 template <int G, int ADJ>
 __device__ __forceinline__ void forward_share(const FwdArgs &a, const ItemInfo &it, int w, float *ringP, float *ringF,
                                               int lane, f2 (&acc)[2], uint32_t (&n)[2], uint32_t &cost,
-                                              uint32_t *touch, int &ntouch, float (&tv)[2]) {
+                                              uint32_t *touch, int tcap, int &ntouch, float (&tv)[2]) {
     const unsigned lt = (1u << lane) - 1u;
     // invalid lanes carry NaN so the support test fails for them
     const float qnan = __int_as_float(0x7fc00000);
@@ -357,7 +357,7 @@ __device__ __forceinline__ void forward_share(const FwdArgs &a, const ItemInfo &
             // the kernels that reach the item box, for the adjoint pass
             const unsigned ba = bp | bf;
             const int pos = ntouch + __popc(ba & lt);
-            if ((part || full) && pos < kTouch) touch[pos] = j;
+            if ((part || full) && pos < tcap) touch[pos] = j;
             ntouch += __popc(ba);
         }
         qp += __popc(bp);
@@ -575,10 +575,10 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
 template <int G, bool KAHAN>
 __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &it, int w, const NzPoints &nz,
                                               int nc0, int nc1, float4 lo, float4 hi, const uint32_t *touch,
-                                              int ntouch, uint32_t *q, int lane, uint32_t &cost) {
+                                              int ntouch, int tcap, uint32_t *q, int lane, uint32_t &cost) {
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t *lst = a.slist + (size_t)it.sup * a.scap;
-    const bool listed = ntouch <= kTouch;
+    const bool listed = ntouch <= tcap;
     const int L = listed ? ntouch : min((int)a.scnt[it.sup], a.scap);
     const int b0 = listed ? 0 : 32 * w, stride = listed ? 32 : 32 * G;
     int head = 0, qn = 0, nk = 0;
@@ -714,15 +714,16 @@ struct FwdBatch {
 };
 constexpr int kMaxBatchFields = 1024;
 
-// Item k of the batch: its field (binary search of the offsets in shared
-// memory) and record; w = 0 when none is left.
-__device__ __forceinline__ uint4 resolve_batch(const FwdBatch &b, const uint32_t *off, uint32_t k, uint32_t &field) {
+// Item k of the batch: its field (binary search of the item offsets, read
+// through the read-only cache) and record; w = 0 when none is left.
+__device__ __forceinline__ uint4 resolve_batch(const FwdBatch &b, uint32_t k, uint32_t &field) {
+    const uint32_t *off = b.item_off;
     field = 0;
-    if (k >= off[b.nfields]) return make_uint4(0u, 0u, 0u, 0u);
+    if (k >= __ldg(off + b.nfields)) return make_uint4(0u, 0u, 0u, 0u);
     int lo = 0, hi = b.nfields - 1;  // largest f with off[f] <= k
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (off[mid] <= k) lo = mid; else hi = mid - 1;
+        if (__ldg(off + mid) <= k) lo = mid; else hi = mid - 1;
     }
     field = (uint32_t)lo;
     return b.args[lo].order_rec[k - off[lo]];
@@ -758,32 +759,36 @@ __device__ __forceinline__ void forward_loop(const FwdArgs &a1, const FwdBatch &
     // two rings per warp (kernels partly / fully covering the item box); a
     // ring holds 64 staged kernels (32 pairs), consumed 32 at a time from
     // slot 0 or 32
+    //
+    // Shared memory is kept small: the L1 cache that serves the kernel-record
+    // gathers gets what the blocks leave of the SM's unified 256 KB.  The
+    // rings are idle during the adjoint, so the nz points live in warp 0's
+    // first ring and each warp's adjoint queue in its second.
+    constexpr int GR = G > 1 ? G : 1;    // the cross-warp sums exist only for G > 1
+    constexpr int RL = G > 1 ? 32 : 1;
+    constexpr int kTouchW = G > 1 ? kTouch / 2 : kTouch;  // kernels remembered per warp
     __shared__ __align__(16) float ringP[G][(kQueue / 2) * kPairFloats];
     __shared__ __align__(16) float ringF[G][(kQueue / 2) * kPairFloats];
-    __shared__ float2 red_psi[G][32];
-    __shared__ uint2 red_n[G][32];
+    __shared__ float2 red_psi[GR][RL];
+    __shared__ uint2 red_n[GR][RL];
     __shared__ uint32_t red_cost[G];
     __shared__ uint4 s_rec;
     // fused adjoint: the item's nz points (tile 0 at 0, tile 1 at 32), their
-    // counts and boxes, and a per-warp queue of kernel indices
-    __shared__ __align__(16) NzPoints nzl[1];
+    // counts and boxes, and the kernels each warp found reaching the item
     __shared__ int s_nc[2];
     __shared__ float4 s_box[2][2];
-    __shared__ uint32_t adjq[ADJ ? G : 1][ADJ ? kQueue : 1];
-    __shared__ uint32_t touch[ADJ ? G : 1][ADJ ? kTouch : 1];
-    // batch: the arguments of the current item's field, the item offsets
-    __shared__ __align__(16) FwdArgs s_args[BATCH ? 1 : 1];
-    __shared__ uint32_t s_off[BATCH ? kMaxBatchFields + 1 : 1];
+    __shared__ uint32_t touch[ADJ ? G : 1][ADJ ? kTouchW : 1];
+    // batch: the arguments of the current item's field
+    __shared__ __align__(16) unsigned char s_args[BATCH ? sizeof(FwdArgs) : 16];
     __shared__ uint32_t s_field;
+    static_assert(sizeof(NzPoints) <= sizeof(ringP[0]) && kQueue * 4 <= (int)sizeof(ringF[0]), "ring aliases");
+    NzPoints &nzs = *reinterpret_cast<NzPoints *>(ringP[0]);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (BATCH) {
-        for (int f = threadIdx.x; f <= b.nfields; f += blockDim.x) s_off[f] = b.item_off[f];
-        __syncthreads();
-    }
+    uint32_t *adjq = reinterpret_cast<uint32_t *>(ringF[warp]);
     if (threadIdx.x == 0) {
         if (BATCH) {
             uint32_t f;
-            s_rec = resolve_batch(b, s_off, atomicAdd(b.next, 1u), f);
+            s_rec = resolve_batch(b, atomicAdd(b.next, 1u), f);
             s_field = f;
         } else {
             s_rec = resolve(a1, atomicAdd(a1.item_next, 1u));
@@ -793,7 +798,7 @@ __device__ __forceinline__ void forward_loop(const FwdArgs &a1, const FwdBatch &
     uint4 rec = s_rec;  // the item's record; no points (w = 0) when done
     uint32_t field = BATCH ? s_field : 0u, loaded = ~0u;
     uint32_t mean = BATCH ? 0u : a1.sched[0];
-    const FwdArgs &a = BATCH ? s_args[0] : a1;
+    const FwdArgs &a = BATCH ? *reinterpret_cast<const FwdArgs *>(s_args) : a1;
     while (rec.w != 0u) {
         if (BATCH && field != loaded) {
             // the block's threads copy the field's arguments (block-uniform
@@ -816,10 +821,10 @@ __device__ __forceinline__ void forward_loop(const FwdArgs &a1, const FwdBatch &
         int ntouch = 0;
         float tv[2];
         forward_share<G, ADJ>(a, it, warp, ringP[warp], ringF[warp], lane, acc, n, cost, touch[ADJ ? warp : 0],
-                              ntouch, tv);
+                              kTouchW, ntouch, tv);
         uint4 rn = make_uint4(0u, 0u, 0u, 0u);
-        if (threadIdx.x == 0) rn = BATCH ? resolve_batch(b, s_off, knext, fnext) : resolve(a, knext);
-        if (G == 1) {
+        if (threadIdx.x == 0) rn = BATCH ? resolve_batch(b, knext, fnext) : resolve(a, knext);
+        if constexpr (G == 1) {
             // one warp: finish both tiles directly
             float l0, h0, l1, h1;
             f2_unpack(acc[0], l0, h0);
@@ -835,14 +840,14 @@ __device__ __forceinline__ void forward_loop(const FwdArgs &a1, const FwdBatch &
             }
             if (ADJ) {
                 float4 lo0, hi0, lo1, hi1;
-                const int nc0 = nz_tile(nzl[0], 0, e0 != 0.f, a.x[it.v0 ? it.i0 : 0], a.y[it.v0 ? it.i0 : 0],
+                const int nc0 = nz_tile(nzs, 0, e0 != 0.f, a.x[it.v0 ? it.i0 : 0], a.y[it.v0 ? it.i0 : 0],
                                         a.z[it.v0 ? it.i0 : 0], e0, lane, lo0, hi0);
-                const int nc1 = nz_tile(nzl[0], kTile, e1 != 0.f, a.x[it.v1 ? it.i1 : 0], a.y[it.v1 ? it.i1 : 0],
+                const int nc1 = nz_tile(nzs, kTile, e1 != 0.f, a.x[it.v1 ? it.i1 : 0], a.y[it.v1 ? it.i1 : 0],
                                         a.z[it.v1 ? it.i1 : 0], e1, lane, lo1, hi1);
                 __syncwarp();
                 if (nc0 + nc1 > 0)
-                    adjoint_share<1, (ADJ > 1)>(a, it, 0, nzl[0], nc0, nc1, box_min(lo0, lo1), box_max(hi0, hi1), touch[0],
-                                     ntouch, adjq[0], lane, cost);
+                    adjoint_share<1, (ADJ > 1)>(a, it, 0, nzs, nc0, nc1, box_min(lo0, lo1), box_max(hi0, hi1), touch[0],
+                                                ntouch, kTouchW, adjq, lane, cost);
                 __syncwarp();
             }
             if (lane == 0) note_cost(a, mean, rec, cost);
@@ -852,7 +857,7 @@ __device__ __forceinline__ void forward_loop(const FwdArgs &a1, const FwdBatch &
             rec.w = __shfl_sync(0xffffffffu, rn.w, 0);
             if (BATCH) field = __shfl_sync(0xffffffffu, fnext, 0);
             continue;
-        }
+        } else {
         {
             float l0, h0, l1, h1;
             f2_unpack(acc[0], l0, h0);
@@ -881,7 +886,7 @@ __device__ __forceinline__ void forward_loop(const FwdArgs &a1, const FwdBatch &
             finish_tile(a, it.t0 + warp, l2, mx, cnt, pr, lane);
             if (ADJ) {
                 float4 lo, hi;
-                const int nc = nz_tile(nzl[0], kTile * warp, e != 0.f, a.x[v ? i : 0], a.y[v ? i : 0],
+                const int nc = nz_tile(nzs, kTile * warp, e != 0.f, a.x[v ? i : 0], a.y[v ? i : 0],
                                        a.z[v ? i : 0], e, lane, lo, hi);
                 if (lane == 0) {
                     s_nc[warp] = nc;
@@ -908,7 +913,7 @@ __device__ __forceinline__ void forward_loop(const FwdArgs &a1, const FwdBatch &
                 const float4 lo = nc1 ? (nc0 ? box_min(s_box[0][0], s_box[1][0]) : s_box[1][0]) : s_box[0][0];
                 const float4 hi = nc1 ? (nc0 ? box_max(s_box[0][1], s_box[1][1]) : s_box[1][1]) : s_box[0][1];
                 uint32_t c = 0;
-                adjoint_share<G, (ADJ > 1)>(a, it, warp, nzl[0], nc0, nc1, lo, hi, touch[warp], ntouch, adjq[warp],
+                adjoint_share<G, (ADJ > 1)>(a, it, warp, nzs, nc0, nc1, lo, hi, touch[warp], ntouch, kTouchW, adjq,
                                             lane, c);
                 if (lane == 0) red_cost[warp] += c;
             }
@@ -923,6 +928,7 @@ __device__ __forceinline__ void forward_loop(const FwdArgs &a1, const FwdBatch &
         __syncthreads();
         rec = s_rec;
         if (BATCH) field = s_field;
+        }
     }
     // the last block out prepares the next launch: every block has made its
     // last claim and recorded its costs before it counts itself out
