@@ -39,8 +39,8 @@ ADJ_INSTR_PER_PAIR = 32  # minimum FP32-pipe instructions of one adjoint pair (r
 # split, valid only for the library version it was taken with (any other
 # version, workload or split reports null)
 TRAFFIC_BYTES = {
-    ("serbf 0.3.2 (sm_103a)", "c4", 1): 170_590_000 + 63_920_000 + 9_920_000,
-    ("serbf 0.3.2 (sm_103a)", "c3", 2): 37_330_000 + 114_180 + 2_320_000,
+    ("serbf 0.3.3 (sm_103a)", "c4", 1): 170_620_000 + 63_680_000 + 9_920_000,
+    ("serbf 0.3.3 (sm_103a)", "c3", 2): 37_330_000 + 109_310 + 2_310_000,
 }
 DEFAULT_STEPS = {"c1": 3000, "c2": 3000, "c3": 500, "c4": 200, "c5": 2000}
 WORKLOADS = {
