@@ -38,10 +38,9 @@ ADJ_INSTR_PER_PAIR = 32  # minimum FP32-pipe instructions of one adjoint pair (r
 # kernel plus its finishing kernel, from one ncu capture per workload and warp
 # split, valid only for the library version it was taken with (any other
 # version, workload or split reports null)
-TRAFFIC_BYTES = {
-    ("serbf 0.3.3 (sm_103a)", "c4", 1): 170_620_000 + 63_680_000 + 9_920_000,
-    ("serbf 0.3.3 (sm_103a)", "c3", 2): 37_330_000 + 109_310 + 2_310_000,
-}
+_TRAFFIC_033 = {("c4", 1): 170_620_000 + 63_680_000 + 9_920_000, ("c3", 2): 37_330_000 + 109_310 + 2_310_000}
+# 0.3.4 changes only the Eq. 3-10 target map, not the two kernels captured
+TRAFFIC_BYTES = {(v,) + k: b for v in ("serbf 0.3.3 (sm_103a)", "serbf 0.3.4 (sm_103a)") for k, b in _TRAFFIC_033.items()}
 DEFAULT_STEPS = {"c1": 3000, "c2": 3000, "c3": 500, "c4": 200, "c5": 2000}
 WORKLOADS = {
     "c1": ("sphere |x|-0.5 on 32^3, M=64 isotropic", None),

@@ -197,9 +197,13 @@ int serbf_state_init(serbf_state *st_dev, const serbf_config *cfg, void *stream)
 
 /* ------------------------------------------------------------------ a1 */
 /* Eq. 3-10 (Sec. 3.3): t_i = 2 exp(-h (S_i - m)^2), m = min_i S_i,
- * h = ln 2 / m^2, evaluated in double and rounded to float.  mh_dev[0] = m,
- * mh_dev[1] = h.  Requires m != 0 (EINVAL is not detectable on the host; a
- * zero minimum yields non-finite t). */
+ * h = ln 2 / m^2.  Evaluated as 2^(1 - u^2), u = (S_i - m) / m, in float-float
+ * arithmetic (no FP64 in the per-sample work): each t_i is the float nearest
+ * the exact value, or, where that value lies within about 2^-40 (2^-45 for
+ * t_i > 1e-3) of a rounding boundary, its neighbour; targets below the
+ * smallest float are 0.  mh_dev[0] = m, mh_dev[1] = h (double).  Requires
+ * m != 0 (not detectable on the host; a zero minimum yields NaN at the
+ * minimum and 0 elsewhere). */
 int serbf_normalize_sdf(const float *S, float *t, int64_t n, double *mh_dev, serbf_workspace *ws,
                         void *stream);
 

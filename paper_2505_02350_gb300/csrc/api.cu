@@ -181,10 +181,12 @@ __global__ void k_normalize(const float *S, float *t, int64_t n, const int *slot
         mh[0] = m;
         mh[1] = h;
     }
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double s = (double)S[i] - m;
-        t[i] = (float)(2.0 * exp(-h * s * s));
-    }
+    __shared__ ff c[kEq310Terms];
+    if (threadIdx.x == 0) eq310_coefs(c);
+    __syncthreads();
+    const float mf = ordered_val(*slot);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        t[i] = eq310_target(S[i], mf, c);
 }
 
 __global__ void k_state_init(serbf_state *st, double lr) {
@@ -220,7 +222,7 @@ int launch_exscan_i64(int64_t *a, int64_t n, cudaStream_t s) {
 
 extern "C" {
 
-const char *serbf_version(void) { return "serbf 0.3.3 (sm_103a)"; }
+const char *serbf_version(void) { return "serbf 0.3.4 (sm_103a)"; }
 
 const char *serbf_status_string(int code) {
     switch (code) {

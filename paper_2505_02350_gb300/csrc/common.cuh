@@ -250,6 +250,73 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
 
 __device__ __forceinline__ ff ff_add(ff a, float b) { return ff_add(a, ff{b, 0.f}); }
 
+// a * b exactly, as a float-float pair (the fused multiply-add gives the
+// rounding error of the product).
+__device__ __forceinline__ ff two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const ff p = two_prod(a.hi, b.hi);
+    const float lo = __fadd_rn(p.lo, __fadd_rn(__fmul_rn(a.hi, b.lo), __fmul_rn(a.lo, b.hi)));
+    const float hi = __fadd_rn(p.hi, lo);
+    return {hi, __fsub_rn(lo, __fsub_rn(hi, p.hi))};
+}
+
+// a / b for a float-float a: the float quotient, then one correction from
+// the exact remainder.
+__device__ __forceinline__ ff ff_div(ff a, float b) {
+    const float q1 = __fdiv_rn(a.hi, b);
+    const ff p = two_prod(q1, b);
+    const ff r = ff_add(a, ff{-p.hi, -p.lo});
+    const float q2 = __fdiv_rn(r.hi, b);
+    const float hi = __fadd_rn(q1, q2);
+    return {hi, __fsub_rn(q2, __fsub_rn(hi, q1))};
+}
+
+// Eq. 3-10 without FP64 (this part's FP64 rate is a small fraction of its
+// FP32 rate).  t = 2 exp(-h (S - m)^2) with h = ln 2 / m^2 is 2^(1 - u^2),
+// u = (S - m) / m.  The exponent z = 1 - u^2 is formed in float-float (exact
+// difference, then a quotient and a square to about 2^-46), split as
+// z = n + f with n an integer and |f| <= 1/2, and 2^f = exp(f ln 2) is summed
+// as its Taylor series to degree 11 in float-float (the first omitted term is
+// below 1e-14).  The result is the float nearest the exact value except where
+// that value lies within about 2^-40 of a rounding boundary (then one of the
+// two neighbours).  c[k] = (ln 2)^k / k! as float-float, from eq310_coefs.
+constexpr int kEq310Terms = 12;
+__device__ __forceinline__ void eq310_coefs(ff *c) {
+    double t = 1.0;
+    for (int k = 0; k < kEq310Terms; ++k) {
+        const float hi = (float)t;
+        c[k] = ff{hi, (float)(t - (double)hi)};
+        t = t * 0.6931471805599453094172321 / (double)(k + 1);
+    }
+}
+__device__ __forceinline__ float eq310_target(float S, float m, const ff *c) {
+    const ff s = two_sum(S, -m);  // S - m, exactly
+    const ff u = ff_div(s, m);
+    const ff u2 = ff_mul(u, u);
+    const ff z = ff_add(ff{1.f, 0.f}, ff{-u2.hi, -u2.lo});
+    if (z.hi != z.hi) return z.hi;  // NaN in, NaN out (m = 0 and S = 0)
+    if (z.hi < -160.f) return 0.f;  // below the smallest float
+    const float n = rintf(z.hi);
+    const ff f = ff_add(z, -n);
+    ff p = c[kEq310Terms - 1];
+#pragma unroll
+    for (int k = kEq310Terms - 2; k >= 0; --k) p = ff_add(ff_mul(p, f), c[k]);
+    if (n > -126.f) return ldexpf(__fadd_rn(p.hi, p.lo), (int)n);  // normal: one rounding, exact scaling
+    // below 2^-125 the floats are the multiples of 2^-149: round p 2^n onto
+    // that grid directly (rounding p first and scaling after would round twice)
+    const float sc = ldexpf(1.f, (int)n + 149);  // 2^-11 .. 2^23, exact
+    const float q = __fmul_rn(p.hi, sc), r = __fmul_rn(p.lo, sc);
+    float k = rintf(q);
+    const float d = __fsub_rn(q, k);  // exact; |r| is below half a unit of q
+    if (d == 0.5f && r > 0.f) k = __fadd_rn(k, 1.f);
+    if (d == -0.5f && r < 0.f) k = __fsub_rn(k, 1.f);
+    return __fmul_rn(k, 1.40129846432481707e-45f);  // k 2^-149, exact
+}
+
 __device__ __forceinline__ ff warp_sum_ff(ff v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

@@ -93,14 +93,15 @@ __global__ void __launch_bounds__(256) k_na_finish(const int *partial, int nbloc
     }
 }
 
-// Eq. 3-10 per element, in double, rounded to float (same arithmetic as the
-// workspace version, so both give identical targets).
+// Eq. 3-10 per element with the workspace version's arithmetic
+// (eq310_target), so both give identical targets.
 __global__ void k_na_apply(const float *S, float *t, int64_t n, const double *mh) {
-    const double m = mh[0], h = mh[1];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double s = (double)S[i] - m;
-        t[i] = (float)(2.0 * exp(-h * s * s));
-    }
+    __shared__ ff c[kEq310Terms];
+    if (threadIdx.x == 0) eq310_coefs(c);
+    __syncthreads();
+    const float m = (float)mh[0];  // the minimum sample, exactly
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        t[i] = eq310_target(S[i], m, c);
 }
 
 }  // namespace

@@ -54,6 +54,40 @@ def test_normalize_matches_oracle(torch, orc):
     np.testing.assert_allclose(t.cpu().numpy(), t_or.astype(np.float32), rtol=2 ** -23, atol=0)
 
 
+def test_normalize_wide_range_within_one_ulp(torch, orc):
+    """Eq. 3-10 on the GPU (float-float exponent, float-float series for
+    2^f) against the FP64 oracle over samples spread from the minimum out to
+    where the target underflows: at most one unit in the last place anywhere.
+    A neighbour instead of the nearest float needs the exact value within the
+    computation's error of a rounding boundary: about 2^-45 relative where
+    the targets matter (t > 1e-3, the Eq. 3-18 band lies at 0.9-1.1), so
+    almost never; about 2^-39 far out, where u^2 ~ 100 scales the error of
+    the exponent and the targets are ~2^-100."""
+    from paper_2505_02350_gb300 import _native as N
+    g = np.random.default_rng(11)
+    n = 1 << 21
+    parts = [g.uniform(-0.35, 1.2, n // 2),                 # a band and its surroundings
+             -0.35 + g.exponential(1e-3, n // 4),          # close to the minimum
+             g.uniform(-0.35, 12.0, n // 4)]               # far field, down to underflow
+    S = np.concatenate(parts).astype(np.float32)
+    St = torch.as_tensor(S, device="cuda")
+    t = torch.zeros_like(St)
+    mh = torch.zeros(2, dtype=torch.float64, device="cuda")
+    pb = problem("c1")
+    N.serbf_normalize_sdf(St, t, mh, pb.ws)
+    t_or, m, h = orc.normalize(S)
+    ref = t_or.astype(np.float32)
+    got = t.cpu().numpy()
+    assert np.all(np.isfinite(got)) and np.all(got >= 0)
+    ulps = np.abs(got.view(np.int32).astype(np.int64) - ref.view(np.int32).astype(np.int64))
+    assert ulps.max() <= 1
+    near = ref > 1e-3
+    assert np.count_nonzero(near) > n // 2
+    assert np.count_nonzero(ulps[near]) <= 5
+    assert np.count_nonzero(ulps) <= 1e-4 * n
+    assert np.count_nonzero(got == 0) > 0 and np.count_nonzero(got == 2.0) >= 1  # underflow and the minimum
+
+
 @pytest.mark.parametrize("which", ["c1", "c2"])
 def test_binning_bitexact(torch, orc, which, c1, c2):
     pb = c1 if which == "c1" else c2
