@@ -253,23 +253,44 @@ def run_native(args, ws, rank, local):
     # (serbf_normalize_sdf), serbf_gather puts targets and samples in binned
     # order, the epoch runs, and the whole parameter block (10 x capacity
     # floats), the kernel count and the loss terms come back device -> host
-    # into pinned rings.  Copies, state restore and the epoch are ordered on
-    # one stream, so the host need not wait between steps; it reads the
-    # rings once the last step is done.
+    # into pinned rings.  The samples of step k + 1 travel on a copy stream
+    # into the second of two device buffers while step k computes; the
+    # state restore, the map, the gathers, the epoch and the result copies
+    # are ordered on the main stream, so the host need not wait between
+    # steps; it reads the rings once the last step is done.
     from paper_2505_02350_gb300 import _native as N
     n = pb.n
     host_S = pb.s_all[:n].cpu().pin_memory()
     host_p = torch.zeros(K, *pb.p.shape, dtype=torch.float32).pin_memory()
     host_m = torch.zeros(K, 1, dtype=torch.int32).pin_memory()
     host_stats = torch.zeros(K, 16, dtype=torch.float64).pin_memory()
+    stage = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(2)]
+    copy_stream = torch.cuda.Stream(dev)
+    main_stream = torch.cuda.current_stream(dev)
+    ready = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
+
+    def send(k):
+        b = k % 2
+        with torch.cuda.stream(copy_stream):
+            if k >= 2:
+                copy_stream.wait_event(free[b])  # step k - 2 has read this buffer
+            stage[b].copy_(host_S, non_blocking=True)
+            ready[b].record(copy_stream)
+
     torch.cuda.synchronize()
     te = time.perf_counter()
+    send(0)
     for k in range(K):
+        b = k % 2
+        if k + 1 < K:
+            send(k + 1)
         pb.restore(snap)
-        pb.s_all[:n].copy_(host_S, non_blocking=True)
-        N.serbf_normalize_sdf(pb.s_all[:n], pb.t_all[:n], pb.mh, pb.ws)
+        main_stream.wait_event(ready[b])
+        N.serbf_normalize_sdf(stage[b], pb.t_all[:n], pb.mh, pb.ws)
         N.serbf_gather(pb.t_all, pb.perm[:n], pb.tb, n)
-        N.serbf_gather(pb.s_all, pb.perm[:n], pb.sb, n)
+        N.serbf_gather(stage[b], pb.perm[:n], pb.sb, n)
+        free[b].record(main_stream)
         pb.epoch_graph()
         host_p[k].copy_(pb.p, non_blocking=True)
         host_m[k].copy_(pb.m_dev, non_blocking=True)
@@ -301,9 +322,9 @@ def run_native(args, ws, rank, local):
                    "timing": "K one-graph steps (value) interleaved with K steps split at the forward (roofline)",
                    "state": "the fit's state after the warm-up, restored before every step (untimed)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_h2d, "d2h_bytes_per_step": e2e_d2h,
-                "basis": "per step: raw SDF samples host->device, Eq. 3-10 and binned-order gathers on the device, "
-                         "the epoch, then the 10 x %d parameter block, kernel count and loss terms device->host"
-                         % pb.cap},
+                "basis": "per step: raw SDF samples host->device (the next step's copy overlaps this step's "
+                         "epoch), Eq. 3-10 and binned-order gathers on the device, the epoch, then the 10 x %d "
+                         "parameter block, kernel count and loss terms device->host" % pb.cap},
         "gpu_launches": 2 * pb.launches_per_epoch() * K,
         "gpu_launches_basis": "%d kernels per step; %d one-graph steps and %d split steps in the timed loop"
                               % (pb.launches_per_epoch(), K, K),
