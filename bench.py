@@ -278,6 +278,26 @@ def run_native(args, ws, rank, local):
             stage[b].copy_(host_S, non_blocking=True)
             ready[b].record(copy_stream)
 
+    # per buffer, one graph of a step's device work: state restore, Eq. 3-10,
+    # the two gathers and the epoch
+    def device_step(b):
+        pb.restore(snap)
+        N.serbf_normalize_sdf(stage[b], pb.t_all[:n], pb.mh, pb.ws)
+        N.serbf_gather(pb.t_all, pb.perm[:n], pb.tb, n)
+        N.serbf_gather(stage[b], pb.perm[:n], pb.sb, n)
+        pb.epoch()
+
+    for b in range(2):
+        stage[b].copy_(pb.s_all[:n])
+        device_step(b)  # warm-up outside capture
+    torch.cuda.synchronize()
+    step_graphs = []
+    for b in range(2):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            device_step(b)
+        step_graphs.append(g)
+    pb.restore(snap)
     torch.cuda.synchronize()
     te = time.perf_counter()
     send(0)
@@ -285,13 +305,9 @@ def run_native(args, ws, rank, local):
         b = k % 2
         if k + 1 < K:
             send(k + 1)
-        pb.restore(snap)
         main_stream.wait_event(ready[b])
-        N.serbf_normalize_sdf(stage[b], pb.t_all[:n], pb.mh, pb.ws)
-        N.serbf_gather(pb.t_all, pb.perm[:n], pb.tb, n)
-        N.serbf_gather(stage[b], pb.perm[:n], pb.sb, n)
+        step_graphs[b].replay()
         free[b].record(main_stream)
-        pb.epoch_graph()
         host_p[k].copy_(pb.p, non_blocking=True)
         host_m[k].copy_(pb.m_dev, non_blocking=True)
         host_stats[k].copy_(pb.stats, non_blocking=True)
@@ -323,8 +339,8 @@ def run_native(args, ws, rank, local):
                    "state": "the fit's state after the warm-up, restored before every step (untimed)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_h2d, "d2h_bytes_per_step": e2e_d2h,
                 "basis": "per step: raw SDF samples host->device (the next step's copy overlaps this step's "
-                         "epoch), Eq. 3-10 and binned-order gathers on the device, the epoch, then the 10 x %d "
-                         "parameter block, kernel count and loss terms device->host" % pb.cap},
+                         "epoch), then one graph of Eq. 3-10, the binned-order gathers and the epoch, then the 10 x "
+                         "%d parameter block, kernel count and loss terms device->host" % pb.cap},
         "gpu_launches": 2 * pb.launches_per_epoch() * K,
         "gpu_launches_basis": "%d kernels per step; %d one-graph steps and %d split steps in the timed loop"
                               % (pb.launches_per_epoch(), K, K),
