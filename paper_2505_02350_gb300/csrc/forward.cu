@@ -51,7 +51,7 @@ struct FwdArgs {
     int32_t *status;      // device status flags
 };
 
-constexpr int kTouch = 256;  // kernels remembered per warp and item for the adjoint (more: re-scan the list)
+constexpr int kTouch = 256;  // kernels an item's warps remember for its adjoint (more: re-scan the list)
 constexpr int kNz = 2 * kTile;
 
 // Two float32 lanes in one 64-bit register: the packed f32x2 arithmetic of
@@ -570,7 +570,7 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
 }
 
 // One warp's share of an item's adjoint: the kernels this warp found
-// reaching the item box (or, if it found more than kTouch, its candidate
+// reaching the item box (or, if it found more than tcap, its candidate
 // chunks of the super cell's list again), filtered against the nz box.
 template <int G, bool KAHAN>
 __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &it, int w, const NzPoints &nz,
