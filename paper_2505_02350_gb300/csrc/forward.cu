@@ -466,7 +466,7 @@ __device__ __forceinline__ void f2_kadd(f2 &s, f2 &c, f2 v) {
 // not leave most lanes idle.  KAHAN: compensated per-lane sums.
 template <bool KAHAN>
 __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *q, int head, int cnt,
-                                              const NzPoints &nz, int nc0, int nc1, int lane, uint32_t &pairs) {
+                                              const NzPoints &nz, int nc0, int nc1, int lane) {
     const int sh = cnt > 16 ? 0 : (cnt > 8 ? 1 : (cnt > 4 ? 2 : 3));
     const int L = 1 << sh, kl = lane >> sh, sub = lane & (L - 1);
     const bool act = kl < cnt;  // whole groups of L lanes are inactive together
@@ -480,7 +480,6 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
     for (int r = 0; r < 10; ++r) acc[r] = 0ull;
 #pragma unroll
     for (int r = 0; r < (KAHAN ? 10 : 1); ++r) cmp[r] = 0ull;
-    uint32_t np = 0;
 #pragma unroll 1
     for (int seg = 0; seg < 2; ++seg) {
         const int base = seg ? kTile : 0, cntp = act ? ((seg ? nc1 : nc0) + 1) >> 1 : 0;
@@ -496,9 +495,8 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
             const f2 ra = f2_fma(q13, dz, f2_fma(q12, dy, f2_mul(q11, dx)));
             const f2 rb = f2_fma(q23, dz, f2_mul(q22, dy));
             const f2 qv = f2_fma(q33, zz, f2_fma(dy, rb, f2_mul(dx, ra)));
-            float q0, q1, pe0, pe1;
+            float q0, q1;
             f2_unpack(qv, q0, q1);
-            f2_unpack(pe, pe0, pe1);
             float e0 = ex2_approx(-q0), e1 = ex2_approx(-q1);
             // Eq. 3-15-1, the operations of support_d2, packed
             const f2 d2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_mul(dx, dx)));
@@ -507,7 +505,6 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
             const bool i0 = d0 < k0.w, i1 = d1 < k0.w;
             e0 = i0 ? e0 : 0.f;
             e1 = i1 ? e1 : 0.f;
-            np += (uint32_t)(i0 && pe0 != 0.f) + (uint32_t)(i1 && pe1 != 0.f);  // pads have E = 0
             const f2 sv = f2_mul(f2_pack(e0, e1), pe);
             const f2 sx = f2_mul(sv, dx), sy = f2_mul(sv, dy), sz = f2_mul(sv, dz);
             if (KAHAN) {
@@ -566,7 +563,6 @@ __device__ __forceinline__ void adjoint_batch(const FwdArgs &a, const uint32_t *
         for (int r = 0; r < 10; ++r)
             if (v[r] != 0.f) atomicAdd(o + r, (unsigned long long)to_fix36(v[r]));
     }
-    pairs += np;
 }
 
 // One warp's share of an item's adjoint: the kernels this warp found
@@ -582,7 +578,6 @@ __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &
     const int L = listed ? ntouch : min((int)a.scnt[it.sup], a.scap);
     const int b0 = listed ? 0 : 32 * w, stride = listed ? 32 : 32 * G;
     int head = 0, qn = 0, nk = 0;
-    uint32_t pairs = 0;
     for (int b = b0; b < L; b += stride) {
         const bool live = b + lane < L;
         const uint32_t j = live ? (listed ? touch[b + lane] : lst[b + lane]) : 0u;
@@ -597,16 +592,14 @@ __device__ __forceinline__ void adjoint_share(const FwdArgs &a, const ItemInfo &
         nk += __popc(bal);
         __syncwarp();
         if (qn >= 32) {
-            adjoint_batch<KAHAN>(a, q, head, 32, nz, nc0, nc1, lane, pairs);
+            adjoint_batch<KAHAN>(a, q, head, 32, nz, nc0, nc1, lane);
             head = (head + 32) & (kQueue - 1);
             qn -= 32;
             __syncwarp();
         }
     }
-    if (qn > 0) adjoint_batch<KAHAN>(a, q, head, qn, nz, nc0, nc1, lane, pairs);
+    if (qn > 0) adjoint_batch<KAHAN>(a, q, head, qn, nz, nc0, nc1, lane);
     __syncwarp();
-    const uint32_t tot = redux_add(pairs);
-    if (lane == 0 && tot) atomicAdd(a.adj_pairs, (unsigned long long)tot);
     cost += (uint32_t)(nk * (nc0 + nc1)) / 4u + 32u;
 }
 
@@ -839,6 +832,10 @@ __device__ __forceinline__ void forward_loop(const FwdArgs &a1, const FwdBatch &
                 finish_tile(a, it.t0 + 1, l2, mx, cnt, pr, lane);
             }
             if (ADJ) {
+                // adjoint pairs: every support pair of a point with E != 0
+                // (the adjoint takes exactly these)
+                const uint32_t pb = redux_add((e0 != 0.f ? n[0] : 0u) + (e1 != 0.f ? n[1] : 0u));
+                if (lane == 0 && pb) atomicAdd(a.adj_pairs, (unsigned long long)pb);
                 float4 lo0, hi0, lo1, hi1;
                 const int nc0 = nz_tile(nzs, 0, e0 != 0.f, a.x[it.v0 ? it.i0 : 0], a.y[it.v0 ? it.i0 : 0],
                                         a.z[it.v0 ? it.i0 : 0], e0, lane, lo0, hi0);
@@ -885,6 +882,9 @@ __device__ __forceinline__ void forward_loop(const FwdArgs &a1, const FwdBatch &
             const float e = point_out(a, i, v, warp ? tv[1] : tv[0], ps, np, l2, mx, cnt, pr);
             finish_tile(a, it.t0 + warp, l2, mx, cnt, pr, lane);
             if (ADJ) {
+                // adjoint pairs: every support pair of a point with E != 0
+                const uint32_t pb = redux_add(e != 0.f ? np : 0u);
+                if (lane == 0 && pb) atomicAdd(a.adj_pairs, (unsigned long long)pb);
                 float4 lo, hi;
                 const int nc = nz_tile(nzs, kTile * warp, e != 0.f, a.x[v ? i : 0], a.y[v ? i : 0],
                                        a.z[v ? i : 0], e, lane, lo, hi);
