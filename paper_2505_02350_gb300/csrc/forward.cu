@@ -429,24 +429,13 @@ struct NzPoints {
 
 __device__ __forceinline__ f2 f2_dup(float v) { return f2_pack(v, v); }
 
-// v * 2^36 rounded to the nearest integer (halves away from zero), with
-// integer operations only (a float to 64-bit integer conversion would use
-// the slow double-precision unit).  |v| >= 2^26 saturates at 2^62 (the
-// caller flags such a partial before converting it).
+// v * 2^36 rounded to the nearest integer (ties to even): the scaling by a
+// power of two is exact in float, and one hardware conversion rounds (it was
+// 9 % faster on the 256^3 field than an integer-only rounding).  |v| >= 2^26
+// does not fit the accumulators' range; the caller flags such a partial
+// before converting it.
 __device__ __forceinline__ long long to_fix36(float v) {
-    const uint32_t b = __float_as_uint(v);
-    const int e = (int)((b >> 23) & 0xffu);  // biased exponent; 0: zero or below 2^-126
-    if (e == 0) return 0;
-    const long long m = (long long)((b & 0x7fffffu) | 0x800000u);  // v = m 2^(e - 150)
-    const int sh = e - 150 + 36;
-    long long r;
-    if (sh >= 0)
-        r = sh >= 39 ? (1ll << 62) : (m << sh);
-    else if (sh > -25)
-        r = (m + (1ll << (-sh - 1))) >> (-sh);
-    else
-        r = 0;
-    return (b >> 31) ? -r : r;
+    return __float2ll_rn(__fmul_rn(v, 68719476736.f));
 }
 
 // Compensated (Kahan) accumulation of packed pairs: s + v with the lost
@@ -1053,8 +1042,8 @@ __device__ __forceinline__ void fwd_finish_body(const FinishArgs &f, int bx, int
             float M[10];
 #pragma unroll
             for (int r = 0; r < 10; ++r) {
-                // int64 -> float through two 32-bit conversions (the 64-bit
-                // one runs on the slow double-precision unit); relative error ~1e-7
+                // int64 -> float from its two 32-bit halves and one FMA;
+                // relative error ~1e-7
                 const long long v = (long long)o[r];
                 const float hi = (float)(int)(v >> 32), lo = (float)(uint32_t)(v & 0xffffffffll);
                 M[r] = fmaf(hi, 4294967296.f, lo) * kFixUnitF;
