@@ -35,12 +35,13 @@ UNIT = "pairs/s"
 FWD_INSTR_PER_PAIR = 17  # minimum FP32-pipe instructions of one forward pair
 ADJ_INSTR_PER_PAIR = 32  # minimum FP32-pipe instructions of one adjoint pair (recompute + ten moments)
 # DRAM bytes (read + write) of one launch of the fused forward + adjoint
-# kernel plus its finishing kernel, from one ncu capture per workload and warp
-# split, valid only for the library version it was taken with (any other
-# version, workload or split reports null)
-_TRAFFIC_033 = {("c4", 1): 170_620_000 + 63_680_000 + 9_920_000, ("c3", 2): 37_330_000 + 109_310 + 2_310_000}
-# 0.3.4 changes only the Eq. 3-10 target map, not the two kernels captured
-TRAFFIC_BYTES = {(v,) + k: b for v in ("serbf 0.3.3 (sm_103a)", "serbf 0.3.4 (sm_103a)") for k, b in _TRAFFIC_033.items()}
+# kernel plus its finishing kernel, from one ncu capture per workload, warp
+# split and super-cell size, valid only for the library version it was taken
+# with (any other version, workload, split or size reports null)
+TRAFFIC_BYTES = {
+    ("serbf 0.3.6 (sm_103a)", "c4", 1, 4): 170_680_000 + 64_060_000 + 9_920_000,
+    ("serbf 0.3.6 (sm_103a)", "c3", 2, 2): 39_480_000 + 258_560 + 2_310_000,
+}
 DEFAULT_STEPS = {"c1": 3000, "c2": 3000, "c3": 500, "c4": 200, "c5": 2000}
 WORKLOADS = {
     "c1": ("sphere |x|-0.5 on 32^3, M=64 isotropic", None),
@@ -141,7 +142,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(inside), "samples_in_window": inside is not rows}
 
 
-SUPER_FACTOR = {"c1": 4, "c2": 4, "c3": 4, "c4": 4}
+# cells per super-cell edge (the candidate lists' granularity): measured per
+# workload, 2 on the 128^3 field (epoch 3 % shorter than with 4: the shorter
+# lists save more in the forward than the finer rebuild costs), 4 elsewhere
+# (on the 256^3 band, 2 makes the rebuild 5x dearer)
+SUPER_FACTOR = {"c1": 4, "c2": 4, "c3": 2, "c4": 4}
 
 
 def build_problem(name, device, sf=None):
@@ -346,7 +351,7 @@ def run_native(args, ws, rank, local):
                               % (pb.launches_per_epoch(), K, K),
         "roofline": {"bound": "alu", "kernel": "k_forward<G, adjoint> + k_fwd_finish<adjoint>", "achieved": achieved / 1e12,
                      "peak": peak_instr / 1e12, "unit": "T FP32-instr/s", "frac": achieved / peak_instr,
-                     "traffic": TRAFFIC_BYTES.get((N.version(), args.config, pb.cfg.fwd_warps)),
+                     "traffic": TRAFFIC_BYTES.get((N.version(), args.config, pb.cfg.fwd_warps, pb.sizes.super_factor)),
                      "instr_per_pair": {"forward": FWD_INSTR_PER_PAIR, "adjoint": ADJ_INSTR_PER_PAIR},
                      "peak_basis": "%d SMs x 128 FP32 lanes x %.0f MHz (of measured max clock)" % (nsm, sm_mhz),
                      "timing": "CUDA events around the forward graph of the interleaved split steps"},

@@ -584,12 +584,20 @@ def test_tiny_ragged_problem(torch, orc):
     _backward_check(torch, orc, pb)
 
 
-def test_full_size_c3_sampled(torch, orc):
-    """128^3, 4096 kernels, launch as in the bench: sampled outputs vs the oracle."""
-    pb = problem("c3")
+@pytest.mark.parametrize("sf", [4, 2])
+def test_full_size_c3_sampled(torch, orc, sf):
+    """128^3, 4096 kernels, sampled outputs vs the oracle: the separate
+    forward and adjoint with 4 x 4 x 4-cell super cells, and the fused pass
+    with two warps per item and 2 x 2 x 2-cell super cells as the bench
+    launches it."""
+    pb = problem("c3", super_factor=sf)
     pb.build_neighbors()
-    pb.forward()
-    pb.backward()
+    if sf == 4:
+        pb.forward()
+        pb.backward()
+    else:
+        pb.cfg.fwd_warps = 2
+        pb.forward_backward()
     torch.cuda.synchronize()
     assert pb.status()[0] == 0
     h, P = _oracle_inputs(pb)
