@@ -38,10 +38,14 @@ ADJ_INSTR_PER_PAIR = 32  # minimum FP32-pipe instructions of one adjoint pair (r
 # kernel plus its finishing kernel, from one ncu capture per workload, warp
 # split and super-cell size, valid only for the library version it was taken
 # with (any other version, workload, split or size reports null)
-TRAFFIC_BYTES = {
-    ("serbf 0.3.6 (sm_103a)", "c4", 1, 4): 170_680_000 + 64_060_000 + 9_920_000,
-    ("serbf 0.3.6 (sm_103a)", "c3", 2, 2): 39_480_000 + 258_560 + 2_310_000,
+_TRAFFIC_036 = {
+    ("c4", 1, 4): 170_680_000 + 64_060_000 + 9_920_000,
+    ("c3", 2, 2): 39_480_000 + 258_560 + 2_310_000,
 }
+# 0.3.7 changes only the neighbour rebuild (a third list level), not the two
+# kernels captured
+TRAFFIC_BYTES = {(v,) + k: b for v in ("serbf 0.3.6 (sm_103a)", "serbf 0.3.7 (sm_103a)") for k, b in _TRAFFIC_036.items()}
+TRAFFIC_BYTES[("serbf 0.3.7 (sm_103a)", "c4", 1, 2)] = 187_060_000 + 64_840_000 + 9_990_000
 DEFAULT_STEPS = {"c1": 3000, "c2": 3000, "c3": 500, "c4": 200, "c5": 2000}
 WORKLOADS = {
     "c1": ("sphere |x|-0.5 on 32^3, M=64 isotropic", None),
@@ -143,10 +147,11 @@ class ClockSampler:
 
 
 # cells per super-cell edge (the candidate lists' granularity): measured per
-# workload, 2 on the 128^3 field (epoch 3 % shorter than with 4: the shorter
-# lists save more in the forward than the finer rebuild costs), 4 elsewhere
-# (on the 256^3 band, 2 makes the rebuild 5x dearer)
-SUPER_FACTOR = {"c1": 4, "c2": 4, "c3": 2, "c4": 4}
+# workload, 2 on the 128^3 field (epoch 3 % shorter than with 4) and on the
+# 256^3 band (7 % shorter, with the three-level rebuild the library picks
+# there): the shorter lists save more in the forward than the finer rebuild
+# costs; 4 on the small torus
+SUPER_FACTOR = {"c1": 4, "c2": 4, "c3": 2, "c4": 2}
 
 
 def build_problem(name, device, sf=None):

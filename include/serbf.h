@@ -99,8 +99,11 @@ typedef struct {
     int32_t rebuild_levels; /* how serbf_build_neighbors forms the candidate list of each super
                                cell: 1 = tests every kernel; 2 = lists the kernels of each block of
                                2 x 2 x 2 super cells first and filters that list (the same lists,
-                               less work when there are many super cells and kernels); 0 = chosen
-                               from the problem size (default) */
+                               less work when there are many super cells and kernels); 3 = lists
+                               blocks of 4 x 4 x 4 super cells first, filters them into the blocks
+                               of 2 x 2 x 2 and those into the super cells (the same lists again;
+                               the batched epoch takes 2 for 3); 0 = chosen from the problem size
+                               (default) */
 } serbf_config;
 
 /* Optimiser state of Algorithm 3; lives in DEVICE memory (sizeof bytes). */

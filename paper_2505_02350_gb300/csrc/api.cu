@@ -222,7 +222,7 @@ int launch_exscan_i64(int64_t *a, int64_t n, cudaStream_t s) {
 
 extern "C" {
 
-const char *serbf_version(void) { return "serbf 0.3.6 (sm_103a)"; }
+const char *serbf_version(void) { return "serbf 0.3.7 (sm_103a)"; }
 
 const char *serbf_status_string(int code) {
     switch (code) {

@@ -194,13 +194,14 @@ __global__ void __launch_bounds__(256) k_rebuild(const float *p, int cap, const 
 }
 
 // Two-level rebuild, for many super cells and kernels.  First launch: blocks
-// [0, ncoarse) list, per block of 2 x 2 x 2 super cells, every kernel whose
-// support may reach the union of their boxes (as k_rebuild does per super
-// cell); the remaining blocks write the per-kernel records.
+// [0, ncoarse) list, per block of f x f x f super cells (f = 2; 4 for the
+// first of three levels), every kernel whose support may reach the union of
+// their boxes (as k_rebuild does per super cell); the remaining blocks write
+// the per-kernel records.
 __device__ __forceinline__ void coarse_lists_body(const float *p, int cap, const int32_t *m_dev, float nle,
                                                   float4 *kfwd, float4 *kbwd, const float4 *slo, const float4 *shi,
                                                   int nsx, int nsy, int nsz, int ncoarse, uint32_t *list,
-                                                  uint32_t *cnt, int scap, int bx, int nbx) {
+                                                  uint32_t *cnt, int scap, int bx, int nbx, int f) {
     __shared__ uint32_t tmp[33];
     __shared__ float4 s_lo, s_hi;
     const int m = *m_dev;
@@ -211,13 +212,13 @@ __device__ __forceinline__ void coarse_lists_body(const float *p, int cap, const
         return;
     }
     if (threadIdx.x == 0) {
-        const int ncx = (nsx + 1) >> 1, ncy = (nsy + 1) >> 1;
+        const int ncx = (nsx + f - 1) / f, ncy = (nsy + f - 1) / f;
         const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
         float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f), hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
-        for (int dz = 0; dz < 2; ++dz)
-            for (int dy = 0; dy < 2; ++dy)
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int sx = 2 * cx + dx, sy = 2 * cy + dy, sz = 2 * cz + dz;
+        for (int dz = 0; dz < f; ++dz)
+            for (int dy = 0; dy < f; ++dy)
+                for (int dx = 0; dx < f; ++dx) {
+                    const int sx = f * cx + dx, sy = f * cy + dy, sz = f * cz + dz;
                     if (sx >= nsx || sy >= nsy || sz >= nsz) continue;
                     const int sc = (sz * nsy + sy) * nsx + sx;
                     const float4 a = slo[sc], b = shi[sc];
@@ -253,11 +254,81 @@ __device__ __forceinline__ void coarse_lists_body(const float *p, int cap, const
 __global__ void __launch_bounds__(256) k_coarse_lists(const float *p, int cap, const int32_t *m_dev, float nle,
                                                       float4 *kfwd, float4 *kbwd, const float4 *slo,
                                                       const float4 *shi, int nsx, int nsy, int nsz, int ncoarse,
-                                                      uint32_t *list, uint32_t *cnt, int scap) {
+                                                      uint32_t *list, uint32_t *cnt, int scap, int f) {
     pdl_wait();
     pdl_trigger();
     coarse_lists_body(p, cap, m_dev, nle, kfwd, kbwd, slo, shi, nsx, nsy, nsz, ncoarse, list, cnt, scap, blockIdx.x,
-                      gridDim.x);
+                      gridDim.x, f);
+}
+
+// Middle of three levels: each block of 2 x 2 x 2 super cells keeps the
+// kernels of its parent's list (blocks of 4 x 4 x 4 super cells) that reach
+// its own box, tested with the records' centre and r2; a parent list that
+// overflowed is not used (every kernel is tested).  A kernel that reaches a
+// box reaches every box containing it, so the lists equal the one-level ones
+// filtered to these blocks.
+__device__ __forceinline__ void mid_lists_body(const int32_t *m_dev, const float4 *kfwd, const float4 *slo,
+                                               const float4 *shi, int nsx, int nsy, int nsz, int nmid,
+                                               const uint32_t *plist, const uint32_t *pcnt, uint32_t *list,
+                                               uint32_t *cnt, int scap, int bx) {
+    __shared__ uint32_t tmp[33];
+    __shared__ float4 s_lo, s_hi;
+    const int c = bx;
+    if (c >= nmid) return;
+    const int ncx = (nsx + 1) >> 1, ncy = (nsy + 1) >> 1;
+    const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
+    if (threadIdx.x == 0) {
+        float4 lo = make_float4(INFINITY, INFINITY, INFINITY, 0.f), hi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int sx = 2 * cx + dx, sy = 2 * cy + dy, sz = 2 * cz + dz;
+                    if (sx >= nsx || sy >= nsy || sz >= nsz) continue;
+                    const int sc = (sz * nsy + sy) * nsx + sx;
+                    const float4 a = slo[sc], b = shi[sc];
+                    lo = make_float4(fminf(lo.x, a.x), fminf(lo.y, a.y), fminf(lo.z, a.z), 0.f);
+                    hi = make_float4(fmaxf(hi.x, b.x), fmaxf(hi.y, b.y), fmaxf(hi.z, b.z), 0.f);
+                }
+        s_lo = lo;
+        s_hi = hi;
+    }
+    __syncthreads();
+    const float4 lo = s_lo, hi = s_hi;
+    if (!(lo.x <= hi.x)) {
+        if (threadIdx.x == 0) cnt[c] = 0;
+        return;
+    }
+    const int npx = (nsx + 3) >> 2, npy = (nsy + 3) >> 2;
+    const int pc = ((cz >> 1) * npy + (cy >> 1)) * npx + (cx >> 1);
+    const uint32_t pn = pcnt[pc];
+    const bool whole = pn > (uint32_t)scap;  // the parent's list overflowed
+    const int L = whole ? *m_dev : (int)pn;
+    const uint32_t *src = plist + (size_t)pc * scap;
+    uint32_t count = 0;
+    uint32_t *out = list + (size_t)c * scap;
+    for (int q0 = 0; q0 < L; q0 += 256) {
+        const int q = q0 + threadIdx.x;
+        uint32_t hit = 0, j = 0;
+        if (q < L) {
+            j = whole ? (uint32_t)q : src[q];
+            const float4 k = kfwd[3 * j];
+            hit = box_d2(k.x, k.y, k.z, lo, hi) < k.w;
+        }
+        uint32_t tot;
+        const uint32_t off = block_exscan(hit, tmp, &tot);
+        if (hit && count + off < (uint32_t)scap) out[count + off] = j;
+        count += tot;
+    }
+    if (threadIdx.x == 0) cnt[c] = count;
+}
+
+__global__ void __launch_bounds__(256) k_mid_lists(const int32_t *m_dev, const float4 *kfwd, const float4 *slo,
+                                                   const float4 *shi, int nsx, int nsy, int nsz, int nmid,
+                                                   const uint32_t *plist, const uint32_t *pcnt, uint32_t *list,
+                                                   uint32_t *cnt, int scap) {
+    pdl_wait();
+    pdl_trigger();
+    mid_lists_body(m_dev, kfwd, slo, shi, nsx, nsy, nsz, nmid, plist, pcnt, list, cnt, scap, blockIdx.x);
 }
 
 // Second launch: each super cell keeps the kernels of its block's list that
@@ -364,7 +435,7 @@ __global__ void __launch_bounds__(256) k_rebuild_batch(const RebuildArgs *ra) {
     if ((int)blockIdx.x >= r.level1_blocks) return;
     if (r.two_level)
         coarse_lists_body(r.p, r.cap, r.m_dev, r.nle, r.kfwd, r.kbwd, r.slo, r.shi, r.nsx, r.nsy, r.nsz, r.ncoarse,
-                          r.clist, r.ccnt, r.scap, blockIdx.x, r.level1_blocks);
+                          r.clist, r.ccnt, r.scap, blockIdx.x, r.level1_blocks, 2);
     else
         rebuild_body(r.p, r.cap, r.m_dev, r.nle, r.kfwd, r.kbwd, r.slo, r.shi, r.nsuper, r.list, r.cnt, r.scap,
                      r.status, r.needed, blockIdx.x, r.level1_blocks);
@@ -459,7 +530,17 @@ bool ws_ok(const serbf_workspace *ws) { return ws && ws->magic == kMagic && ws->
 // cells, capacity 32768) rebuilds 4x faster in two levels, while the 128^3
 // one (729, 8192) is slower by the extra launch.
 bool rebuild_two_level(int levels, int64_t nsuper, int cap) {
-    return levels == 2 || (levels == 0 && nsuper * (int64_t)cap >= (int64_t)1 << 25);
+    return levels >= 2 || (levels == 0 && nsuper * (int64_t)cap >= (int64_t)1 << 25);
+}
+
+// Three levels (blocks of 4 x 4 x 4 super cells against every kernel, then
+// blocks of 2 x 2 x 2, then super cells) when asked, or by default once the
+// second level alone would make 2^25 box tests: measured, the 256^3 band
+// with super cells of 2 x 2 x 2 cells (4913 blocks of 2 x 2 x 2, capacity
+// 32768) rebuilds in a fraction of its two-level time.  Single fields only;
+// the batched epoch takes two levels.
+bool rebuild_three_level(int levels, int64_t ncoarse, int cap) {
+    return levels == 3 || (levels == 0 && ncoarse * (int64_t)cap >= (int64_t)1 << 25);
 }
 
 }  // namespace
@@ -480,7 +561,7 @@ int batch_rebuild_args(const serbf_points *pts, const serbf_params *prm, const s
     if (!pts || !prm || !cfg || !ws_ok(ws)) return SERBF_EINVAL;
     if (!prm->p || !prm->m || prm->cap < 1 || prm->cap > ws->sz.max_kernels) return SERBF_EINVAL;
     if (pts->n != ws->npoints) return SERBF_EINVAL;
-    if (!(cfg->eps > 0.0 && cfg->eps < 1.0) || cfg->rebuild_levels < 0 || cfg->rebuild_levels > 2) return SERBF_EINVAL;
+    if (!(cfg->eps > 0.0 && cfg->eps < 1.0) || cfg->rebuild_levels < 0 || cfg->rebuild_levels > 3) return SERBF_EINVAL;
     RebuildArgs r;
     memset(&r, 0, sizeof(r));
     const int nsx = ws->ns[0], nsy = ws->ns[1], nsz = ws->ns[2];
@@ -546,7 +627,7 @@ extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params
     if (!prm->p || !prm->m || prm->cap < 1 || prm->cap > ws->sz.max_kernels) return SERBF_EINVAL;
     if (pts->n != ws->npoints || (pts->n > 0 && (!pts->x || !pts->y || !pts->z))) return SERBF_EINVAL;
     if (!(cfg->eps > 0.0 && cfg->eps < 1.0)) return SERBF_EINVAL;
-    if (cfg->rebuild_levels < 0 || cfg->rebuild_levels > 2) return SERBF_EINVAL;
+    if (cfg->rebuild_levels < 0 || cfg->rebuild_levels > 3) return SERBF_EINVAL;
     if (kmajor && (!kmajor->rowptr || (kmajor->cap > 0 && !kmajor->col))) return SERBF_EINVAL;
     if (pmajor && (!pmajor->rowptr || (pmajor->cap > 0 && !pmajor->col))) return SERBF_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -567,11 +648,26 @@ extern "C" int serbf_build_neighbors(const serbf_points *pts, const serbf_params
         const int prep_blocks = (prm->cap + 255) / 256;
         const int nsx = ws->ns[0], nsy = ws->ns[1], nsz = ws->ns[2];
         const int64_t ncoarse = (int64_t)((nsx + 1) / 2) * ((nsy + 1) / 2) * ((nsz + 1) / 2);
+        const int64_t ntop = (int64_t)((nsx + 3) / 4) * ((nsy + 3) / 4) * ((nsz + 3) / 4);
         if (rebuild_two_level(cfg->rebuild_levels, ws->nsuper, prm->cap) && ncoarse <= ws->max_coarse) {
-            launch_pdl(k_coarse_lists, dim3((unsigned)(ncoarse + prep_blocks)), dim3(256), 0, s,
-                       (const float *)prm->p, prm->cap, (const int32_t *)prm->m, nle, ws->kfwd, ws->kbwd,
-                       (const float4 *)ws->sup_lo, (const float4 *)ws->sup_hi, nsx, nsy, nsz, (int)ncoarse,
-                       ws->crs_list, ws->crs_cnt, ws->sz.super_cap);
+            if (rebuild_three_level(cfg->rebuild_levels, ncoarse, prm->cap) && ntop <= ws->nsuper) {
+                // blocks of 4 x 4 x 4 super cells against every kernel (their
+                // lists and counts held in the super cells' storage, which the
+                // last level rewrites), then blocks of 2 x 2 x 2
+                launch_pdl(k_coarse_lists, dim3((unsigned)(ntop + prep_blocks)), dim3(256), 0, s,
+                           (const float *)prm->p, prm->cap, (const int32_t *)prm->m, nle, ws->kfwd, ws->kbwd,
+                           (const float4 *)ws->sup_lo, (const float4 *)ws->sup_hi, nsx, nsy, nsz, (int)ntop,
+                           ws->sup_list, ws->sup_cnt, ws->sz.super_cap, 4);
+                launch_pdl(k_mid_lists, dim3((unsigned)ncoarse), dim3(256), 0, s, (const int32_t *)prm->m,
+                           (const float4 *)ws->kfwd, (const float4 *)ws->sup_lo, (const float4 *)ws->sup_hi, nsx, nsy,
+                           nsz, (int)ncoarse, (const uint32_t *)ws->sup_list, (const uint32_t *)ws->sup_cnt,
+                           ws->crs_list, ws->crs_cnt, ws->sz.super_cap);
+            } else {
+                launch_pdl(k_coarse_lists, dim3((unsigned)(ncoarse + prep_blocks)), dim3(256), 0, s,
+                           (const float *)prm->p, prm->cap, (const int32_t *)prm->m, nle, ws->kfwd, ws->kbwd,
+                           (const float4 *)ws->sup_lo, (const float4 *)ws->sup_hi, nsx, nsy, nsz, (int)ncoarse,
+                           ws->crs_list, ws->crs_cnt, ws->sz.super_cap, 2);
+            }
             launch_pdl(k_fine_lists, dim3(ws->nsuper), dim3(256), 0, s, (const int32_t *)prm->m,
                        (const float4 *)ws->kfwd, (const float4 *)ws->sup_lo, (const float4 *)ws->sup_hi, nsx, nsy,
                        ws->nsuper, (const uint32_t *)ws->crs_list, (const uint32_t *)ws->crs_cnt, ws->sup_list,

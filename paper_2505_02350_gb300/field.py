@@ -217,18 +217,21 @@ class Problem:
 
     def launches_per_epoch(self):
         """Kernel launches of one fused full-batch epoch: item order (2, side
-        stream), rebuild (1, or 2 when the library builds the candidate lists
-        in two levels: cfg.rebuild_levels == 2, or 0 with super cells x
+        stream), rebuild (1; 2 when the library builds the candidate lists
+        in two levels: cfg.rebuild_levels >= 2, or 0 with super cells x
         kernel capacity >= 2^25 on a grid whose blocks of 2 x 2 x 2 super
-        cells fit the workspace), forward + finish (2), step (2), deletion
-        (1), addition (3)."""
+        cells fit the workspace; 3 in three levels: cfg.rebuild_levels == 3,
+        or 0 with those blocks x capacity >= 2^25 as well), forward + finish
+        (2), step (2), deletion (1), addition (3)."""
         sf = self.sizes.super_factor
         ns = [(self.grid.n[k] + sf - 1) // sf for k in range(3)]
         nsuper = ns[0] * ns[1] * ns[2]
         ncoarse = ((ns[0] + 1) // 2) * ((ns[1] + 1) // 2) * ((ns[2] + 1) // 2)
+        ntop = ((ns[0] + 3) // 4) * ((ns[1] + 3) // 4) * ((ns[2] + 3) // 4)
         lv = self.cfg.rebuild_levels
-        two = (lv == 2 or (lv == 0 and nsuper * self.cap >= 1 << 25)) and ncoarse <= nsuper // 4 + 16
-        return 11 + (1 if two else 0)
+        two = (lv >= 2 or (lv == 0 and nsuper * self.cap >= 1 << 25)) and ncoarse <= nsuper // 4 + 16
+        three = two and (lv == 3 or (lv == 0 and ncoarse * self.cap >= 1 << 25)) and ntop <= nsuper
+        return 11 + (1 if two else 0) + (1 if three else 0)
 
     def epoch(self):
         """One Algorithm 3 epoch with the full batch: no host synchronisation."""

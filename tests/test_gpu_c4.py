@@ -1,6 +1,7 @@
 """The largest single-GPU field (60 random primitives on a 256^3 band + far
 field, 9.4 M points, M = 16384) through the C ABI in the launch configuration
-the bench times: two-level neighbour rebuild, fused forward + adjoint with one
+the bench times: super cells of 2 x 2 x 2 cells with the three-level neighbour
+rebuild, fused forward + adjoint with one
 warp per work item.  The oracle checks sampled outputs it can compute one by
 one: the binning (bit-exact), Psi and the support pair counts at every point of
 the 64^3 sub-lattice (every 4th grid point per axis), and the App. A gradients
@@ -28,7 +29,7 @@ def c4():
     cfg, lay, P = synth.workload("c4")
     x, y, z, S = lay[0]
     m = cfg["m"]
-    pb = field.Problem(x, y, z, S, P, m, synth.spacing(256), cap=2 * m, super_factor=4)
+    pb = field.Problem(x, y, z, S, P, m, synth.spacing(256), cap=2 * m, super_factor=2)
     pb.cfg.fwd_warps = 1
     pb.build_neighbors()
     pb.forward_backward()
@@ -39,7 +40,7 @@ def c4():
 def test_c4_binning_and_launch_configuration(c4, orc):
     torch, pb, (x, y, z, S, P, m) = c4
     assert pb.n == x.size > 9_000_000
-    assert pb.launches_per_epoch() == 12  # the two-level rebuild
+    assert pb.launches_per_epoch() == 13  # the three-level rebuild
     assert pb.status()[0] == 0
     g = pb.grid
     orc.set_threads(os.cpu_count() or 1)

@@ -675,7 +675,7 @@ def _list_lengths(pb):
     return out
 
 
-@pytest.mark.parametrize("levels", [1, 2])
+@pytest.mark.parametrize("levels", [1, 2, 3])
 def test_csr_bitexact_rebuild_levels(torch, orc, levels):
     pb = problem("c2", layers=[32, 64])
     pb.cfg.rebuild_levels = levels
@@ -696,27 +696,30 @@ def _small_kernel_problem(**kw):
     return pb
 
 
-def test_two_level_rebuild_with_overflowing_block_lists(torch, orc):
-    """A block list longer than the capacity is not used: its super cells test
-    every kernel, and the lists stay exact."""
+@pytest.mark.parametrize("levels", [2, 3])
+def test_two_level_rebuild_with_overflowing_block_lists(torch, orc, levels):
+    """A block list longer than the capacity is not used: its super cells (or,
+    in three levels, its blocks of 2 x 2 x 2 super cells) test every kernel,
+    and the lists stay exact."""
     probe = _small_kernel_problem()
     L = _list_lengths(probe)
     probe.close()
     assert L["block"] - L["super"] >= 8, L
     cap = (L["block"] + L["super"]) // 2
     pb = _small_kernel_problem(super_cap=cap)
-    pb.cfg.rebuild_levels = 2
+    pb.cfg.rebuild_levels = levels
     _csr_check(torch, orc, pb)
     _forward_check(torch, orc, pb)
 
 
-def test_two_level_rebuild_tiny_ragged(torch, orc):
+@pytest.mark.parametrize("levels", [2, 3])
+def test_two_level_rebuild_tiny_ragged(torch, orc, levels):
     from paper_2505_02350_gb300 import field
     x, y, z = synth.grid(23)
     S = synth.sdf_sphere(x, y, z)
     P = synth.init_kernels(5, 40, rotate=True, length_range=(0.05, 0.3))
     pb = field.Problem(x, y, z, S, P, 40, spacing=synth.spacing(23))
     pb.test_src = (x, y, z, S, np.asarray(P, np.float64))
-    pb.cfg.rebuild_levels = 2
+    pb.cfg.rebuild_levels = levels
     _csr_check(torch, orc, pb)
     _forward_check(torch, orc, pb)
